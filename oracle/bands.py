@@ -1,0 +1,48 @@
+"""Number of propagating channels of a pristine armchair ribbon at energy E.
+
+Paper: an ideal ribbon's conductance is step-like, a multiple of 2e^2/h
+(discussion of Fig. 3).  The multiple is the number of right-moving Bloch
+states at E.  Two independent counts:
+
+* ``channels_closed_form``: the armchair ribbon of N dimer lines separates into
+  transverse modes p = 1..N with c_p = cos(p pi / (N + 1)); mode p carries one
+  right-mover for |t| |1 + 2 c_p| < |E| < |t| (1 + 2 |c_p|)  (the standard
+  nearest-neighbour armchair band edges).
+* ``channels_band_structure``: diagonalise H(k) = H00 + H01 e^{ik} + H01^T e^{-ik}
+  of the unit cell on a k grid and count, for every band, the sign changes of
+  E_b(k) - E with positive slope.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .lattice import blocks
+
+
+def channels_closed_form(N: int, E: float, t: float = -2.7) -> int:
+    p = np.arange(1, N + 1)
+    c = np.cos(p * np.pi / (N + 1))
+    lo = abs(t) * np.abs(1.0 + 2.0 * c)
+    hi = abs(t) * (1.0 + 2.0 * np.abs(c))
+    return int(np.sum((lo < abs(E)) & (abs(E) < hi)))
+
+
+def band_structure(N: int, nk: int = 2001, t: float = -2.7):
+    """Bands E_b(k), k in [-pi, pi) (nk points), shape [nk, 2N] sorted per k."""
+    H00, H01 = blocks(N, t)
+    ks = np.linspace(-np.pi, np.pi, nk, endpoint=False)
+    out = np.empty((nk, 2 * N))
+    for i, k in enumerate(ks):
+        Hk = H00 + H01 * np.exp(1j * k) + H01.T * np.exp(-1j * k)
+        out[i] = np.linalg.eigvalsh(Hk)
+    return ks, out
+
+
+def channels_band_structure(N: int, E: float, nk: int = 2001, t: float = -2.7, bands=None) -> int:
+    """Count right-moving crossings of E (periodic k grid)."""
+    if bands is None:
+        _, bands = band_structure(N, nk, t)
+    d = bands - E
+    d_next = np.roll(d, -1, axis=0)
+    up = (d < 0) & (d_next >= 0)
+    return int(np.sum(up))

@@ -1,0 +1,188 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the mathematics
+(no GPU).  Each test names the passage or the property it checks."""
+import json
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import bands, dense, gradient, lattice, leads, mp, rgf
+
+T_HOP = -2.7
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+def test_lattice_bonds_and_coordination():
+    # Honeycomb lattice, one p orbital per atom (text around Fig. 1(a)): every atom
+    # has at most 3 neighbours, interior atoms exactly 3; H01 has N-1 bonds.
+    for N in (2, 5, 11, 12):
+        H00, H01 = lattice.blocks(N, T_HOP)
+        assert np.allclose(H00, H00.T)
+        deg = (np.abs(H00) > 0).sum(1) + (np.abs(H01) > 0).sum(1) + (np.abs(H01) > 0).sum(0)
+        assert deg.max() == (2 if N == 2 else 3)
+        assert (np.abs(H01) > 0).sum() == N - 1
+        # interior rows (1..N-2) are fully coordinated
+        for j in range(1, N - 1):
+            assert deg[2 * j] == 3 and deg[2 * j + 1] == 3
+
+
+def test_band_edges_closed_form_vs_band_structure():
+    # Step-like conductance in multiples of 2e^2/h (Fig. 3 discussion): the
+    # closed-form channel count equals a brute-force band-structure count.
+    for N in (2, 5, 11, 12, 13):
+        _, bs = bands.band_structure(N, nk=4001)
+        for E in np.linspace(-3.3, 3.3, 37):
+            if np.min(np.abs(np.abs(E) - np.abs(T_HOP) * np.abs(
+                    1 + 2 * np.cos(np.arange(1, N + 1) * np.pi / (N + 1))))) < 1e-2:
+                continue
+            assert bands.channels_closed_form(N, E) == bands.channels_band_structure(N, E, bands=bs), (N, E)
+
+
+def test_metallic_armchair_has_one_channel_at_low_energy():
+    # N = 3q + 2 armchair ribbons are metallic; N = 11 has one channel on [-1, 1] eV.
+    for E in np.linspace(-1, 1, 21):
+        if E == 0:
+            continue
+        assert bands.channels_closed_form(11, E) == 1
+    assert bands.channels_closed_form(245, 0.5) == 17
+
+
+def _chain_surface(E, eta, t=T_HOP):
+    # Semi-infinite monatomic chain: g = (z - sqrt(z^2 - 4 t^2)) / (2 t^2), Im g < 0.
+    z = E + 1j * eta
+    s = np.sqrt(z * z - 4 * t * t + 0j)
+    g1, g2 = (z - s) / (2 * t * t), (z + s) / (2 * t * t)
+    return g1 if g1.imag < 0 else g2
+
+
+def test_decimation_matches_monatomic_chain_closed_form():
+    # N = 2 is a monatomic chain (4 atoms per cell, all hoppings t): Sigma = t^2 g_chain.
+    for E in (-4.0, -1.3, 0.2, 2.5, 6.0):
+        sL, sR = leads.self_energies(2, E, 1e-8, T_HOP)
+        ref = T_HOP ** 2 * _chain_surface(E, 1e-8)
+        assert abs(sR[3, 3] - ref) < 1e-10 * max(1, abs(ref))
+        assert abs(sL[0, 0] - ref) < 1e-10 * max(1, abs(ref))
+        mask = np.ones_like(sR, dtype=bool)
+        mask[3, 3] = False
+        assert np.abs(sR[mask]).max() == 0.0
+
+
+def test_decimation_fixed_point_residual_and_symmetry():
+    for N in (5, 11, 12):
+        H00, H01 = lattice.blocks(N, T_HOP)
+        for E in (-0.9, 0.01, 0.37, 1.7):
+            z = E + 1e-8j
+            gR, it = leads.surface_green(H00, H01, H01.T, z)
+            assert it < 60
+            assert leads.fixed_point_residual(gR, H00, H01, H01.T, z) < 1e-10
+            assert np.abs(gR - gR.T).max() < 1e-10 * np.abs(gR).max()
+
+
+def test_decimation_fails_loudly_at_exact_charge_neutrality():
+    # At E = 0 exactly the N = 23 iteration diverges instead of converging.
+    with pytest.raises(leads.NoConvergence):
+        leads.self_energies(23, 0.0, 1e-8, T_HOP)
+
+
+def test_eq2_forms_agree_and_rgf_equals_dense_definition():
+    # Eq. 2 as printed (Tr[G_L G^a G_R G^r]) equals Tr[G_L G_1L G_R G_1L^+]; the
+    # recursion of Eqs. 4-5 reaches the dense inverse of Eq. 1.
+    N, L = 11, 7
+    eps = workloads.anderson_onsite(N, L, 0.25, 3)
+    rem = workloads.edge_removed(N, L, 0.3, 4)
+    assert rem.sum() > 0
+    for E in (-0.77, -0.1, 0.003, 0.45):
+        Td = dense.transmission_dense(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        Tp = dense.transmission_dense_paper_form(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        Tr = rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        assert abs(Tp - Td) < 1e-12
+        assert abs(Tr - Td) < 1e-11
+        assert 0.0 <= Tr <= bands.channels_closed_form(N, E) + 1e-12
+
+
+def test_reciprocity():
+    N, L = 12, 6
+    eps = workloads.anderson_onsite(N, L, 0.4, 9)
+    rem = workloads.edge_removed(N, L, 0.2, 10)
+    for E in (-1.1, 0.2, 0.9):
+        a = rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        b = rgf.transmission_right_to_left(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        assert abs(a - b) < 1e-12
+
+
+def test_pristine_ribbon_is_quantised():
+    # Ideal ribbon: T is the number of propagating channels (Fig. 3 discussion),
+    # exactly when no absorption is added inside the device (eta_device = 0).
+    for N in (5, 11, 12):
+        for E in (0.15, -0.6, 1.4, -2.3):
+            n = bands.channels_closed_form(N, E)
+            T = rgf.transmission(N, 15, E, 0.0, 1e-8, T_HOP)
+            assert abs(T - n) < 1e-9, (N, E, T, n)
+
+
+def test_eta_absorption_is_linear_in_eta_and_length():
+    # With eta_device > 0 the device absorbs: n_ch - T = O(eta * L).
+    N, E = 11, 0.5
+    d1 = 1.0 - rgf.transmission(N, 20, E, 1e-8, 1e-8, T_HOP)
+    d2 = 1.0 - rgf.transmission(N, 20, E, 2e-8, 1e-8, T_HOP)
+    d3 = 1.0 - rgf.transmission(N, 40, E, 1e-8, 1e-8, T_HOP)
+    assert d1 > 0
+    assert abs(d2 / d1 - 2.0) < 1e-3
+    assert abs(d3 / d1 - 2.0) < 1e-3
+
+
+def test_gradient_adjoint_closed_form_and_finite_differences():
+    N, L, E = 11, 6, 0.31
+    eps = workloads.anderson_onsite(N, L, 0.3, 11)
+    rem = workloads.edge_removed(N, L, 0.3, 12)
+    T, gadj = gradient.adjoint(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+    gcf = gradient.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+    assert np.abs(gadj - gcf).max() < 1e-12 * max(1.0, np.abs(gcf).max())
+    assert np.all(gcf[rem.astype(bool)] == 0.0)
+    rng = np.random.default_rng(0)
+    d = 1e-6
+    for _ in range(6):
+        n, i = rng.integers(L), rng.integers(2 * N)
+        if rem[n, i]:
+            continue
+        ep, em = eps.copy(), eps.copy()
+        ep[n, i] += d
+        em[n, i] -= d
+        fd = (rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, ep, rem)
+              - rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, em, rem)) / (2 * d)
+        assert abs(fd - gcf[n, i]) < 1e-8 + 1e-5 * abs(gcf[n, i])
+
+
+def test_gradient_sums_to_uniform_shift_derivative():
+    # The derivative along a uniform shift of every device on-site energy is the
+    # sum of the gradient.
+    N, L, E = 5, 5, 0.4
+    eps = workloads.anderson_onsite(N, L, 0.2, 5)
+    _, g = gradient.adjoint(N, L, E, 0.0, 1e-8, T_HOP, eps, None)
+    d = 1e-6
+    Tp = rgf.transmission(N, L, E, 0.0, 1e-8, T_HOP, eps + d)
+    Tm = rgf.transmission(N, L, E, 0.0, 1e-8, T_HOP, eps - d)
+    assert abs(g.sum() - (Tp - Tm) / (2 * d)) < 1e-7
+
+
+def test_complex128_against_arbitrary_precision_golden():
+    # 40-digit values written by tests/golden/make_golden.py (oracle.mp only).
+    g = json.loads((GOLDEN / "mp_transmission.json").read_text())
+    for name, v in g.items():
+        eps = workloads.anderson_onsite(v["N"], v["L"], v["W"], v["seed"]) if v["W"] > 0 else None
+        T = rgf.transmission(v["N"], v["L"], v["E"], v["eta_device"], v["eta_lead"], T_HOP, eps)
+        if v["E"] == 0.0:
+            # E = 0 exactly is condition-limited in complex128 (edge-state pole of
+            # the leads): the error is large but bounded.
+            assert abs(T - v["T"]) < 5e-3, name
+        else:
+            assert abs(T - v["T"]) < 1e-10, name
+
+
+def test_mp_recursion_matches_complex128_when_well_conditioned():
+    N, L, E = 5, 4, 0.37
+    eps = workloads.anderson_onsite(N, L, 0.2, 2)
+    a = mp.transmission(N, L, E, 1e-8, 1e-8, T_HOP, eps, dps=30)
+    b = rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, eps)
+    assert abs(a - b) < 1e-12
