@@ -1,0 +1,173 @@
+/*
+ * rgf.h -- C ABI of the GB300 recursive Green's function (RGF) library.
+ *
+ * Computes the two-terminal Landauer conductance of armchair graphene
+ * nanoribbons (one p orbital per carbon atom, nearest-neighbour hopping t,
+ * semi-infinite pristine leads of the same width), following S. Ihnatsenka,
+ * Comput. Phys. Commun. 183 (2012) 543:
+ *
+ *   Eq. 1   G = (E - H)^-1, retarded: E -> E + i*eta
+ *   Eq. 2   T = Tr[Gamma_L G_1L Gamma_R G_1L^dagger]   (conductance in 2e^2/h)
+ *   Eq. 3   Dyson equation G = G0 + G0 Sigma G, applied slice by slice as
+ *   Eqs. 4-5  g_j = (z - H_jj - V^T g_{j-1} V)^-1,   G_1j = G_1,j-1 V g_j
+ *
+ * with the lead self-energies Sigma_L, Sigma_R included at the first and the
+ * last slice (text after Eqs. 4-5), computed here by Lopez Sancho-Rubio
+ * decimation, and Gamma = i (Sigma - Sigma^dagger).
+ *
+ * Geometry and orbital order.  A ribbon has N dimer lines (rows j = 0..N-1)
+ * and L unit cells along the transport axis; a unit cell holds M = 2N atoms.
+ * Even rows hold atoms at x = 0 and a, odd rows at x = 1.5a and 2.5a (a = C-C
+ * distance).  Orbital o = 2*j + k of a cell is the left (k = 0) or right (k = 1)
+ * atom of row j.  Per-orbital arrays are row-major [L][2N].
+ *
+ * Conventions for every entry point:
+ *   - Callers own every buffer they pass; the library never keeps a pointer
+ *     to caller memory after the call returns (except rgf_build_ribbon_dev,
+ *     which documents its own rule).
+ *   - Nothing throws or aborts across this ABI.  A call returns RGF_OK or the
+ *     first error; rgf_last_error() then gives a message (per thread).
+ *   - Calls without a `stream` argument run on the legacy default stream of the
+ *     current device and return after the results are on the host.
+ *   - "Host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device.
+ *   - On a failing call, host outputs are left untouched where the error is
+ *     caught before launch (RGF_EINVAL, RGF_ENOMEM); per-chain numeric failures
+ *     (RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE, RGF_ETIMEOUT) are reported
+ *     per chain in chain_status, that chain's T is NaN, and the other chains'
+ *     results are valid.
+ */
+#ifndef RGF_H
+#define RGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RGF_OK = 0,
+    RGF_EINVAL = 1,      /* bad argument (sizes, NULL pointer, unknown enum)          */
+    RGF_ENOMEM = 2,      /* device or host allocation failed                          */
+    RGF_ECUDA = 3,       /* a CUDA runtime call failed                                */
+    RGF_ENOCONV = 4,     /* lead decimation hit its iteration cap or went non-finite   */
+    RGF_ESINGULAR = 5,   /* a zero pivot in a slice inverse                           */
+    RGF_ENONFINITE = 6,  /* NaN or Inf in a slice Green's function or in T            */
+    RGF_ETIMEOUT = 7     /* a device-side wait exceeded its spin limit                */
+} rgf_status;
+
+typedef enum {
+    RGF_FP64 = 0,        /* every step in IEEE binary64                               */
+    RGF_MIXED = 1        /* slice recursion in double-float (pairs of binary32 on the
+                            FP32 pipes, ~48-bit significand); leads and trace binary64 */
+} rgf_precision;
+
+/* One ribbon instance (the paper's input step: geometry, defects, disorder). */
+typedef struct {
+    int N;                     /* dimer lines, >= 2; orbitals per cell M = 2N          */
+    int L;                     /* unit cells in the scattering region, >= 1            */
+    double t;                  /* nearest-neighbour hopping in eV (e.g. -2.7)          */
+    const double* onsite;      /* host [L][2N] on-site energies (eV), or NULL          */
+    double anderson_W;         /* if onsite == NULL: eps ~ U[-W, W] from `seed`        */
+    uint64_t seed;             /* SplitMix64 stream of the Anderson energies           */
+    double edge_p;             /* if removed == NULL: rows 0 and N-1 atoms removed     */
+    uint64_t edge_seed;        /*   with probability edge_p, from stream `edge_seed`   */
+    const uint8_t* removed;    /* host [L][2N], 1 = atom absent, or NULL               */
+} rgf_ribbon_desc;
+
+typedef struct rgf_ribbon rgf_ribbon;   /* opaque; device-resident copy of a ribbon */
+
+/*
+ * Random inputs.  Draw i of stream s is the SplitMix64 output
+ * mix64(s + (i+1) * 0x9E3779B97F4A7C15) and u = (bits >> 11) * 2^-53.
+ * Orbital o of cell n uses draw n*2N + o.  Anderson: eps = W (2u - 1).
+ * Edge roughness: an atom of row 0 or row N-1 is removed when u < p (other
+ * rows are never drawn).  Leads are always pristine.
+ *
+ * rgf_generate_onsite: host only (no GPU needed).  Fills onsite_out[L*2N]
+ * and removed_out[L*2N] (both host, caller-owned, either may be NULL) with
+ * the arrays `desc` describes (copies when desc gives explicit arrays).
+ * Errors: RGF_EINVAL.
+ */
+rgf_status rgf_generate_onsite(const rgf_ribbon_desc* desc, double* onsite_out,
+                               uint8_t* removed_out);
+
+/* Build a ribbon on the current device (generates or copies the arrays, then
+ * uploads them).  *out is owned by the caller; release with rgf_free_ribbon.
+ * Errors: RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA. */
+rgf_status rgf_build_ribbon(const rgf_ribbon_desc* desc, rgf_ribbon** out);
+
+/* Same, from arrays already on the device: onsite_dev [L*2N] (binary64) and
+ * removed_dev [L*2N] (uint8, or NULL for none).  The arrays are copied
+ * device-to-device on `stream`; the caller may free them once the stream has
+ * passed this call. */
+rgf_status rgf_build_ribbon_dev(int N, int L, double t, const double* onsite_dev,
+                                const uint8_t* removed_dev, void* stream, rgf_ribbon** out);
+
+void rgf_free_ribbon(rgf_ribbon* rib);
+
+/*
+ * Lead self-energies by Lopez Sancho-Rubio decimation (binary64), one per
+ * energy, for the pristine ribbon of N dimer lines (paper: the self-energies
+ * of the leads enter at the first and the last slice, text after Eqs. 4-5).
+ *   side 0: Sigma_L = H01^T g_s H01 on the first device cell (left lead);
+ *   side 1: Sigma_R = H01 g_s H01^T on the last device cell (right lead);
+ * with z = E + i*eta and the decimation stopped when the largest entry of the
+ * effective couplings is below 1e-14 eV (cap 200 iterations).
+ * sigma: host [nE][2N][2N] complex, interleaved (re, im) binary64, row-major
+ *        (caller-owned, 8*nE*(2N)^2 doubles).
+ * iters: host [nE] or NULL: iterations used, or -1 where decimation failed.
+ * Returns RGF_ENOCONV if any energy failed (its sigma entries are NaN).
+ */
+rgf_status rgf_lead_selfenergy(int N, double t, const double* E, int nE, double eta,
+                               int side, double* sigma, int* iters);
+
+/*
+ * Conductance T (in units of 2e^2/h) for `nchains` independent chains.  Chain c
+ * is ribbon rib[c] at energy E[c] (several chains may share a ribbon).
+ * eta_device is the broadening inside the scattering region, eta_lead the one
+ * of the lead decimation.
+ *   rib:   host array of nchains ribbon pointers.
+ *   E:     host [nchains] energies (eV).
+ *   T:     host [nchains] output.
+ *   chain_status: host [nchains] int32 output (rgf_status per chain) or NULL.
+ * Errors: RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA, or the first per-chain failure.
+ */
+rgf_status rgf_conductance(const rgf_ribbon* const* rib, const double* E, int nchains,
+                           double eta_device, double eta_lead, int precision,
+                           double* T, int32_t* chain_status);
+
+/* Same with device buffers and a caller stream (E_dev, T_dev, status_dev on
+ * the device; status_dev may be NULL).  Asynchronous: returns after launch;
+ * results are valid once `stream` has passed the call.  Launch-time errors are
+ * returned; per-chain failures appear in status_dev. */
+rgf_status rgf_conductance_dev(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
+                               double eta_device, double eta_lead, int precision,
+                               void* stream, double* T_dev, int32_t* status_dev);
+
+/*
+ * Conductance and its gradient dT/d eps for every on-site energy of the
+ * scattering region (adjoint, reverse sweep over the recursion of Eqs. 4-5;
+ * the slice Green's functions are checkpointed every ckpt_stride unit cells
+ * and recomputed between checkpoints).  ckpt_stride <= 0 picks ~sqrt(L).
+ *   dT_deps: host [nchains][L*2N] binary64 (row-major per chain, orbital
+ *            order of rgf_ribbon_desc); 0 on removed atoms.
+ * Other arguments and errors as rgf_conductance.
+ */
+rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, int nchains,
+                                double eta_device, double eta_lead, int precision,
+                                int ckpt_stride, double* T, double* dT_deps,
+                                int32_t* chain_status);
+
+const char* rgf_status_str(int status);
+const char* rgf_last_error(void);
+
+/* Library version string. */
+const char* rgf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGF_H */

@@ -1,0 +1,156 @@
+// rgf_common.cuh -- number types and small helpers shared by the RGF kernels.
+//
+// Two arithmetic types carry the slice recursion:
+//   double  -- IEEE binary64 (the RGF_FP64 path, FP64 pipe);
+//   df32    -- "double-float": an unevaluated sum hi + lo of two binary32 values
+//              (|lo| <= ulp(hi)/2 after normalisation, ~48-bit significand),
+//              evaluated on the FP32 pipes (the RGF_MIXED path).
+// The double-float operations below are the classical error-free
+// transformations: Knuth's TwoSum, the FMA form of Dekker's TwoProduct and
+// Dekker's Fast2Sum (T. J. Dekker, Numer. Math. 18 (1971) 224; D. E. Knuth,
+// TAOCP vol. 2, 4.2.2).  They are written with explicit round-to-nearest
+// intrinsics so that the compiler cannot contract or reorder them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rgf {
+
+// ---------------------------------------------------------------------------
+// double-float
+// ---------------------------------------------------------------------------
+struct df32 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ df32 df_from_double(double x) {
+    float h = __double2float_rn(x);
+    float l = __double2float_rn(x - (double)h);
+    return {h, l};
+}
+__device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    df32 r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ df32 df_neg(df32 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df32 df_sub(df32 a, df32 b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    df32 r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// complex numbers over a real type R (double or df32)
+// ---------------------------------------------------------------------------
+template <class R> struct cx { R re, im; };
+using zd = cx<double>;
+using zf = cx<df32>;
+
+// Conversions to / from binary64 complex.
+__device__ __forceinline__ zd to_z(zd a) { return a; }
+__device__ __forceinline__ zd to_z(zf a) { return {df_to_double(a.re), df_to_double(a.im)}; }
+template <class R> __device__ __forceinline__ cx<R> from_z(double re, double im);
+template <> __device__ __forceinline__ zd from_z<double>(double re, double im) { return {re, im}; }
+template <> __device__ __forceinline__ zf from_z<df32>(double re, double im) {
+    return {df_from_double(re), df_from_double(im)};
+}
+template <class R> __device__ __forceinline__ cx<R> czero() { return from_z<R>(0.0, 0.0); }
+
+// a + b, a - b, a * b
+__device__ __forceinline__ zd cadd(zd a, zd b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ zd csub(zd a, zd b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ zd cmul(zd a, zd b) {
+    return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ zf cadd(zf a, zf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ zf csub(zf a, zf b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ zf cmul(zf a, zf b) {
+    return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)),
+            df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+
+// c + s * a * b with s = +1 or -1 (multiply-accumulate).
+__device__ __forceinline__ zd cmac(zd c, zd a, zd b, bool neg) {
+    double ar = neg ? -a.re : a.re, ai = neg ? -a.im : a.im;
+    c.re = fma(ar, b.re, c.re);
+    c.re = fma(-ai, b.im, c.re);
+    c.im = fma(ar, b.im, c.im);
+    c.im = fma(ai, b.re, c.im);
+    return c;
+}
+
+// One real component of c + x1*y1 - x2*y2 in double-float, unnormalised
+// result (hi, lo) with the product errors and cross terms folded into lo.
+__device__ __forceinline__ df32 df_dot2(df32 c, df32 x1, df32 y1, df32 x2, df32 y2) {
+    float p1 = __fmul_rn(x1.hi, y1.hi);
+    float e1 = __fmaf_rn(x1.hi, y1.hi, -p1);
+    float p2 = __fmul_rn(x2.hi, y2.hi);
+    float e2 = __fmaf_rn(x2.hi, y2.hi, -p2);
+    float x = __fmaf_rn(x1.hi, y1.lo, __fmaf_rn(x1.lo, y1.hi, e1));
+    x = __fsub_rn(x, __fmaf_rn(x2.hi, y2.lo, __fmaf_rn(x2.lo, y2.hi, e2)));
+    float s1, t1, s2, t2;
+    two_sum(c.hi, p1, s1, t1);
+    two_sum(s1, -p2, s2, t2);
+    float lo = __fadd_rn(__fadd_rn(c.lo, x), __fadd_rn(t1, t2));
+    df32 r;
+    fast_two_sum(s2, lo, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ zf cmac(zf c, zf a, zf b, bool neg) {
+    df32 ar = neg ? df_neg(a.re) : a.re, ai = neg ? df_neg(a.im) : a.im;
+    zf r;
+    r.re = df_dot2(c.re, ar, b.re, ai, b.im);      // c.re + ar*br - ai*bi
+    r.im = df_dot2(c.im, ar, b.im, df_neg(ai), b.re);  // c.im + ar*bi + ai*br
+    return r;
+}
+
+// Scale by a real binary64 constant.
+__device__ __forceinline__ zd cscale(zd a, double s) { return {a.re * s, a.im * s}; }
+__device__ __forceinline__ zf cscale(zf a, double s) {
+    df32 d = df_from_double(s);
+    return {df_mul(a.re, d), df_mul(a.im, d)};
+}
+
+// |a|^2 as a binary64 estimate (pivot selection only).
+__device__ __forceinline__ double cabs2(zd a) { return a.re * a.re + a.im * a.im; }
+__device__ __forceinline__ double cabs2(zf a) {
+    double r = a.re.hi, i = a.im.hi;
+    return r * r + i * i;
+}
+
+__device__ __forceinline__ bool cfinite(zd a) { return isfinite(a.re) && isfinite(a.im); }
+__device__ __forceinline__ bool cfinite(zf a) { return isfinite(a.re.hi) && isfinite(a.im.hi); }
+
+// ---------------------------------------------------------------------------
+// Status codes (mirror rgf_status in include/rgf.h).
+// ---------------------------------------------------------------------------
+enum : int {
+    ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOCONV = 4,
+    ST_ESINGULAR = 5, ST_ENONFINITE = 6, ST_ETIMEOUT = 7
+};
+
+}  // namespace rgf

@@ -1,0 +1,239 @@
+// rgf_device.cuh -- thread-block (CTA) level dense complex kernels used by the
+// RGF sweeps: a tiled GEMM and an in-place Gauss-Jordan inverse with partial
+// pivoting.  All matrices are row-major in global memory (L2-resident per
+// chain); every routine is called by all threads of the block and ends with a
+// __syncthreads().  The block size is RGF_NT threads.
+#pragma once
+
+#include "rgf_common.cuh"
+
+#ifndef RGF_NT
+#define RGF_NT 512
+#endif
+
+namespace rgf {
+
+constexpr int NT = RGF_NT;
+constexpr int NWARP = NT / 32;
+
+// ---------------------------------------------------------------------------
+// Block reductions
+// ---------------------------------------------------------------------------
+// Max of a non-negative binary64 value over the block; NaN wins (so that a
+// non-finite matrix is noticed).  red: >= NWARP doubles of shared memory.
+__device__ __forceinline__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = (isnan(w) || w > v) ? w : v;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = red[0];
+    for (int w = 1; w < NWARP; ++w) {
+        double x = red[w];
+        r = (isnan(x) || x > r) ? x : r;
+    }
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int w = 0; w < NWARP; ++w) r += red[w];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// C (m x n) {=, +=, -=} op(A) (m x kd) * op(B) (kd x n)
+// op(X) = X or X^T (no conjugation).  64 x 64 output tiles, k-chunks of 8,
+// each thread owns a 2 x 4 register tile.  C must not alias A or B.
+// smem: 2 * 8 * 64 elements of cx<R>.
+// ---------------------------------------------------------------------------
+enum GemmMode { GEMM_SET = 0, GEMM_ADD = 1, GEMM_SUB = 2 };
+
+template <class R, bool TA, bool TB>
+__device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int lda,
+                         const cx<R>* __restrict__ B, int ldb, cx<R>* __restrict__ C, int ldc,
+                         int mode, cx<R>* sm) {
+    cx<R>* As = sm;            // [8][64], k-major
+    cx<R>* Bs = sm + 8 * 64;   // [8][64]
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    static_assert(NT == 512, "cta_gemm assumes 512 threads");
+    for (int i0 = 0; i0 < m; i0 += 64) {
+        for (int j0 = 0; j0 < n; j0 += 64) {
+            cx<R> acc[2][4];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = czero<R>();
+            for (int k0 = 0; k0 < kd; k0 += 8) {
+                {
+                    int r, kk;
+                    if (TA) { kk = tid >> 6; r = tid & 63; }   // A^T: rows of A are k
+                    else    { r = tid >> 3;  kk = tid & 7;  }
+                    int gi = i0 + r, gk = k0 + kk;
+                    cx<R> v = czero<R>();
+                    if (gi < m && gk < kd) v = TA ? A[(size_t)gk * lda + gi] : A[(size_t)gi * lda + gk];
+                    As[kk * 64 + r] = v;
+                }
+                {
+                    int kk, c;
+                    if (TB) { c = tid >> 3; kk = tid & 7; }
+                    else    { kk = tid >> 6; c = tid & 63; }
+                    int gk = k0 + kk, gj = j0 + c;
+                    cx<R> v = czero<R>();
+                    if (gk < kd && gj < n) v = TB ? B[(size_t)gj * ldb + gk] : B[(size_t)gk * ldb + gj];
+                    Bs[kk * 64 + c] = v;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    cx<R> a0 = As[kk * 64 + ty * 2], a1 = As[kk * 64 + ty * 2 + 1];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        cx<R> b = Bs[kk * 64 + tx * 4 + c];
+                        acc[0][c] = cmac(acc[0][c], a0, b, false);
+                        acc[1][c] = cmac(acc[1][c], a1, b, false);
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                int gi = i0 + ty * 2 + r;
+                if (gi >= m) continue;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    int gj = j0 + tx * 4 + c;
+                    if (gj >= n) continue;
+                    cx<R>* p = C + (size_t)gi * ldc + gj;
+                    if (mode == GEMM_SET) *p = acc[r][c];
+                    else if (mode == GEMM_ADD) *p = cadd(*p, acc[r][c]);
+                    else *p = csub(*p, acc[r][c]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inverse with partial (row) pivoting.
+//   A (K x K, leading dim lda) is destroyed; A^-1 is written to G (ldg).
+//   Pivot j: pick the row p >= j with the largest |A[p][j]|, swap rows j and p,
+//   scale the pivot row by 1/A[j][j] (kept in its column j), eliminate column
+//   j from every other row (storing -A[i][j]/A[j][j] in column j).  The row
+//   swaps are undone at the end by a column permutation applied while copying
+//   into G.  The pivot reciprocal is formed in binary64.
+// Returns a flag: bit 0 = zero pivot met, bit 1 = non-finite pivot met.
+// ---------------------------------------------------------------------------
+template <class R>
+struct GJSmem {
+    cx<R>* rowbuf;   // [Kmax]
+    cx<R>* colbuf;   // [Kmax]
+    cx<R>* colval;   // [Kmax] next pivot column (fresh values)
+    double* colabs;  // [Kmax]
+    int* perm;       // [Kmax]
+    int* idx;        // [Kmax]
+    int* ctl;        // [4]: pivot row, flag
+    zd* inv;         // [1]
+};
+
+template <class R>
+__device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __restrict__ G, int ldg,
+                             GJSmem<R> s) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < K; i += NT) {
+        cx<R> v = A[(size_t)i * lda];
+        s.colval[i] = v;
+        s.colabs[i] = cabs2(v);
+    }
+    if (tid == 0) s.ctl[1] = 0;
+    __syncthreads();
+    for (int j = 0; j < K; ++j) {
+        if (warp == 0) {
+            double best = -1.0;
+            int bi = j;
+            for (int i = j + lane; i < K; i += 32) {
+                double v = s.colabs[i];
+                if (v > best || isnan(v)) { best = isnan(v) ? INFINITY : v; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                zd pz = to_z(s.colval[bi]);
+                double d = pz.re * pz.re + pz.im * pz.im;
+                int flag = s.ctl[1];
+                if (!(d > 0.0)) { flag |= 1; d = 1.0; pz = {1.0, 0.0}; }
+                if (!isfinite(d)) { flag |= 2; }
+                s.ctl[1] = flag;
+                s.ctl[0] = bi;
+                s.perm[j] = bi;
+                *s.inv = zd{pz.re / d, -pz.im / d};
+            }
+        }
+        __syncthreads();
+        const int p = s.ctl[0];
+        const zd invz = *s.inv;
+        const cx<R> invR = from_z<R>(invz.re, invz.im);
+        for (int k = tid; k < K; k += NT) {
+            cx<R> rb = A[(size_t)p * lda + k];
+            if (p != j) A[(size_t)p * lda + k] = A[(size_t)j * lda + k];
+            s.rowbuf[k] = (k == j) ? invR : cmul(rb, invR);
+        }
+        for (int i = tid; i < K; i += NT) {
+            cx<R> v = czero<R>();
+            if (i != j) v = (i == p) ? A[(size_t)j * lda + j] : A[(size_t)i * lda + j];
+            s.colbuf[i] = v;
+        }
+        __syncthreads();
+        for (int i = warp; i < K; i += NWARP) {
+            cx<R>* row = A + (size_t)i * lda;
+            if (i == j) {
+                for (int k = lane; k < K; k += 32) row[k] = s.rowbuf[k];
+            } else {
+                const cx<R> ci = s.colbuf[i];
+                for (int k = lane; k < K; k += 32) {
+                    cx<R> a = (k == j) ? czero<R>() : row[k];
+                    a = cmac(a, ci, s.rowbuf[k], true);
+                    row[k] = a;
+                    if (k == j + 1 && i > j) {
+                        s.colval[i] = a;
+                        s.colabs[i] = cabs2(a);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        for (int c = 0; c < K; ++c) s.idx[c] = c;
+        for (int j = K - 1; j >= 0; --j) {
+            int p = s.perm[j];
+            int tmp = s.idx[j]; s.idx[j] = s.idx[p]; s.idx[p] = tmp;
+        }
+    }
+    __syncthreads();
+    for (int i = warp; i < K; i += NWARP) {
+        const cx<R>* row = A + (size_t)i * lda;
+        cx<R>* grow = G + (size_t)i * ldg;
+        for (int c = lane; c < K; c += 32) grow[c] = row[s.idx[c]];
+    }
+    const int flag = s.ctl[1];
+    __syncthreads();
+    return flag;
+}
+
+}  // namespace rgf

@@ -1,0 +1,206 @@
+"""Python binding of the C ABI in ``include/rgf.h`` (argument marshalling only).
+
+Every numeric step runs in ``librgf.so``; this module only converts arrays,
+owns ribbon handles and raises on error codes.  It raises ``ImportError`` at
+import time if the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(os.environ.get("RGF_LIB", Path(__file__).resolve().parent / "librgf.so"))
+if not _LIB_PATH.exists():
+    raise ImportError(f"{_LIB_PATH} not found: build it with `python -m paper_1107_5300_gb300.build`")
+lib = C.CDLL(str(_LIB_PATH))
+
+RGF_OK, RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA, RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE, RGF_ETIMEOUT = range(8)
+RGF_FP64, RGF_MIXED = 0, 1
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENONFINITE", "ETIMEOUT"]
+
+# Symbols declared in include/rgf.h (checked by the CPU tests).
+EXPORTS = ["rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "rgf_free_ribbon",
+           "rgf_lead_selfenergy", "rgf_conductance", "rgf_conductance_dev",
+           "rgf_conductance_grad", "rgf_status_str", "rgf_last_error", "rgf_version"]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("N", C.c_int), ("L", C.c_int), ("t", C.c_double),
+                ("onsite", C.POINTER(C.c_double)), ("anderson_W", C.c_double),
+                ("seed", C.c_uint64), ("edge_p", C.c_double), ("edge_seed", C.c_uint64),
+                ("removed", C.POINTER(C.c_uint8))]
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_i32p = C.POINTER(C.c_int32)
+_u8p = C.POINTER(C.c_uint8)
+_vp = C.c_void_p
+
+lib.rgf_generate_onsite.argtypes = [C.POINTER(_Desc), _dp, _u8p]
+lib.rgf_build_ribbon.argtypes = [C.POINTER(_Desc), C.POINTER(_vp)]
+lib.rgf_build_ribbon_dev.argtypes = [C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, C.POINTER(_vp)]
+lib.rgf_free_ribbon.argtypes = [_vp]
+lib.rgf_free_ribbon.restype = None
+lib.rgf_lead_selfenergy.argtypes = [C.c_int, C.c_double, _dp, C.c_int, C.c_double, C.c_int, _dp, _ip]
+lib.rgf_conductance.argtypes = [C.POINTER(_vp), _dp, C.c_int, C.c_double, C.c_double, C.c_int,
+                                _dp, _i32p]
+lib.rgf_conductance_dev.argtypes = [C.POINTER(_vp), _vp, C.c_int, C.c_double, C.c_double,
+                                    C.c_int, _vp, _vp, _vp]
+lib.rgf_conductance_grad.argtypes = [C.POINTER(_vp), _dp, C.c_int, C.c_double, C.c_double,
+                                     C.c_int, C.c_int, _dp, _dp, _i32p]
+lib.rgf_status_str.restype = C.c_char_p
+lib.rgf_status_str.argtypes = [C.c_int]
+lib.rgf_last_error.restype = C.c_char_p
+lib.rgf_version.restype = C.c_char_p
+for _f in ("rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "rgf_lead_selfenergy",
+           "rgf_conductance", "rgf_conductance_dev", "rgf_conductance_grad"):
+    getattr(lib, _f).restype = C.c_int
+
+
+class RGFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, allow=()):
+    if st != RGF_OK and st not in allow:
+        raise RGFError(st, lib.rgf_last_error().decode())
+    return st
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
+
+
+def _desc(N, L, t, onsite, W, seed, edge_p, edge_seed, removed):
+    d = _Desc()
+    d.N, d.L, d.t = int(N), int(L), float(t)
+    d.onsite = _ptr(onsite, C.c_double)
+    d.anderson_W, d.seed = float(W), int(seed) & 0xFFFFFFFFFFFFFFFF
+    d.edge_p, d.edge_seed = float(edge_p), int(edge_seed) & 0xFFFFFFFFFFFFFFFF
+    d.removed = _ptr(removed, C.c_uint8)
+    return d
+
+
+def generate_onsite(N, L, t=-2.7, W=0.0, seed=0, edge_p=0.0, edge_seed=0):
+    """Host-only: the (eps, removed) arrays [L, 2N] a seeded ribbon description yields."""
+    eps = np.empty((L, 2 * N), dtype=np.float64)
+    rem = np.empty((L, 2 * N), dtype=np.uint8)
+    d = _desc(N, L, t, None, W, seed, edge_p, edge_seed, None)
+    _check(lib.rgf_generate_onsite(C.byref(d), _ptr(eps, C.c_double), _ptr(rem, C.c_uint8)))
+    return eps, rem
+
+
+class Ribbon:
+    """A ribbon instance resident on the current CUDA device (rgf_build_ribbon)."""
+
+    def __init__(self, N, L, t=-2.7, onsite=None, W=0.0, seed=0, edge_p=0.0, edge_seed=0,
+                 removed=None):
+        self.N, self.L, self.t = int(N), int(L), float(t)
+        on = None if onsite is None else np.ascontiguousarray(onsite, dtype=np.float64).reshape(-1)
+        rm = None if removed is None else np.ascontiguousarray(removed, dtype=np.uint8).reshape(-1)
+        if on is not None and on.size != self.L * 2 * self.N:
+            raise ValueError("onsite must have L*2N entries")
+        if rm is not None and rm.size != self.L * 2 * self.N:
+            raise ValueError("removed must have L*2N entries")
+        d = _desc(N, L, t, on, W, seed, edge_p, edge_seed, rm)
+        h = _vp()
+        _check(lib.rgf_build_ribbon(C.byref(d), C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_device(cls, N, L, t, onsite_ptr, removed_ptr=None, stream=0):
+        """Build from device buffers (e.g. torch CUDA tensors' data_ptr())."""
+        self = cls.__new__(cls)
+        self.N, self.L, self.t = int(N), int(L), float(t)
+        h = _vp()
+        _check(lib.rgf_build_ribbon_dev(self.N, self.L, self.t, _vp(onsite_ptr),
+                                        _vp(removed_ptr) if removed_ptr else None,
+                                        _vp(stream), C.byref(h)))
+        self._h = h
+        return self
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.rgf_free_ribbon(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _handles(ribbons):
+    arr = (_vp * len(ribbons))()
+    for i, r in enumerate(ribbons):
+        arr[i] = r.handle
+    return arr
+
+
+def lead_selfenergy(N, E, eta=1e-8, side=0, t=-2.7, check=True):
+    """Full-cell (2N x 2N) lead self-energies, one per energy: returns (sigma[nE,2N,2N], iters)."""
+    E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+    M = 2 * N
+    out = np.empty((E.size, M, M, 2), dtype=np.float64)
+    it = np.empty(E.size, dtype=np.int32)
+    st = lib.rgf_lead_selfenergy(int(N), float(t), _ptr(E, C.c_double), E.size, float(eta),
+                                 int(side), _ptr(out, C.c_double), it.ctypes.data_as(_ip))
+    if check:
+        _check(st)
+    sig = out[..., 0] + 1j * out[..., 1]
+    return sig, it
+
+
+def conductance(ribbons, E, eta_device=1e-8, eta_lead=1e-8, precision=RGF_FP64, check=True):
+    """T for chains (ribbons[c], E[c]); host buffers.  Returns (T, status)."""
+    E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+    if len(ribbons) != E.size:
+        raise ValueError("one ribbon per energy")
+    T = np.empty(E.size)
+    st = np.empty(E.size, dtype=np.int32)
+    r = lib.rgf_conductance(_handles(ribbons), _ptr(E, C.c_double), E.size, float(eta_device),
+                            float(eta_lead), int(precision), _ptr(T, C.c_double),
+                            st.ctypes.data_as(_i32p))
+    if check:
+        _check(r)
+    return T, st
+
+
+def conductance_dev(ribbons, E_ptr, n, T_ptr, status_ptr=0, eta_device=1e-8, eta_lead=1e-8,
+                    precision=RGF_FP64, stream=0):
+    """Device-buffer variant: pointers to n float64 energies / outputs on the device."""
+    _check(lib.rgf_conductance_dev(_handles(ribbons), _vp(E_ptr), int(n), float(eta_device),
+                                   float(eta_lead), int(precision), _vp(stream), _vp(T_ptr),
+                                   _vp(status_ptr) if status_ptr else None))
+
+
+def conductance_grad(ribbons, E, eta_device=1e-8, eta_lead=1e-8, precision=RGF_FP64,
+                     ckpt_stride=0, check=True):
+    """T and dT/d eps [nchains, L, 2N] (host buffers).  Returns (T, grad, status)."""
+    E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+    if len(ribbons) != E.size:
+        raise ValueError("one ribbon per energy")
+    sizes = [r.L * 2 * r.N for r in ribbons]
+    if len(set(sizes)) > 1:
+        raise ValueError("conductance_grad binding expects ribbons of one size")
+    T = np.empty(E.size)
+    g = np.empty((E.size, ribbons[0].L, 2 * ribbons[0].N)) if ribbons else np.empty(0)
+    st = np.empty(E.size, dtype=np.int32)
+    r = lib.rgf_conductance_grad(_handles(ribbons), _ptr(E, C.c_double), E.size,
+                                 float(eta_device), float(eta_lead), int(precision),
+                                 int(ckpt_stride), _ptr(T, C.c_double), _ptr(g, C.c_double),
+                                 st.ctypes.data_as(_i32p))
+    if check:
+        _check(r)
+    return T, g, st

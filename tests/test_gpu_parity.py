@@ -1,0 +1,144 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import bands, leads as oleads, rgf as orgf
+
+pytestmark = pytest.mark.gpu
+T_HOP = -2.7
+
+
+def _oracle_T(N, L, E, etad, etal, eps, rem):
+    try:
+        return orgf.transmission(N, L, E, etad, etal, T_HOP, eps, rem)
+    except oleads.NoConvergence:
+        return None
+
+
+@pytest.mark.parametrize("N", [2, 5, 11, 12, 24])
+def test_lead_selfenergy_matches_oracle(rgflib, N):
+    E = np.array([-1.3, -0.2, 0.003, 0.4, 1.7, 3.1])
+    for side in (0, 1):
+        sig, it = rgflib.lead_selfenergy(N, E, 1e-8, side)
+        for i, e in enumerate(E):
+            sL, sR, iL, iR = oleads.self_energies(N, e, 1e-8, T_HOP, return_iters=True)
+            ref = sL if side == 0 else sR
+            err = np.abs(sig[i] - ref).max() / max(1.0, np.abs(ref).max())
+            assert err < 1e-10, (N, e, side, err)
+            assert abs(int(it[i]) - (iL if side == 0 else iR)) <= 1
+
+
+def test_lead_reports_noconv_at_exact_charge_neutrality(rgflib):
+    with pytest.raises(oleads.NoConvergence):
+        oleads.self_energies(23, 0.0, 1e-8, T_HOP)
+    sig, it = rgflib.lead_selfenergy(23, np.array([0.0, 0.2]), 1e-8, 1, check=False)
+    assert it[0] == -1 and np.isnan(sig[0]).all()
+    assert it[1] > 0 and np.isfinite(sig[1]).all()
+
+
+def _run(rgflib, N, L, Es, eps, rem, prec, etad=1e-8, etal=1e-8):
+    rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps, removed=rem)
+    T, st = rgflib.conductance([rib] * len(Es), Es, etad, etal, prec, check=False)
+    return T, st
+
+
+def test_pristine_n11_energy_grid_fp64(rgflib):
+    # 201 energies in [-1, 1] eV, N = 11, L = 50, eta = 1e-8 eV.
+    w = workloads.WORKLOADS["agnr11_L50_pristine"]
+    N, L = w["N"], w["L"]
+    Es = w["energies"]()
+    T, st = _run(rgflib, N, L, Es, None, None, rgflib.RGF_FP64)
+    assert (st == 0).all()
+    for e, t in zip(Es, T):
+        ref = _oracle_T(N, L, e, 1e-8, 1e-8, None, None)
+        tol = 5e-3 if e == 0.0 else 1e-9      # E = 0 exactly is condition-limited
+        assert abs(t - ref) < tol, (e, t, ref)
+    # quantisation: T ~ n_ch up to the eta absorption of the device
+    nz = Es != 0
+    assert np.all(np.abs(T[nz] - 1.0) < 1e-5)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N,L,W,p", [(2, 5, 0.3, 0.0), (3, 4, 0.2, 0.0), (5, 1, 0.25, 0.3),
+                                     (11, 3, 0.25, 0.3), (12, 17, 0.4, 0.25), (23, 9, 0.25, 0.2),
+                                     (64, 6, 0.1, 0.05), (150, 3, 0.25, 0.05)])
+def test_disordered_rough_ribbons(rgflib, N, L, W, p, prec):
+    eps = workloads.anderson_onsite(N, L, W, 100 + N)
+    rem = workloads.edge_removed(N, L, p, 200 + N)
+    Es = np.array([-1.1, -0.3, -5e-3, 1e-3, 0.02, 0.45, 2.2])
+    T, st = _run(rgflib, N, L, Es, eps, rem, prec)
+    tol = 1e-9 if prec == 0 else 1e-7
+    for e, t, s in zip(Es, T, st):
+        ref = _oracle_T(N, L, e, 1e-8, 1e-8, eps, rem)
+        assert s == 0
+        assert abs(t - ref) < tol * max(1.0, abs(ref)), (N, L, e, t, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pristine_quantised_without_device_absorption(rgflib, prec):
+    for N in (5, 12, 17):
+        Es = np.array([0.15, -0.6, 1.4, -2.3])
+        T, st = _run(rgflib, N, 12, Es, None, None, prec, etad=0.0)
+        for e, t in zip(Es, T):
+            assert abs(t - bands.channels_closed_form(N, e)) < 1e-9
+
+
+def test_batched_uneven_chains_one_call(rgflib):
+    rng = np.random.default_rng(5)
+    ribs, Es, refs = [], [], []
+    for c in range(24):
+        N = int(rng.integers(4, 70))
+        L = int(rng.integers(1, 25))
+        eps = workloads.anderson_onsite(N, L, 0.1, 1000 + c)
+        rem = workloads.edge_removed(N, L, 0.05, 2000 + c)
+        E = float(rng.uniform(-1, 1))
+        ribs.append(rgflib.Ribbon(N, L, T_HOP, onsite=eps, removed=rem))
+        Es.append(E)
+        refs.append(_oracle_T(N, L, E, 1e-8, 1e-8, eps, rem))
+    for prec, tol in ((0, 1e-9), (1, 1e-7)):
+        T, st = rgflib.conductance(ribs, np.array(Es), 1e-8, 1e-8, prec)
+        assert (st == 0).all()
+        assert np.max(np.abs(T - np.array(refs))) < tol
+
+
+def test_failed_chain_does_not_spoil_the_batch(rgflib):
+    rib = rgflib.Ribbon(23, 4, T_HOP, W=0.1, seed=3)
+    T, st = rgflib.conductance([rib, rib, rib], np.array([0.3, 0.0, -0.4]), check=False)
+    assert st[1] == rgflib.RGF_ENOCONV and np.isnan(T[1])
+    assert st[0] == 0 and st[2] == 0
+    eps, _ = rgflib.generate_onsite(23, 4, T_HOP, 0.1, 3)
+    assert abs(T[0] - _oracle_T(23, 4, 0.3, 1e-8, 1e-8, eps, None)) < 1e-9
+    with pytest.raises(rgflib.RGFError) as e:
+        rgflib.conductance([rib], np.array([0.0]))
+    assert e.value.status == rgflib.RGF_ENOCONV
+
+
+def test_device_buffer_variant_on_a_stream(rgflib):
+    import torch
+    rib = rgflib.Ribbon(11, 8, T_HOP, W=0.2, seed=9)
+    Es = np.array([-0.4, 0.1, 0.33])
+    Th, _ = rgflib.conductance([rib] * 3, Es)
+    s = torch.cuda.Stream()
+    Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
+    Td = torch.empty(3, dtype=torch.float64, device="cuda")
+    Sd = torch.empty(3, dtype=torch.int32, device="cuda")
+    s.wait_stream(torch.cuda.current_stream())
+    rgflib.conductance_dev([rib] * 3, Ed.data_ptr(), 3, Td.data_ptr(), Sd.data_ptr(),
+                           stream=s.cuda_stream)
+    s.synchronize()
+    assert np.array_equal(Td.cpu().numpy(), Th)
+    assert (Sd.cpu().numpy() == 0).all()
+
+
+def test_invalid_arguments_are_rejected(rgflib):
+    with pytest.raises(rgflib.RGFError) as e:
+        rgflib.Ribbon(1, 5)
+    assert e.value.status == rgflib.RGF_EINVAL
+    rib = rgflib.Ribbon(5, 2)
+    with pytest.raises(rgflib.RGFError):
+        rgflib.conductance([rib], np.array([np.nan]))
+    with pytest.raises(rgflib.RGFError):
+        rgflib.conductance([rib], np.array([0.1]), precision=7)
+    with pytest.raises(rgflib.RGFError):
+        rgflib.conductance([rib], np.array([0.1]), eta_lead=0.0)
