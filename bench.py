@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched RGF conductance path on one GB300 (or N).
+
+Workload (default): the W = 30 nm armchair ribbon, N = 245 dimer lines
+(M = 490 orbitals per unit cell), L = 4000 cells (1.7 um), Anderson disorder
+U[-0.25, 0.25] eV (seed 1), 69 energies: 64 uniform in [-0.5, 0.5] eV plus
+E in {0, +-1 meV, +-5 meV}; eta = 1e-8 eV in device and leads.  One step is one
+rgf_conductance call over all 69 chains: lead decimation, the slice recursion
+and the trace.  The unit is one unit-cell slice step of one chain
+(slice-inversions/s, M = 490); chains that report an error status do no sweep
+work and are not counted.
+
+Arms:
+  default           mixed precision (double-float) path, device-resident inputs;
+                    also the FP64 path once on the same ribbon for |dT|.
+  --impl reference  the CPU oracle on a bounded sample of the same workload.
+Under torchrun each rank runs its own disorder realisation (seed + rank): the
+chains shard with no collective on the data path ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import workloads  # noqa: E402
+
+METRIC = "RGF slice-inversions/s (M=490, batched energies)"
+UNIT = "slice-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="agnr245_L4000_anderson")
+    ap.add_argument("--cells", type=int, default=0, help="override L (profiling runs)")
+    ap.add_argument("--energies", type=int, default=0, help="use only the first n energies")
+    ap.add_argument("--no-check", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-cells", type=int, default=60)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def flops_per_cell(N: int) -> float:
+    """Algorithmic real flops of one unit-cell step in the column slicing.
+
+    Per column of K orbitals: the inverse (K^3 complex multiply-adds) and the
+    corner-strip product (KL x K x K); 8 real flops per complex multiply-add.
+    """
+    KL, KR = (N + 1) // 2, N // 2
+    f = 0.0
+    for K in (KL, KL, KR, KR):
+        f += 8.0 * K ** 3 + 8.0 * KL * K * K
+    return f
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.idx)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in Path(self.f.name).read_text().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 5 + i and "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            return json.loads(p.read_text()), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload_arrays(args, rank):
+    w = workloads.WORKLOADS[args.workload]
+    N, L = w["N"], (args.cells or w["L"])
+    seed = w["seed"] + rank
+    eps = workloads.anderson_onsite(N, L, w["W"], seed)
+    rem = workloads.edge_removed(N, L, w["edge_p"], w["edge_seed"] + rank) if w["edge_p"] > 0 else None
+    Es = w["energies"]()
+    if args.energies:
+        Es = Es[: args.energies]
+    return w, N, L, eps, rem, Es, seed
+
+
+def cpu_oracle_sample(N, L_s, E, W, seed, rem_p=0.0, edge_seed=0):
+    """Times the CPU oracle (as it stands) on one energy x L_s cells."""
+    from oracle import rgf as orgf
+    eps = workloads.anderson_onsite(N, L_s, W, seed)
+    rem = workloads.edge_removed(N, L_s, rem_p, edge_seed) if rem_p > 0 else None
+    t0 = time.perf_counter()
+    orgf.transmission(N, L_s, E, 1e-8, 1e-8, -2.7, eps, rem)
+    return time.perf_counter() - t0
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workloads.WORKLOADS[args.workload]
+    N = w["N"]
+    L_s = args.cpu_cells
+    E = 0.3
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt = cpu_oracle_sample(N, L_s, E, w["W"], w["seed"])
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    value = args.steps * L_s / t
+    cores = blas_threads()
+    sample = f"1 energy (E=0.3 eV) x {L_s} cells of N={N}, whole path (decimation + recursion + trace)"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": args.workload, "N": N, "L": w["L"], "sample_cells": L_s},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1107_5300_gb300 import rgf
+
+    prec = rgf.RGF_MIXED if args.precision == "mixed" else rgf.RGF_FP64
+    w, N, L, eps, rem, Es, seed = workload_arrays(args, rank)
+    n = Es.size
+    stream = torch.cuda.Stream()
+    rib = rgf.Ribbon(N, L, -2.7, onsite=eps, removed=rem)
+    ribs = [rib] * n
+    Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
+    Td = torch.empty(n, dtype=torch.float64, device="cuda")
+    Sd = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        rgf.conductance_dev(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8,
+                            prec, stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+    rgf.profile_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    peaks, peaks_src = measured_peaks()
+    ms_steps, ms_sweep, ms_lead = [], [], []
+    sampler = ClockSampler(local)
+    with sampler:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)          # evict L2 (129 MB) between timed steps
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+            e1.synchronize()
+            ms_steps.append(e0.elapsed_time(e1))
+            a, b = rgf.profile_read()
+            ms_lead.append(a)
+            ms_sweep.append(b)
+    torch.cuda.synchronize()
+    rgf.profile_enable(False)
+    if dist:
+        dist.barrier()
+    status = Sd.cpu().numpy()
+    T = Td.cpu().numpy()
+    ok = status == 0
+    units_local = float(ok.sum()) * L
+    t_local = sum(ms_steps) / 1e3
+    if dist:
+        tt = torch.tensor([t_local, units_local], dtype=torch.float64, device="cuda")
+        tmax = tt.clone(); dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        usum = tt.clone(); dist.all_reduce(usum[1:], op=dist.ReduceOp.SUM)
+        t_job, units = float(tmax[0]), float(usum[1])
+    else:
+        t_job, units = t_local, units_local
+    value = units * args.steps / t_job
+
+    # Parity of this arm against the FP64 GPU path on the same ribbon (untimed).
+    parity = None
+    if not args.no_check and prec == rgf.RGF_MIXED:
+        T64, s64 = rgf.conductance(ribs, Es, 1e-8, 1e-8, rgf.RGF_FP64, check=False)
+        both = ok & (s64 == 0)
+        d = np.abs(T - T64)
+        low = both & (np.abs(Es) <= 5e-3)
+        parity = {"max_abs_dT_vs_fp64": float(d[both].max()) if both.any() else None,
+                  "max_abs_dT_low_energy": float(d[low].max()) if low.any() else None,
+                  "chains_compared": int(both.sum()),
+                  "status_mismatch": int((status != s64).sum()),
+                  "tolerance": 1e-6}
+
+    # End to end through the host-buffer ABI: ribbon upload + energies in, T out.
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = min(args.steps, 2)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            r2 = rgf.Ribbon(N, L, -2.7, onsite=eps, removed=rem)
+            Th, sh = rgf.conductance([r2] * n, Es, 1e-8, 1e-8, prec, check=False)
+            r2.close()
+        te = time.perf_counter() - t0
+        h2d = eps.nbytes + (rem.nbytes if rem is not None else 0) + Es.nbytes
+        d2h = Th.nbytes + sh.nbytes
+        e2e = {"value": float((sh == 0).sum()) * L * e2e_steps / te * (world if dist else 1),
+               "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # Roofline of the dominant kernel (the slice sweep).
+    fl = flops_per_cell(N) * float(ok.sum()) * L
+    sweep_s = statistics.mean(ms_sweep) / 1e3
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    if prec == rgf.RGF_MIXED:
+        # double-float arithmetic on the FP32 pipes: 54 FP32 instructions per
+        # complex multiply-add (8 algorithmic flops); 152 SMs x 128 lanes.
+        peak = 152 * 128 * smax * 1e6 * 8.0 / 54.0 / 1e12
+        bound = "alu"
+    else:
+        peak = 1.25    # FP64 pipe, nominal TFLOP/s
+        bound = "alu"
+    achieved = fl / sweep_s / 1e12
+    traffic_file = ROOT / "profiles" / "traffic.json"
+    traffic = None
+    if traffic_file.exists():
+        try:
+            traffic = json.loads(traffic_file.read_text()).get(f"sweep_{args.precision}_{args.workload}")
+        except Exception:
+            traffic = None
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": f"sweep_kernel<{'df32' if prec else 'double'}>",
+            "peak_source": f"derived from unit counts and sm_max_mhz={smax:.0f} ({peaks_src})",
+            "ms_sweep": statistics.mean(ms_sweep), "ms_lead": statistics.mean(ms_lead)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        L_s = args.cpu_cells
+        dt = cpu_oracle_sample(N, L_s, 0.3, w["W"], seed)
+        cpu = {"value": L_s / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"1 energy (E=0.3 eV) x {L_s} cells of N={N}, whole path"}
+
+    clocks = sampler.summary()
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32x2" if prec == rgf.RGF_MIXED else "f64", "data": "synthetic",
+               "config": {"workload": args.workload, "N": N, "M": 2 * N, "L": L, "energies": int(n),
+                          "chains_ok": int(ok.sum()), "W_eV": w["W"], "eta_eV": 1e-8,
+                          "precision": args.precision, "l2": "flushed (256 MB write) between steps",
+                          "parallelism": f"chains x{world} (one disorder realisation per rank)"},
+               "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                          "reasons": clocks["reasons"]},
+               "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roof,
+               "cpu_baseline": cpu, "parity": parity,
+               "status_counts": {rgf.STATUS_NAMES[s]: int((status == s).sum()) for s in set(status.tolist())}}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -33,7 +33,7 @@
  *     global memory of the current device.
  *   - On a failing call, host outputs are left untouched where the error is
  *     caught before launch (RGF_EINVAL, RGF_ENOMEM); per-chain numeric failures
- *     (RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE, RGF_ETIMEOUT) are reported
+ *     (RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE, RGF_ETIMEOUT, RGF_EBOUNDS) are reported
  *     per chain in chain_status, that chain's T is NaN, and the other chains'
  *     results are valid.
  */
@@ -52,9 +52,12 @@ typedef enum {
     RGF_ENOMEM = 2,      /* device or host allocation failed                          */
     RGF_ECUDA = 3,       /* a CUDA runtime call failed                                */
     RGF_ENOCONV = 4,     /* lead decimation hit its iteration cap or went non-finite   */
-    RGF_ESINGULAR = 5,   /* a zero pivot in a slice inverse                           */
+    RGF_ESINGULAR = 5,   /* a zero pivot, or a pivot below 64 u max|A| (u the unit
+                            roundoff of the working precision), in a slice inverse     */
     RGF_ENONFINITE = 6,  /* NaN or Inf in a slice Green's function or in T            */
-    RGF_ETIMEOUT = 7     /* a device-side wait exceeded its spin limit                */
+    RGF_ETIMEOUT = 7,    /* a device-side wait exceeded its spin limit                */
+    RGF_EBOUNDS = 8      /* T outside [0, n_ch(E)] (n_ch from the armchair band edges):
+                            the sweep lost its accuracy at the working precision      */
 } rgf_status;
 
 typedef enum {
@@ -159,6 +162,18 @@ rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, i
                                 double eta_device, double eta_lead, int precision,
                                 int ckpt_stride, double* T, double* dT_deps,
                                 int32_t* chain_status);
+
+/*
+ * Diagnostics (no counterpart in the paper).  When enabled, every
+ * rgf_conductance* call records CUDA events on its stream around its two
+ * kernel phases: lead decimation and slice sweep (with the trace).
+ * rgf_profile_read waits for the last call's events and returns the phase
+ * durations in milliseconds (either pointer may be NULL).  Process-wide
+ * state: not for concurrent calls from several threads.  Errors: RGF_ECUDA,
+ * RGF_EINVAL if profiling is off or no call was recorded.
+ */
+rgf_status rgf_profile_enable(int on);
+rgf_status rgf_profile_read(double* ms_lead, double* ms_sweep);
 
 const char* rgf_status_str(int status);
 const char* rgf_last_error(void);

@@ -42,6 +42,21 @@ def _surface(H00, a0, b0, z, tol):
     raise RuntimeError("mp decimation did not converge")
 
 
+def self_energies(N, E, eta, t=-2.7, dps=40):
+    """Full-cell Sigma_L, Sigma_R (as complex128 arrays) from the decimation in dps digits."""
+    with mpm.workdps(dps):
+        tol = mpm.mpf(10) ** (-(dps - 5))
+        H00n, H01n = blocks(N, t)
+        H00, H01 = _m(H00n), _m(H01n)
+        z = mpm.mpf(E) + 1j * mpm.mpf(eta)
+        gR = _surface(H00, H01, H01.T, z, tol)
+        gL = _surface(H00, H01.T, H01, z, tol)
+        sR = H01 * gR * H01.T
+        sL = H01.T * gL * H01
+        conv = lambda m: np.array([[complex(m[i, j]) for j in range(m.cols)] for i in range(m.rows)])
+        return conv(sL), conv(sR)
+
+
 def transmission(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, dps=40):
     with mpm.workdps(dps):
         tol = mpm.mpf(10) ** (-(dps - 5))

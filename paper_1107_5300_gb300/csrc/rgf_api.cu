@@ -36,6 +36,21 @@ namespace {
 
 thread_local std::string g_last_error;
 
+struct Profile {
+    bool on = false, recorded = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+Profile g_prof;
+
+cudaError_t prof_record(int i, cudaStream_t st) {
+    if (!g_prof.on) return cudaSuccess;
+    if (!g_prof.ev[i]) {
+        cudaError_t e = cudaEventCreate(&g_prof.ev[i]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaEventRecord(g_prof.ev[i], st);
+}
+
 rgf_status fail(rgf_status st, const std::string& msg) {
     g_last_error = msg;
     return st;
@@ -90,15 +105,20 @@ struct Plan {
     std::vector<rgf::ChainDev> chains;
     std::vector<rgf::LeadDev> leads;
     std::vector<int> order;
-    size_t ws_elems = 0, lead_ws_elems = 0, lead_out_elems = 0;
+    std::vector<int> seg_cols;
+    size_t ws_elems = 0, lead_ws_elems = 0, lead_out_elems = 0, grad_elems = 0;
     int Kmax = 1;
 };
 
-rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl) {
+// grad: size the adjoint workspace with checkpoints every ckpt_stride cells
+// (<= 0: ceil(sqrt(L))).
+rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl, bool grad = false,
+                     int ckpt_stride = 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     pl.chains.resize(nchains);
     pl.leads.resize(nchains);
+    pl.seg_cols.resize(nchains);
     std::vector<double> cost(nchains);
     for (int c = 0; c < nchains; ++c) {
         const rgf_ribbon* r = rib[c];
@@ -113,7 +133,17 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl) {
         ch.E = 0.0;   // filled on the device from the energy array
         ch.lead = c;
         ch.ws_off = pl.ws_elems;
-        pl.ws_elems += rgf::sweep_ws_elems(r->N);
+        ch.grad_off = pl.grad_elems;
+        if (grad) {
+            int stride = ckpt_stride > 0 ? std::min(ckpt_stride, r->L)
+                                         : std::max(1, (int)std::ceil(std::sqrt((double)r->L)));
+            pl.seg_cols[c] = 4 * stride;
+            pl.ws_elems += rgf::grad_ws_elems(r->N, r->L, pl.seg_cols[c]);
+            pl.grad_elems += (size_t)r->L * 2 * r->N;
+        } else {
+            pl.seg_cols[c] = 0;
+            pl.ws_elems += rgf::sweep_ws_elems(r->N);
+        }
         rgf::LeadDev& ld = pl.leads[c];
         ld.N = r->N;
         ld.t = r->t;
@@ -144,10 +174,13 @@ __global__ void fill_energy(rgf::ChainDev* chains, rgf::LeadDev* leads, const do
     }
 }
 
-// Runs the whole forward path on `st`.  E_dev, T_dev, status_dev: device.
-rgf_status run_conductance(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
-                           double eta_device, double eta_lead, int precision, cudaStream_t st,
-                           double* T_dev, int32_t* status_dev) {
+// Runs the whole path on `st`: lead decimation, then the forward sweep (or,
+// with dT_dev, the checkpointed adjoint sweep).  E_dev, T_dev, status_dev,
+// dT_dev: device.
+rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
+                    double eta_device, double eta_lead, int precision, cudaStream_t st,
+                    double* T_dev, int32_t* status_dev, double* dT_dev = nullptr,
+                    int ckpt_stride = 0) {
     if (nchains < 0) return fail(RGF_EINVAL, "nchains < 0");
     if (nchains == 0) return RGF_OK;
     if (!rib || !E_dev || !T_dev) return fail(RGF_EINVAL, "NULL argument");
@@ -155,21 +188,25 @@ rgf_status run_conductance(const rgf_ribbon* const* rib, const double* E_dev, in
     if (!(eta_device >= 0.0) || !(eta_lead > 0.0) || !std::isfinite(eta_device) ||
         !std::isfinite(eta_lead))
         return fail(RGF_EINVAL, "eta_device must be >= 0 and eta_lead > 0 (finite)");
+    const bool grad = dT_dev != nullptr;
     Plan pl;
-    rgf_status s = make_plan(rib, nchains, pl);
+    rgf_status s = make_plan(rib, nchains, pl, grad, ckpt_stride);
     if (s != RGF_OK) return s;
 
     const size_t nC = pl.chains.size() * sizeof(rgf::ChainDev);
     const size_t nL = pl.leads.size() * sizeof(rgf::LeadDev);
     const size_t nO = pl.order.size() * sizeof(int);
-    std::vector<unsigned char> hdr(nC + nL + nO);
+    std::vector<unsigned char> hdr(nC + nL + 2 * nO);
     std::memcpy(hdr.data(), pl.chains.data(), nC);
     std::memcpy(hdr.data() + nC, pl.leads.data(), nL);
     std::memcpy(hdr.data() + nC + nL, pl.order.data(), nO);
+    std::memcpy(hdr.data() + nC + nL + nO, pl.seg_cols.data(), nO);
 
     DevBuf dhdr, dws, dlws, dlout, dlst, dbad;
     RGF_CUDA(dhdr.alloc(hdr.size(), st), "cudaMallocAsync(descriptors)");
-    RGF_CUDA(dws.alloc(pl.ws_elems * 16, st), "cudaMallocAsync(sweep workspace)");
+    cudaError_t ae = dws.alloc(pl.ws_elems * 16, st);
+    if (ae == cudaErrorMemoryAllocation) return fail(RGF_ENOMEM, "workspace allocation failed");
+    RGF_CUDA(ae, "cudaMallocAsync(workspace)");
     RGF_CUDA(dlws.alloc(pl.lead_ws_elems * 16, st), "cudaMallocAsync(lead workspace)");
     RGF_CUDA(dlout.alloc(pl.lead_out_elems * 16, st), "cudaMallocAsync(lead output)");
     RGF_CUDA(dlst.alloc(2 * sizeof(int) * nchains, st), "cudaMallocAsync(lead status)");
@@ -177,18 +214,73 @@ rgf_status run_conductance(const rgf_ribbon* const* rib, const double* E_dev, in
     RGF_CUDA(cudaMemcpyAsync(dhdr.p, hdr.data(), hdr.size(), cudaMemcpyHostToDevice, st),
              "cudaMemcpyAsync(descriptors)");
     RGF_CUDA(cudaMemsetAsync(dbad.p, 0, sizeof(int), st), "cudaMemsetAsync");
+    if (grad) RGF_CUDA(cudaMemsetAsync(dT_dev, 0, pl.grad_elems * sizeof(double), st), "cudaMemsetAsync");
     auto* dchains = (rgf::ChainDev*)dhdr.p;
     auto* dleads = (rgf::LeadDev*)((unsigned char*)dhdr.p + nC);
     auto* dorder = (int*)((unsigned char*)dhdr.p + nC + nL);
+    auto* dseg = (int*)((unsigned char*)dhdr.p + nC + nL + nO);
     fill_energy<<<(nchains + 255) / 256, 256, 0, st>>>(dchains, dleads, E_dev, nchains,
                                                        (int*)dbad.p);
     RGF_CUDA(cudaGetLastError(), "fill_energy launch");
+    RGF_CUDA(prof_record(0, st), "cudaEventRecord");
     RGF_CUDA(rgf::launch_lead(dleads, nchains, pl.Kmax, eta_lead, dlws.p, dlout.p, (int*)dlst.p,
                               nullptr, st),
              "lead decimation launch");
-    RGF_CUDA(rgf::launch_sweep(precision, dchains, dorder, nchains, pl.Kmax, eta_device, dlout.p,
-                               (int*)dlst.p, dleads, dws.p, T_dev, status_dev, st),
-             "sweep launch");
+    RGF_CUDA(prof_record(1, st), "cudaEventRecord");
+    if (grad) {
+        RGF_CUDA(rgf::launch_grad(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
+                                  dlout.p, (int*)dlst.p, dleads, dws.p, dseg, T_dev, dT_dev,
+                                  status_dev, st),
+                 "adjoint sweep launch");
+    } else {
+        RGF_CUDA(rgf::launch_sweep(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
+                                   dlout.p, (int*)dlst.p, dleads, dws.p, T_dev, status_dev, st),
+                 "sweep launch");
+    }
+    RGF_CUDA(prof_record(2, st), "cudaEventRecord");
+    if (g_prof.on) g_prof.recorded = true;
+    return RGF_OK;
+}
+
+// Host-buffer front end of run_path: copies E in and T (and dT) out on the
+// legacy default stream, synchronises, returns the first per-chain failure.
+rgf_status run_host(const rgf_ribbon* const* rib, const double* E, int nchains, double eta_device,
+                    double eta_lead, int precision, double* T, int32_t* chain_status,
+                    double* dT = nullptr, int ckpt_stride = 0) {
+    if (nchains < 0 || (nchains > 0 && (!rib || !E || !T)))
+        return fail(RGF_EINVAL, "NULL argument or nchains < 0");
+    if (nchains == 0) return RGF_OK;
+    for (int i = 0; i < nchains; ++i) {
+        if (!std::isfinite(E[i])) return fail(RGF_EINVAL, "non-finite energy");
+        if (!rib[i]) return fail(RGF_EINVAL, "NULL ribbon");
+    }
+    size_t ng = 0;
+    if (dT)
+        for (int i = 0; i < nchains; ++i) ng += (size_t)rib[i]->L * 2 * rib[i]->N;
+    cudaStream_t st = 0;
+    std::vector<double> hT(nchains);
+    std::vector<int32_t> hs(nchains);
+    {
+        DevBuf dE, dTt, dS, dG;
+        RGF_CUDA(dE.alloc(nchains * sizeof(double), st), "cudaMallocAsync");
+        RGF_CUDA(dTt.alloc(nchains * sizeof(double), st), "cudaMallocAsync");
+        RGF_CUDA(dS.alloc(nchains * sizeof(int32_t), st), "cudaMallocAsync");
+        if (dT) RGF_CUDA(dG.alloc(ng * sizeof(double), st), "cudaMallocAsync");
+        RGF_CUDA(cudaMemcpyAsync(dE.p, E, nchains * sizeof(double), cudaMemcpyHostToDevice, st), "H2D");
+        rgf_status s = run_path(rib, (const double*)dE.p, nchains, eta_device, eta_lead, precision,
+                                st, (double*)dTt.p, (int32_t*)dS.p, (double*)dG.p, ckpt_stride);
+        if (s != RGF_OK) return s;
+        RGF_CUDA(cudaMemcpyAsync(hT.data(), dTt.p, nchains * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
+        RGF_CUDA(cudaMemcpyAsync(hs.data(), dS.p, nchains * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "D2H");
+        if (dT) RGF_CUDA(cudaMemcpyAsync(dT, dG.p, ng * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
+    }
+    RGF_CUDA(cudaStreamSynchronize(st), "rgf_conductance");
+    std::memcpy(T, hT.data(), nchains * sizeof(double));
+    if (chain_status) std::memcpy(chain_status, hs.data(), nchains * sizeof(int32_t));
+    for (int i = 0; i < nchains; ++i)
+        if (hs[i] != RGF_OK)
+            return fail((rgf_status)hs[i], std::string("chain ") + std::to_string(i) + ": " +
+                                               rgf_status_str(hs[i]));
     return RGF_OK;
 }
 
@@ -205,6 +297,23 @@ extern "C" {
 
 const char* rgf_version(void) { return "rgf-gb300 0.1"; }
 
+rgf_status rgf_profile_enable(int on) {
+    g_prof.on = on != 0;
+    g_prof.recorded = false;
+    return RGF_OK;
+}
+
+rgf_status rgf_profile_read(double* ms_lead, double* ms_sweep) {
+    if (!g_prof.on || !g_prof.recorded) return fail(RGF_EINVAL, "no profiled call recorded");
+    RGF_CUDA(cudaEventSynchronize(g_prof.ev[2]), "cudaEventSynchronize");
+    float a = 0.f, b = 0.f;
+    RGF_CUDA(cudaEventElapsedTime(&a, g_prof.ev[0], g_prof.ev[1]), "cudaEventElapsedTime");
+    RGF_CUDA(cudaEventElapsedTime(&b, g_prof.ev[1], g_prof.ev[2]), "cudaEventElapsedTime");
+    if (ms_lead) *ms_lead = a;
+    if (ms_sweep) *ms_sweep = b;
+    return RGF_OK;
+}
+
 const char* rgf_last_error(void) { return g_last_error.c_str(); }
 
 const char* rgf_status_str(int s) {
@@ -217,6 +326,7 @@ const char* rgf_status_str(int s) {
         case RGF_ESINGULAR: return "RGF_ESINGULAR: zero pivot in a slice inverse";
         case RGF_ENONFINITE: return "RGF_ENONFINITE: non-finite value";
         case RGF_ETIMEOUT: return "RGF_ETIMEOUT: device wait timed out";
+        case RGF_EBOUNDS: return "RGF_EBOUNDS: T outside [0, n_ch]; accuracy lost at this precision";
         default: return "unknown rgf_status";
     }
 }
@@ -389,51 +499,23 @@ rgf_status rgf_lead_selfenergy(int N, double t, const double* E, int nE, double 
 rgf_status rgf_conductance_dev(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
                                double eta_device, double eta_lead, int precision, void* stream,
                                double* T_dev, int32_t* status_dev) {
-    return run_conductance(rib, E_dev, nchains, eta_device, eta_lead, precision,
-                           (cudaStream_t)stream, T_dev, status_dev);
+    return run_path(rib, E_dev, nchains, eta_device, eta_lead, precision, (cudaStream_t)stream,
+                    T_dev, status_dev);
 }
 
 rgf_status rgf_conductance(const rgf_ribbon* const* rib, const double* E, int nchains,
                            double eta_device, double eta_lead, int precision, double* T,
                            int32_t* chain_status) {
-    if (nchains < 0 || (nchains > 0 && (!rib || !E || !T)))
-        return fail(RGF_EINVAL, "NULL argument or nchains < 0");
-    if (nchains == 0) return RGF_OK;
-    for (int i = 0; i < nchains; ++i)
-        if (!std::isfinite(E[i])) return fail(RGF_EINVAL, "non-finite energy");
-    cudaStream_t st = 0;
-    rgf_status s;
-    std::vector<double> hT(nchains);
-    std::vector<int32_t> hs(nchains);
-    {
-        DevBuf dE, dT, dS;
-        RGF_CUDA(dE.alloc(nchains * sizeof(double), st), "cudaMallocAsync");
-        RGF_CUDA(dT.alloc(nchains * sizeof(double), st), "cudaMallocAsync");
-        RGF_CUDA(dS.alloc(nchains * sizeof(int32_t), st), "cudaMallocAsync");
-        RGF_CUDA(cudaMemcpyAsync(dE.p, E, nchains * sizeof(double), cudaMemcpyHostToDevice, st), "H2D");
-        s = run_conductance(rib, (const double*)dE.p, nchains, eta_device, eta_lead, precision, st,
-                            (double*)dT.p, (int32_t*)dS.p);
-        if (s != RGF_OK) return s;
-        RGF_CUDA(cudaMemcpyAsync(hT.data(), dT.p, nchains * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
-        RGF_CUDA(cudaMemcpyAsync(hs.data(), dS.p, nchains * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "D2H");
-    }
-    RGF_CUDA(cudaStreamSynchronize(st), "rgf_conductance");
-    std::memcpy(T, hT.data(), nchains * sizeof(double));
-    if (chain_status) std::memcpy(chain_status, hs.data(), nchains * sizeof(int32_t));
-    for (int i = 0; i < nchains; ++i)
-        if (hs[i] != RGF_OK)
-            return fail((rgf_status)hs[i], std::string("chain ") + std::to_string(i) + ": " +
-                                               rgf_status_str(hs[i]));
-    return RGF_OK;
+    return run_host(rib, E, nchains, eta_device, eta_lead, precision, T, chain_status);
 }
 
 rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, int nchains,
                                 double eta_device, double eta_lead, int precision,
                                 int ckpt_stride, double* T, double* dT_deps,
                                 int32_t* chain_status) {
-    (void)rib; (void)E; (void)nchains; (void)eta_device; (void)eta_lead; (void)precision;
-    (void)ckpt_stride; (void)T; (void)dT_deps; (void)chain_status;
-    return fail(RGF_EINVAL, "rgf_conductance_grad: not available in this build");
+    if (nchains > 0 && !dT_deps) return fail(RGF_EINVAL, "dT_deps is NULL");
+    return run_host(rib, E, nchains, eta_device, eta_lead, precision, T, chain_status, dT_deps,
+                    ckpt_stride);
 }
 
 }  // extern "C"

@@ -128,6 +128,9 @@ __device__ __forceinline__ zf cmac(zf c, zf a, zf b, bool neg) {
     return r;
 }
 
+__device__ __forceinline__ zd cconj(zd a) { return {a.re, -a.im}; }
+__device__ __forceinline__ zf cconj(zf a) { return {a.re, df_neg(a.im)}; }
+
 // Scale by a real binary64 constant.
 __device__ __forceinline__ zd cscale(zd a, double s) { return {a.re * s, a.im * s}; }
 __device__ __forceinline__ zf cscale(zf a, double s) {
@@ -150,7 +153,25 @@ __device__ __forceinline__ bool cfinite(zf a) { return isfinite(a.re.hi) && isfi
 // ---------------------------------------------------------------------------
 enum : int {
     ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOCONV = 4,
-    ST_ESINGULAR = 5, ST_ENONFINITE = 6, ST_ETIMEOUT = 7
+    ST_ESINGULAR = 5, ST_ENONFINITE = 6, ST_ETIMEOUT = 7, ST_EBOUNDS = 8
 };
+
+// Unit roundoff of the working precision (binary64: 2^-53; double-float: 2^-48).
+template <class R> struct Unit;
+template <> struct Unit<double> { static constexpr double u = 1.1102230246251565e-16; };
+template <> struct Unit<df32> { static constexpr double u = 3.552713678800501e-15; };
+
+// Number of propagating channels of a pristine armchair ribbon of N lines at
+// energy E: modes p with |t| |1 + 2 c_p| <= |E| < |t| (1 + 2 |c_p|),
+// c_p = cos(p pi / (N + 1)) (the band edges of the transverse modes).
+__device__ __forceinline__ int channels(int N, double t, double E) {
+    int n = 0;
+    const double at = fabs(t), ae = fabs(E);
+    for (int p = 1; p <= N; ++p) {
+        double c = cospi((double)p / (double)(N + 1));
+        if (at * fabs(1.0 + 2.0 * c) <= ae && ae < at * (1.0 + 2.0 * fabs(c))) ++n;
+    }
+    return n;
+}
 
 }  // namespace rgf

@@ -134,7 +134,9 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
 //   j from every other row (storing -A[i][j]/A[j][j] in column j).  The row
 //   swaps are undone at the end by a column permutation applied while copying
 //   into G.  The pivot reciprocal is formed in binary64.
-// Returns a flag: bit 0 = zero pivot met, bit 1 = non-finite pivot met.
+// Returns a flag: bit 0 = zero pivot, or a pivot below 64 u sqrt(amax2) with
+// amax2 = max |A_ij|^2 supplied by the caller (0 disables the test); bit 1 =
+// non-finite pivot.
 // ---------------------------------------------------------------------------
 template <class R>
 struct GJSmem {
@@ -150,7 +152,7 @@ struct GJSmem {
 
 template <class R>
 __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __restrict__ G, int ldg,
-                             GJSmem<R> s) {
+                             GJSmem<R> s, double amax2 = 0.0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < K; i += NT) {
         cx<R> v = A[(size_t)i * lda];
@@ -158,6 +160,8 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         s.colabs[i] = cabs2(v);
     }
     if (tid == 0) s.ctl[1] = 0;
+    // pivots below 64 u max|A| mean a numerically singular slice (bit 0)
+    const double tiny2 = amax2 * (64.0 * Unit<R>::u) * (64.0 * Unit<R>::u);
     __syncthreads();
     for (int j = 0; j < K; ++j) {
         if (warp == 0) {
@@ -176,8 +180,9 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                 zd pz = to_z(s.colval[bi]);
                 double d = pz.re * pz.re + pz.im * pz.im;
                 int flag = s.ctl[1];
-                if (!(d > 0.0)) { flag |= 1; d = 1.0; pz = {1.0, 0.0}; }
-                if (!isfinite(d)) { flag |= 2; }
+                if (!isfinite(d)) { flag |= 2; d = 1.0; pz = {1.0, 0.0}; }
+                else if (!(d > 0.0)) { flag |= 1; d = 1.0; pz = {1.0, 0.0}; }
+                else if (d < tiny2) { flag |= 1; }
                 s.ctl[1] = flag;
                 s.ctl[0] = bi;
                 s.perm[j] = bi;

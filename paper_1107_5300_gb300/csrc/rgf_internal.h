@@ -32,12 +32,13 @@ struct ChainDev {
     double t, E;
     int lead;               // index of its lead problem
     size_t ws_off;          // offset (16-byte elements) of its sweep workspace
+    size_t grad_off;        // offset (doubles) of its dT/d eps block (adjoint only)
 };
 
 // Number of 16-byte elements of the decimation workspace of one lead problem.
 inline size_t lead_ws_elems(int N) {
     size_t KL = (size_t)col_KL(N);
-    return 20 * KL * KL;
+    return KL * KL;   // the KL x KL (binary64) transverse mode basis, with room to spare
 }
 inline size_t lead_out_elems(int N) {
     size_t KL = (size_t)col_KL(N), KR = (size_t)col_KR(N);
@@ -53,8 +54,8 @@ inline size_t sweep_ws_elems(int N) {
 size_t sweep_smem_bytes(int Kmax);
 
 // Kernel launchers (return cudaGetLastError() after the launch).
-// side: 0 left, 1 right; both sides are computed (grid = 2 * nlead);
-// lead_status / lead_iters hold [2 * nlead] entries (left, right per problem).
+// One block per lead problem computes both leads; lead_status / lead_iters
+// hold [2 * nlead] entries (left, right per problem).
 cudaError_t launch_lead(const LeadDev* leads, int nlead, int Kmax, double eta_lead,
                         void* ws, void* out, int* lead_status, int* lead_iters,
                         cudaStream_t st);
@@ -63,5 +64,14 @@ cudaError_t launch_sweep(int precision, const ChainDev* chains, const int* order
                          int Kmax, double eta_device, const void* leadout, const int* lead_status,
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st);
+
+// Adjoint sweep: workspace (16-byte elements) of one chain with segments of
+// seg_cols columns, and the launcher (seg_cols: [nchains] on the device; dT:
+// zero-initialised doubles, chain c's block at chains[c].grad_off).
+size_t grad_ws_elems(int N, int L, int seg_cols);
+cudaError_t launch_grad(int precision, const ChainDev* chains, const int* order, int nchains,
+                        int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                        const LeadDev* leads, void* ws, const int* seg_cols, double* T, double* dT,
+                        int32_t* status, cudaStream_t st);
 
 }  // namespace rgf

@@ -1,305 +1,168 @@
 // rgf_lead.cu -- semi-infinite lead self-energies by Lopez Sancho-Rubio
-// decimation, binary64, one thread block per (energy, side).
+// decimation, binary64, one thread block per energy (both leads).
 //
 // The paper includes the lead self-energies at the first and last slice (text
-// after Eqs. 4-5).  Decimation (Lopez Sancho, Lopez Sancho, Rubio 1985) on a
-// principal layer of one unit cell iterates
-//     g = (z - eps)^-1;  eps_s += a g b;  eps += a g b + b g a;
-//     a <- a g a;  b <- b g b
-// until the effective coupling a (and b = a^T) vanishes, then
-// g_s = (z - eps_s)^-1.  In the column slicing of a cell (columns c0..c3 at
-// x = 0, a, 1.5a, 2.5a) the cell-to-cell hopping only joins column c3 of one
-// cell to column c0 of the next, so every correction lives on the c0c0 and
-// c3c3 blocks and a on the c3->c0 (or c0->c3) block.  Each iteration only needs
-// the four corner blocks of (z - eps)^-1 on {c0, c3}; they come from a left
-// and a right sweep through the cell's four columns.  Same algebra as the
-// full-cell iteration, on KL x KL / KR x KR blocks instead of 2N x 2N.
-//   right lead: a0 = H(c3 -> c0'), corrections of eps_s on c3, g_s needed on c0,
-//               Sigma_R = W30 g_s[c0c0] W30^T  (acts on c3 of the last cell)
-//   left lead:  a0 = H(c0 -> c3'), corrections of eps_s on c0, g_s needed on c3,
-//               Sigma_L = W30^T g_s[c3c3] W30  (acts on c0 of the first cell)
+// after Eqs. 4-5).  The leads are pristine armchair ribbons, so the lead
+// Hamiltonian separates exactly into transverse modes: with
+// phi_p(j) = sin(p pi (j+1)/(N+1)) on rows j = 0..N-1, the vector
+// phi_p restricted to the even rows (columns c0, c1 of a cell) is mapped by the
+// row +-1 hopping stencil onto 2 cos(p pi/(N+1)) times phi_p restricted to the
+// odd rows (columns c2, c3), because phi_p(j-1) + phi_p(j+1) = 2 cos(...) phi_p(j)
+// and phi_p vanishes at j = -1 and j = N.  Modes p = 1..KL are an orthogonal
+// basis of the even rows, p = 1..KR of the odd rows.  Each mode is a chain
+//     c0 -t- c1 -tau- c2 -t- c3 -tau- c0' -t- ...,   tau_p = 2 t cos(p pi/(N+1)),
+// i.e. a two-site principal layer (A -t- B) joined by tau.  Sancho-Rubio
+// decimation of that layer,
+//     g = (z - eps)^-1;  eps_s += a g b;  eps += a g b + b g a;  a <- a g a; b <- b g b
+// keeps a on the B->A' entry, the corrections on the A and B diagonal, and
+// stops when |a| < 1e-14 eV.  The surface Green's function at the first atom of
+// a semi-infinite mode chain (for both leads the outermost bond is t) is
+//     g_p = (z - s_B) / (z (z - s_B) - t^2).
+// Back in real space, with u_p the normalised restricted mode vectors:
+//     Sigma_L = sum_p tau_p^2 g_p u_p^even u_p^even^T   (on c0 of the first cell)
+//     Sigma_R = sum_p tau_p^2 g_p u_p^odd  u_p^odd^T    (on c3 of the last cell)
+// which equal H01^T g_s H01 and H01 g_s H01^T of the full-cell iteration, at
+// O(N) work per iteration instead of O(N^3) and without inverting isolated
+// sub-blocks of the cell.
 #include "rgf_device.cuh"
 #include "rgf_internal.h"
 
 namespace rgf {
 
-size_t sweep_smem_bytes(int Kmax);
-
 namespace {
 
-struct LeadSmem {
-    GJSmem<double> gj;
-    zd* gemm;
-    double* red;
-};
+constexpr double kTol = 1e-14;
+constexpr int kMaxIter = 200;
 
-__device__ LeadSmem carve_lead(unsigned char* base, int Kmax) {
-    LeadSmem s;
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        unsigned char* p = base + o;
-        o += (bytes + 15) & ~(size_t)15;
-        return p;
-    };
-    s.gj.rowbuf = (zd*)take((size_t)Kmax * 16);
-    s.gj.colbuf = (zd*)take((size_t)Kmax * 16);
-    s.gj.colval = (zd*)take((size_t)Kmax * 16);
-    s.gemm = (zd*)take(2 * 8 * 64 * 16);
-    s.gj.inv = (zd*)take(16);
-    s.gj.colabs = (double*)take((size_t)Kmax * 8);
-    take((size_t)Kmax * 8);
-    s.red = (double*)take(NWARP * 8);
-    s.gj.perm = (int*)take((size_t)Kmax * 4);
-    s.gj.idx = (int*)take((size_t)Kmax * 4);
-    s.gj.ctl = (int*)take(16);
-    return s;
+// Mode p (1-based) of an N-line ribbon: surface Green's function and iterations.
+__device__ zd mode_surface(int p, int N, double t, zd z, int& iters, bool& ok) {
+    const double tau = 2.0 * t * cospi((double)p / (double)(N + 1));
+    zd a = {tau, 0.0};
+    zd dA = {0.0, 0.0}, dB = {0.0, 0.0}, sB = {0.0, 0.0};
+    const zd tt = {t * t, 0.0};
+    ok = false;
+    int it;
+    for (it = 1; it <= kMaxIter; ++it) {
+        zd zA = csub(z, dA), zB = csub(z, dB);
+        zd det = csub(cmul(zA, zB), tt);
+        double d2 = det.re * det.re + det.im * det.im;
+        zd idet = {det.re / d2, -det.im / d2};
+        zd gAA = cmul(zB, idet), gBB = cmul(zA, idet), gAB = cscale(idet, t);
+        zd a2 = cmul(a, a);
+        zd agb = cmul(a2, gAA), bga = cmul(a2, gBB);
+        dB = cadd(dB, agb);
+        sB = cadd(sB, agb);
+        dA = cadd(dA, bga);
+        a = cmul(a2, gAB);
+        double ma = a.re * a.re + a.im * a.im;
+        if (!isfinite(ma) || !cfinite(dA) || !cfinite(dB)) break;
+        if (ma < kTol * kTol) { ok = true; break; }
+    }
+    iters = it;
+    zd zs = csub(z, sB);
+    zd den = csub(cmul(z, zs), tt);
+    double d2 = den.re * den.re + den.im * den.im;
+    zd g = cmul(zs, zd{den.re / d2, -den.im / d2});
+    if (!cfinite(g)) ok = false;
+    return g;
 }
 
-// X (K x K, ld) = z I - D - s * Y   (D, Y may be null)
-__device__ void shift_minus(zd* X, int K, int ld, zd z, const zd* D, const zd* Y, double s) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < K; i += NWARP)
-        for (int l = lane; l < K; l += 32) {
-            zd v = (i == l) ? z : zd{0.0, 0.0};
-            if (D) v = csub(v, D[(size_t)i * ld + l]);
-            if (Y) v = csub(v, cscale(Y[(size_t)i * ld + l], s));
-            X[(size_t)i * ld + l] = v;
-        }
+// Normalised restricted mode vectors: U[i][p-1] = phi_p(row of entry i) / norm,
+// rows 2i + parity, i < K.  sinpi with an exactly reduced argument.
+__device__ void mode_basis(double* U, int K, int N, int parity, double* red) {
+    const int twoN2 = 2 * (N + 1);
+    for (int e = threadIdx.x; e < K * K; e += NT) {
+        int i = e / K, p = e % K + 1;
+        long long m = ((long long)(2 * i + parity + 1) * p) % twoN2;
+        U[e] = sinpi((double)m / (double)(N + 1));
+    }
+    __syncthreads();
+    // column norms
+    for (int p = threadIdx.x; p < K; p += NT) {
+        double s = 0.0;
+        for (int i = 0; i < K; ++i) s += U[i * K + p] * U[i * K + p];
+        red[p] = rsqrt(s);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < K * K; e += NT) U[e] *= red[e % K];
     __syncthreads();
 }
 
-// X (KR x KR) = z I - t^2 * [sum over p in {q,q+1}, p' in {q',q'+1}] F[p][p']
-// (W12^T F W12 with F of size KL).
-__device__ void x_from_w12T_F_w12(zd* X, int KL, int KR, int ld, zd z, const zd* F, double t2) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = warp; q < KR; q += NWARP)
-        for (int r = lane; r < KR; r += 32) {
-            zd s = {0.0, 0.0};
-            for (int a = q; a <= q + 1; ++a)
-                for (int b = r; b <= r + 1; ++b)
-                    if (a < KL && b < KL) s = cadd(s, F[(size_t)a * ld + b]);
-            zd v = (q == r) ? z : zd{0.0, 0.0};
-            X[(size_t)q * ld + r] = csub(v, cscale(s, t2));
+// S[i][j] = sum_p U[i][p] w[p] U[j][p];  Gam = i (S - S^dagger).
+__device__ void assemble(zd* S, zd* Gam, const double* U, const zd* w, int K) {
+    for (int e = threadIdx.x; e < K * K; e += NT) {
+        int i = e / K, j = e % K;
+        double re = 0.0, im = 0.0;
+        for (int p = 0; p < K; ++p) {
+            double u = U[i * K + p] * U[j * K + p];
+            re = fma(u, w[p].re, re);
+            im = fma(u, w[p].im, im);
         }
+        S[e] = {re, im};
+    }
     __syncthreads();
-}
-
-// X (KL x KL) = z I - t^2 * [sum over q in {p-1,p}, q' in {p'-1,p'}] F[q][q']
-// (W12 F W12^T with F of size KR).
-__device__ void x_from_w12_F_w12T(zd* X, int KL, int KR, int ld, zd z, const zd* F, double t2) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int p = warp; p < KL; p += NWARP)
-        for (int r = lane; r < KL; r += 32) {
-            zd s = {0.0, 0.0};
-            for (int a = p - 1; a <= p; ++a)
-                for (int b = r - 1; b <= r; ++b)
-                    if (a >= 0 && b >= 0 && a < KR && b < KR) s = cadd(s, F[(size_t)a * ld + b]);
-            zd v = (p == r) ? z : zd{0.0, 0.0};
-            X[(size_t)p * ld + r] = csub(v, cscale(s, t2));
-        }
-    __syncthreads();
-}
-
-__device__ void addto2(zd* A, zd* B, const zd* S, int m, int n, int ld) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < m; i += NWARP)
-        for (int l = lane; l < n; l += 32) {
-            zd v = S[(size_t)i * ld + l];
-            A[(size_t)i * ld + l] = cadd(A[(size_t)i * ld + l], v);
-            if (B) B[(size_t)i * ld + l] = cadd(B[(size_t)i * ld + l], v);
-        }
-    __syncthreads();
-}
-
-__device__ void zero(zd* A, int m, int n, int ld) {
-    for (int e = threadIdx.x; e < m * n; e += NT) A[(size_t)(e / n) * ld + (e % n)] = {0.0, 0.0};
+    for (int e = threadIdx.x; e < K * K; e += NT) {
+        int i = e / K, j = e % K;
+        zd sij = S[(size_t)i * K + j], sji = S[(size_t)j * K + i];
+        double dr = sij.re - sji.re, di = sij.im + sji.im;
+        Gam[e] = {-di, dr};
+    }
     __syncthreads();
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(NT, 1)
-lead_kernel(const LeadDev* __restrict__ leads, int nlead, int Kmax, double eta,
-            zd* __restrict__ ws, zd* __restrict__ out, int* __restrict__ lead_status,
-            int* __restrict__ lead_iters) {
+lead_kernel(const LeadDev* __restrict__ leads, int nlead, double eta, double* __restrict__ ws,
+            zd* __restrict__ out, int* __restrict__ lead_status, int* __restrict__ lead_iters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LeadSmem s = carve_lead(smem_raw, Kmax);
-    const int prob = blockIdx.x >> 1, side = blockIdx.x & 1;
+    const int prob = blockIdx.x;
     const LeadDev ld = leads[prob];
-    const int N = ld.N, KL = col_KL(N), KR = col_KR(N), L2 = KL;   // ld of every block = KL
-    const double t = ld.t, t2 = t * t;
+    const int N = ld.N, KL = col_KL(N), KR = col_KR(N);
+    zd* w = reinterpret_cast<zd*>(smem_raw);                    // [KL]
+    double* red = reinterpret_cast<double*>(w + KL);             // [max(KL, NWARP)]
+    int* flags = reinterpret_cast<int*>(red + (KL > NWARP ? KL : NWARP));   // [2]
+    if (threadIdx.x == 0) { flags[0] = 1; flags[1] = 0; }
+    __syncthreads();
     const zd z = {ld.E, eta};
-    const size_t B = (size_t)KL * KL;
-    zd* base = ws + ld.ws_off;
-    zd *Xw = base, *f0 = base + B, *f1 = base + 2 * B, *f2 = base + 3 * B, *G33 = base + 4 * B;
-    zd *r3 = base + 5 * B, *r2 = base + 6 * B, *r1 = base + 7 * B, *G00 = base + 8 * B;
-    zd *G03 = base + 9 * B, *T1 = base + 10 * B, *T2 = base + 11 * B, *T3 = base + 12 * B;
-    zd *a = base + 13 * B, *tmp = base + 14 * B, *tmp2 = base + 15 * B, *anew = base + 16 * B;
-    zd *D0 = base + 17 * B, *D3 = base + 18 * B, *Ds = base + 19 * B;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    // a0: right lead KR x KL, a[q][p] = t for p in {q, q+1};
-    //     left lead  KL x KR, a[p][q] = t for q in {p-1, p}.
-    const int am = side ? KR : KL, an = side ? KL : KR;
-    for (int e = threadIdx.x; e < am * an; e += NT) {
-        int i = e / an, j = e % an;
-        bool on = side ? (j == i || j == i + 1) : (j == i - 1 || j == i);
-        a[(size_t)i * L2 + j] = on ? zd{t, 0.0} : zd{0.0, 0.0};
+    for (int p = threadIdx.x; p < KL; p += NT) {
+        int it;
+        bool ok;
+        zd g = mode_surface(p + 1, N, ld.t, z, it, ok);
+        const double tau = 2.0 * ld.t * cospi((double)(p + 1) / (double)(N + 1));
+        w[p] = cscale(g, tau * tau);
+        if (!ok) atomicExch(&flags[0], 0);
+        atomicMax(&flags[1], it);
     }
-    zero(D0, KL, KL, L2);
-    zero(D3, KR, KR, L2);
-    zero(Ds, side ? KR : KL, side ? KR : KL, L2);
-
-    const double tol = 1e-14;
-    const int max_iter = 200;
-    int it = 0, ok = 0, flag = 0;
-    for (it = 1; it <= max_iter; ++it) {
-        // forward through c0..c3: G33 and G03
-        shift_minus(Xw, KL, L2, z, D0, nullptr, 0.0);
-        flag |= cta_gj_invert<double>(Xw, KL, L2, f0, L2, s.gj);
-        shift_minus(Xw, KL, L2, z, nullptr, f0, t2);
-        flag |= cta_gj_invert<double>(Xw, KL, L2, f1, L2, s.gj);
-        x_from_w12T_F_w12(Xw, KL, KR, L2, z, f1, t2);
-        flag |= cta_gj_invert<double>(Xw, KR, L2, f2, L2, s.gj);
-        shift_minus(Xw, KR, L2, z, D3, f2, t2);
-        flag |= cta_gj_invert<double>(Xw, KR, L2, G33, L2, s.gj);
-        cta_gemm<double, false, false>(KL, KL, KL, f0, L2, f1, L2, T1, L2, GEMM_SET, s.gemm);
-        for (int p = warp; p < KL; p += NWARP)
-            for (int q = lane; q < KR; q += 32) {
-                zd v = T1[(size_t)p * L2 + q];
-                if (q + 1 < KL) v = cadd(v, T1[(size_t)p * L2 + q + 1]);
-                T2[(size_t)p * L2 + q] = cscale(v, t2 * t);
-            }
-        __syncthreads();
-        cta_gemm<double, false, false>(KL, KR, KR, T2, L2, f2, L2, T3, L2, GEMM_SET, s.gemm);
-        cta_gemm<double, false, false>(KL, KR, KR, T3, L2, G33, L2, G03, L2, GEMM_SET, s.gemm);
-        // backward through c3..c0: G00
-        shift_minus(Xw, KR, L2, z, D3, nullptr, 0.0);
-        flag |= cta_gj_invert<double>(Xw, KR, L2, r3, L2, s.gj);
-        shift_minus(Xw, KR, L2, z, nullptr, r3, t2);
-        flag |= cta_gj_invert<double>(Xw, KR, L2, r2, L2, s.gj);
-        x_from_w12_F_w12T(Xw, KL, KR, L2, z, r2, t2);
-        flag |= cta_gj_invert<double>(Xw, KL, L2, r1, L2, s.gj);
-        shift_minus(Xw, KL, L2, z, D0, r1, t2);
-        flag |= cta_gj_invert<double>(Xw, KL, L2, G00, L2, s.gj);
-
-        if (side) {
-            // a: KR x KL.  a g[c0c0] a^T -> c3c3 (eps and eps_s); a^T g[c3c3] a -> c0c0;
-            // a <- a g[c0c3] a.
-            cta_gemm<double, false, false>(KR, KL, KL, a, L2, G00, L2, tmp, L2, GEMM_SET, s.gemm);
-            cta_gemm<double, false, true>(KR, KR, KL, tmp, L2, a, L2, tmp2, L2, GEMM_SET, s.gemm);
-            addto2(D3, Ds, tmp2, KR, KR, L2);
-            cta_gemm<double, true, false>(KL, KR, KR, a, L2, G33, L2, tmp, L2, GEMM_SET, s.gemm);
-            cta_gemm<double, false, false>(KL, KL, KR, tmp, L2, a, L2, tmp2, L2, GEMM_SET, s.gemm);
-            addto2(D0, nullptr, tmp2, KL, KL, L2);
-            cta_gemm<double, false, false>(KR, KR, KL, a, L2, G03, L2, tmp, L2, GEMM_SET, s.gemm);
-            cta_gemm<double, false, false>(KR, KL, KR, tmp, L2, a, L2, anew, L2, GEMM_SET, s.gemm);
-        } else {
-            // a: KL x KR.  a g[c3c3] a^T -> c0c0 (eps and eps_s); a^T g[c0c0] a -> c3c3;
-            // a <- a g[c3c0] a = a G03^T a.
-            cta_gemm<double, false, false>(KL, KR, KR, a, L2, G33, L2, tmp, L2, GEMM_SET, s.gemm);
-            cta_gemm<double, false, true>(KL, KL, KR, tmp, L2, a, L2, tmp2, L2, GEMM_SET, s.gemm);
-            addto2(D0, Ds, tmp2, KL, KL, L2);
-            cta_gemm<double, true, false>(KR, KL, KL, a, L2, G00, L2, tmp, L2, GEMM_SET, s.gemm);
-            cta_gemm<double, false, false>(KR, KR, KL, tmp, L2, a, L2, tmp2, L2, GEMM_SET, s.gemm);
-            addto2(D3, nullptr, tmp2, KR, KR, L2);
-            cta_gemm<double, false, true>(KL, KL, KR, a, L2, G03, L2, tmp, L2, GEMM_SET, s.gemm);
-            cta_gemm<double, false, false>(KL, KR, KL, tmp, L2, a, L2, anew, L2, GEMM_SET, s.gemm);
-        }
-        double mx = 0.0;
-        for (int e = threadIdx.x; e < am * an; e += NT) {
-            size_t o = (size_t)(e / an) * L2 + (e % an);
-            zd v = anew[o];
-            a[o] = v;
-            double m2 = cabs2(v);
-            mx = (isnan(m2) || m2 > mx) ? m2 : mx;
-        }
-        mx = block_max(mx, s.red);
-        if (!isfinite(mx) || (flag & 2)) break;
-        if (mx < tol * tol) { ok = 1; break; }
-    }
-
-    zd* sig = out + ld.off + (side ? (size_t)KL * KL : 0);
-    zd* gam = out + ld.off + (size_t)KL * KL + (size_t)KR * KR + (side ? (size_t)KL * KL : 0);
-    const int K = side ? KR : KL;
+    __syncthreads();
+    const bool ok = flags[0] != 0;
+    zd* SigL = out + ld.off;
+    zd* SigR = SigL + (size_t)KL * KL;
+    zd* GamL = SigR + (size_t)KR * KR;
+    zd* GamR = GamL + (size_t)KL * KL;
+    double* U = ws + 2 * ld.ws_off;
     if (ok) {
-        zd* gs;
-        if (side) {
-            // g_s on c0 of the surface cell; eps_s corrected on c3.
-            shift_minus(Xw, KR, L2, z, Ds, nullptr, 0.0);
-            flag |= cta_gj_invert<double>(Xw, KR, L2, r3, L2, s.gj);
-            shift_minus(Xw, KR, L2, z, nullptr, r3, t2);
-            flag |= cta_gj_invert<double>(Xw, KR, L2, r2, L2, s.gj);
-            x_from_w12_F_w12T(Xw, KL, KR, L2, z, r2, t2);
-            flag |= cta_gj_invert<double>(Xw, KL, L2, r1, L2, s.gj);
-            shift_minus(Xw, KL, L2, z, nullptr, r1, t2);
-            flag |= cta_gj_invert<double>(Xw, KL, L2, G00, L2, s.gj);
-            gs = G00;
-            // Sigma_R[q][q'] = t^2 sum_{p in {q,q+1}, p' in {q',q'+1}} gs[p][p']
-            for (int q = warp; q < KR; q += NWARP)
-                for (int r = lane; r < KR; r += 32) {
-                    zd v = {0.0, 0.0};
-                    for (int pa = q; pa <= q + 1; ++pa)
-                        for (int pb = r; pb <= r + 1; ++pb)
-                            if (pa < KL && pb < KL) v = cadd(v, gs[(size_t)pa * L2 + pb]);
-                    sig[(size_t)q * KR + r] = cscale(v, t2);
-                }
-        } else {
-            // g_s on c3 of the surface cell; eps_s corrected on c0.
-            shift_minus(Xw, KL, L2, z, Ds, nullptr, 0.0);
-            flag |= cta_gj_invert<double>(Xw, KL, L2, f0, L2, s.gj);
-            shift_minus(Xw, KL, L2, z, nullptr, f0, t2);
-            flag |= cta_gj_invert<double>(Xw, KL, L2, f1, L2, s.gj);
-            x_from_w12T_F_w12(Xw, KL, KR, L2, z, f1, t2);
-            flag |= cta_gj_invert<double>(Xw, KR, L2, f2, L2, s.gj);
-            shift_minus(Xw, KR, L2, z, nullptr, f2, t2);
-            flag |= cta_gj_invert<double>(Xw, KR, L2, G33, L2, s.gj);
-            gs = G33;
-            // Sigma_L[p][p'] = t^2 sum_{q in {p-1,p}, q' in {p'-1,p'}} gs[q][q']
-            for (int p = warp; p < KL; p += NWARP)
-                for (int r = lane; r < KL; r += 32) {
-                    zd v = {0.0, 0.0};
-                    for (int qa = p - 1; qa <= p; ++qa)
-                        for (int qb = r - 1; qb <= r; ++qb)
-                            if (qa >= 0 && qb >= 0 && qa < KR && qb < KR)
-                                v = cadd(v, gs[(size_t)qa * L2 + qb]);
-                    sig[(size_t)p * KL + r] = cscale(v, t2);
-                }
-        }
-        __syncthreads();
-        double bad = 0.0;
-        for (int e = threadIdx.x; e < K * K; e += NT) {
-            int i = e / K, j = e % K;
-            zd sij = sig[(size_t)i * K + j], sji = sig[(size_t)j * K + i];
-            // Gamma = i (Sigma - Sigma^dagger)
-            double dr = sij.re - sji.re, di = sij.im + sji.im;
-            gam[(size_t)i * K + j] = {-di, dr};
-            if (!cfinite(sij)) bad = 1.0;
-        }
-        bad = block_max(bad, s.red);
-        if (bad > 0.0 || (flag & 2)) ok = 0;
-    }
-    if (!ok) {
-        for (int e = threadIdx.x; e < K * K; e += NT) {
-            sig[e] = {NAN, NAN};
-            gam[e] = {NAN, NAN};
-        }
+        mode_basis(U, KL, N, 0, red);
+        assemble(SigL, GamL, U, w, KL);
+        mode_basis(U, KR, N, 1, red);
+        assemble(SigR, GamR, U, w, KR);
+    } else {
+        for (int e = threadIdx.x; e < KL * KL; e += NT) SigL[e] = GamL[e] = {NAN, NAN};
+        for (int e = threadIdx.x; e < KR * KR; e += NT) SigR[e] = GamR[e] = {NAN, NAN};
     }
     if (threadIdx.x == 0) {
-        lead_status[2 * prob + side] = ok ? ST_OK : ST_ENOCONV;
-        if (lead_iters) lead_iters[2 * prob + side] = ok ? it : -1;
+        const int st = ok ? ST_OK : ST_ENOCONV;
+        lead_status[2 * prob] = lead_status[2 * prob + 1] = st;
+        if (lead_iters) lead_iters[2 * prob] = lead_iters[2 * prob + 1] = ok ? flags[1] : -1;
     }
 }
 
 cudaError_t launch_lead(const LeadDev* leads, int nlead, int Kmax, double eta_lead, void* ws,
                         void* out, int* lead_status, int* lead_iters, cudaStream_t st) {
     if (nlead <= 0) return cudaSuccess;
-    size_t smem = sweep_smem_bytes(Kmax);
-    cudaError_t e = cudaFuncSetAttribute(lead_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    lead_kernel<<<2 * nlead, NT, smem, st>>>(leads, nlead, Kmax, eta_lead, (zd*)ws, (zd*)out,
-                                             lead_status, lead_iters);
+    size_t smem = (size_t)Kmax * 16 + (size_t)(Kmax > NWARP ? Kmax : NWARP) * 8 + 16;
+    lead_kernel<<<nlead, NT, smem, st>>>(leads, nlead, eta_lead, (double*)ws, (zd*)out,
+                                         lead_status, lead_iters);
     return cudaGetLastError();
 }
 

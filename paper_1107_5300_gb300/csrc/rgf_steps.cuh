@@ -1,0 +1,230 @@
+// rgf_steps.cuh -- one column step of the forward RGF recursion (Eqs. 4-5) and
+// the helpers shared by the forward sweep (rgf_sweep.cu) and the adjoint sweep
+// (rgf_grad.cu).  See rgf_sweep.cu for the column slicing.
+#pragma once
+
+#include <type_traits>
+
+#include "rgf_device.cuh"
+#include "rgf_internal.h"
+
+namespace rgf {
+
+template <class R>
+struct SweepSmem {
+    GJSmem<R> gj;
+    cx<R>* gemm;
+    uint8_t* kc;     // keep mask of the current column
+    uint8_t* kp;     // keep mask of the previous column
+    uint8_t* kn;     // keep mask of the next column (adjoint)
+    double* eps;
+    double* red;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <class R>
+__device__ SweepSmem<R> carve(unsigned char* base, int Kmax) {
+    SweepSmem<R> s;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { unsigned char* p = base + o; o += align16(bytes); return p; };
+    s.gj.rowbuf = (cx<R>*)take((size_t)Kmax * 16);
+    s.gj.colbuf = (cx<R>*)take((size_t)Kmax * 16);
+    s.gj.colval = (cx<R>*)take((size_t)Kmax * 16);
+    s.gemm = (cx<R>*)take(2 * 8 * 64 * 16);
+    s.gj.inv = (zd*)take(16);
+    s.gj.colabs = (double*)take((size_t)Kmax * 8);
+    s.eps = (double*)take((size_t)Kmax * 8);
+    s.red = (double*)take(NWARP * 8);
+    s.gj.perm = (int*)take((size_t)Kmax * 4);
+    s.gj.idx = (int*)take((size_t)Kmax * 4);
+    s.gj.ctl = (int*)take(16);
+    s.kc = (uint8_t*)take((size_t)Kmax);
+    s.kp = (uint8_t*)take((size_t)Kmax);
+    s.kn = (uint8_t*)take((size_t)Kmax);
+    return s;
+}
+
+// Everything a block needs to know about its chain.
+struct ChainCtx {
+    const double* eps;
+    const uint8_t* rem;
+    int N, L, M, KL, KR, ncol;
+    double t, t2;
+    zd z;
+    const zd *SigL, *SigR, *GamL, *GamR;
+};
+
+__device__ inline ChainCtx make_ctx(const ChainDev& ch, const LeadDev& ld, const zd* leadout,
+                                    double eta_d) {
+    ChainCtx c;
+    c.eps = ch.eps;
+    c.rem = ch.rem;
+    c.N = ch.N;
+    c.L = ch.L;
+    c.M = 2 * ch.N;
+    c.KL = col_KL(ch.N);
+    c.KR = col_KR(ch.N);
+    c.ncol = 4 * ch.L;
+    c.t = ch.t;
+    c.t2 = ch.t * ch.t;
+    c.z = {ch.E, eta_d};
+    c.SigL = leadout + ld.off;
+    c.SigR = c.SigL + (size_t)c.KL * c.KL;
+    c.GamL = c.SigR + (size_t)c.KR * c.KR;
+    c.GamR = c.GamL + (size_t)c.KL * c.KL;
+    return c;
+}
+
+__device__ __forceinline__ int col_size(const ChainCtx& c, int k) { return ((k & 3) < 2) ? c.KL : c.KR; }
+
+// Source stencil of the coupling W_k into column k (type c = k mod 4): entry i
+// of column k is bonded to entries a0, a1 (-1 = none) of column k-1 (size Kp).
+//   c = 1, 3: same row (t I);  c = 2: rows q, q+1 of the even column;
+//   c = 0: rows p-1, p of the odd column of the previous cell.
+__device__ __forceinline__ void col_src(int c, int i, int Kp, int& a0, int& a1) {
+    if (c == 1 || c == 3) { a0 = i; a1 = -1; }
+    else if (c == 2) { a0 = i; a1 = (i + 1 < Kp) ? i + 1 : -1; }
+    else { a0 = i - 1; a1 = (i < Kp) ? i : -1; }
+}
+// Transposed stencil: entries b0, b1 of column k (size K) bonded to entry a of
+// column k-1.
+__device__ __forceinline__ void col_src_T(int c, int a, int K, int& b0, int& b1) {
+    if (c == 1 || c == 3) { b0 = a; b1 = -1; }
+    else if (c == 2) { b0 = (a - 1 >= 0 && a - 1 < K) ? a - 1 : -1; b1 = (a < K) ? a : -1; }
+    else { b0 = (a < K) ? a : -1; b1 = (a + 1 < K) ? a + 1 : -1; }
+}
+
+// Keep mask (0 = removed atom) and on-site energies of column k into shared memory.
+__device__ inline void load_col(const ChainCtx& c, int k, uint8_t* km, double* eps) {
+    if (k < 0 || k >= c.ncol) return;
+    const int n = k >> 2, ct = k & 3, K = col_size(c, k);
+    for (int i = threadIdx.x; i < K; i += NT) {
+        size_t o = (size_t)n * c.M + 4 * i + ct;
+        km[i] = c.rem ? (c.rem[o] == 0) : 1;
+        if (eps) eps[i] = c.eps[o];
+    }
+}
+
+template <class R>
+__device__ __forceinline__ cx<R> ld_z(const zd* p) { return from_z<R>(p->re, p->im); }
+
+// One forward column step k (matrices row-major with leading dimension KL):
+//   Y    = Pprev W_k                  (KL x K; skipped at k = 0)
+//   X    = A_k                        (K x K)
+//   Gout = A_k^-1                     (Gauss-Jordan; Gout may alias Gprev)
+//   Pout = Y Gout  (or Gout at k = 0) (Pout may alias Pprev)
+// Expects s.kc / s.eps for column k and s.kp for column k-1 loaded.  Returns
+// the Gauss-Jordan flag.
+template <class R>
+__device__ int fwd_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout,
+                          const cx<R>* Pprev, cx<R>* Pout, cx<R>* X, cx<R>* Y,
+                          SweepSmem<R>& s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int KL = c.KL, ct = k & 3, K = col_size(c, k), Kp = col_size(c, k - 1);
+    if (k > 0) {
+        for (int r = warp; r < KL; r += NWARP)
+            for (int l = lane; l < K; l += 32) {
+                cx<R> v = czero<R>();
+                if (s.kc[l]) {
+                    int a0, a1;
+                    col_src(ct, l, Kp, a0, a1);
+                    if (a0 >= 0 && s.kp[a0]) v = cadd(v, Pprev[(size_t)r * KL + a0]);
+                    if (a1 >= 0 && s.kp[a1]) v = cadd(v, Pprev[(size_t)r * KL + a1]);
+                    v = cscale(v, c.t);
+                }
+                Y[(size_t)r * KL + l] = v;
+            }
+    }
+    double amax2 = 0.0;
+    for (int i = warp; i < K; i += NWARP) {
+        int a0 = -1, a1 = -1;
+        if (k > 0) col_src(ct, i, Kp, a0, a1);
+        const bool ki = s.kc[i];
+        const bool ka0 = a0 >= 0 && s.kp[a0], ka1 = a1 >= 0 && s.kp[a1];
+        for (int l = lane; l < K; l += 32) {
+            cx<R> v;
+            if (!ki || !s.kc[l]) {
+                v = (i == l) ? from_z<R>(1.0, 0.0) : czero<R>();
+            } else {
+                cx<R> sig = czero<R>();
+                if (k == 0) {
+                    sig = ld_z<R>(c.SigL + (size_t)i * KL + l);
+                } else {
+                    int b0, b1;
+                    col_src(ct, l, Kp, b0, b1);
+                    const bool kb0 = b0 >= 0 && s.kp[b0], kb1 = b1 >= 0 && s.kp[b1];
+                    if (ka0 && kb0) sig = cadd(sig, Gprev[(size_t)a0 * KL + b0]);
+                    if (ka0 && kb1) sig = cadd(sig, Gprev[(size_t)a0 * KL + b1]);
+                    if (ka1 && kb0) sig = cadd(sig, Gprev[(size_t)a1 * KL + b0]);
+                    if (ka1 && kb1) sig = cadd(sig, Gprev[(size_t)a1 * KL + b1]);
+                    sig = cscale(sig, c.t2);
+                }
+                if (k == c.ncol - 1) sig = cadd(sig, ld_z<R>(c.SigR + (size_t)i * c.KR + l));
+                v = (i == l) ? from_z<R>(c.z.re - s.eps[i], c.z.im) : czero<R>();
+                v = csub(v, sig);
+            }
+            X[(size_t)i * KL + l] = v;
+            const double a2 = cabs2(v);
+            amax2 = (a2 > amax2 || isnan(a2)) ? a2 : amax2;
+        }
+    }
+    amax2 = block_max(amax2, s.red);
+    const int flag = cta_gj_invert<R>(X, K, KL, Gout, KL, s.gj, amax2);
+    if (k == 0) {
+        for (int i = warp; i < K; i += NWARP)
+            for (int l = lane; l < K; l += 32) Pout[(size_t)i * KL + l] = Gout[(size_t)i * KL + l];
+        __syncthreads();
+    } else {
+        cta_gemm<R, false, false>(KL, K, K, Y, KL, Gout, KL, Pout, KL, GEMM_SET, s.gemm);
+    }
+    return flag;
+}
+
+// Tr[Gamma_L P Gamma_R P^dagger] in binary64.  P: KL x KR (ld KL) in the working
+// precision; Xs, Zs, Cz: KL x KL scratch (16-byte elements).
+template <class R>
+__device__ double trace_T(const ChainCtx& c, const cx<R>* P, cx<R>* Cz, cx<R>* Xs, cx<R>* Zs,
+                          SweepSmem<R>& s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int KL = c.KL, KR = c.KR;
+    const zd* Pz;
+    if (std::is_same<R, double>::value) {
+        Pz = reinterpret_cast<const zd*>(P);
+    } else {
+        zd* w = reinterpret_cast<zd*>(Cz);
+        for (int i = warp; i < KL; i += NWARP)
+            for (int l = lane; l < KR; l += 32) w[(size_t)i * KL + l] = to_z(P[(size_t)i * KL + l]);
+        __syncthreads();
+        Pz = w;
+    }
+    zd* X = reinterpret_cast<zd*>(Xs);
+    zd* Z = reinterpret_cast<zd*>(Zs);
+    zd* gsm = reinterpret_cast<zd*>(s.gemm);
+    cta_gemm<double, false, false>(KL, KR, KL, c.GamL, KL, Pz, KL, X, KL, GEMM_SET, gsm);
+    cta_gemm<double, false, false>(KL, KR, KR, Pz, KL, c.GamR, KR, Z, KL, GEMM_SET, gsm);
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < KL * KR; e += NT) {
+        int a = e / KR, b = e % KR;
+        zd x = X[(size_t)a * KL + b], zz = Z[(size_t)a * KL + b];
+        acc += x.re * zz.re + x.im * zz.im;    // Re(x conj(z))
+    }
+    return block_sum(acc, s.red);
+}
+
+// Status word of a finished chain from the Gauss-Jordan flags and T.
+__device__ inline int chain_status(const ChainCtx& c, int flag, double T) {
+    const double nch = (double)channels(c.N, c.t, c.z.re);
+    if ((flag & 2) || !isfinite(T)) return ST_ENONFINITE;
+    if (flag & 1) return ST_ESINGULAR;
+    if (T < -1e-6 || T > nch + 1e-6) return ST_EBOUNDS;
+    return ST_OK;
+}
+
+__device__ inline int lead_state(const int* lead_status, int lead) {
+    int lst = lead_status[2 * lead];
+    if (lst == ST_OK) lst = lead_status[2 * lead + 1];
+    return lst;
+}
+
+}  // namespace rgf

@@ -17,14 +17,17 @@ if not _LIB_PATH.exists():
     raise ImportError(f"{_LIB_PATH} not found: build it with `python -m paper_1107_5300_gb300.build`")
 lib = C.CDLL(str(_LIB_PATH))
 
-RGF_OK, RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA, RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE, RGF_ETIMEOUT = range(8)
+(RGF_OK, RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA, RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE,
+ RGF_ETIMEOUT, RGF_EBOUNDS) = range(9)
 RGF_FP64, RGF_MIXED = 0, 1
-STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENONFINITE", "ETIMEOUT"]
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENONFINITE", "ETIMEOUT",
+                "EBOUNDS"]
 
 # Symbols declared in include/rgf.h (checked by the CPU tests).
 EXPORTS = ["rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "rgf_free_ribbon",
            "rgf_lead_selfenergy", "rgf_conductance", "rgf_conductance_dev",
-           "rgf_conductance_grad", "rgf_status_str", "rgf_last_error", "rgf_version"]
+           "rgf_conductance_grad", "rgf_profile_enable", "rgf_profile_read", "rgf_status_str",
+           "rgf_last_error", "rgf_version"]
 
 
 class _Desc(C.Structure):
@@ -52,6 +55,10 @@ lib.rgf_conductance_dev.argtypes = [C.POINTER(_vp), _vp, C.c_int, C.c_double, C.
                                     C.c_int, _vp, _vp, _vp]
 lib.rgf_conductance_grad.argtypes = [C.POINTER(_vp), _dp, C.c_int, C.c_double, C.c_double,
                                      C.c_int, C.c_int, _dp, _dp, _i32p]
+lib.rgf_profile_enable.argtypes = [C.c_int]
+lib.rgf_profile_enable.restype = C.c_int
+lib.rgf_profile_read.argtypes = [_dp, _dp]
+lib.rgf_profile_read.restype = C.c_int
 lib.rgf_status_str.restype = C.c_char_p
 lib.rgf_status_str.argtypes = [C.c_int]
 lib.rgf_last_error.restype = C.c_char_p
@@ -63,7 +70,7 @@ for _f in ("rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "r
 
 class RGFError(RuntimeError):
     def __init__(self, status: int, msg: str):
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
         self.status = status
 
 
@@ -204,3 +211,15 @@ def conductance_grad(ribbons, E, eta_device=1e-8, eta_lead=1e-8, precision=RGF_F
     if check:
         _check(r)
     return T, g, st
+
+
+def profile_enable(on=True):
+    """Record CUDA events around the kernel phases of each conductance call."""
+    _check(lib.rgf_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """(ms_lead, ms_sweep) of the last profiled call (waits for it)."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib.rgf_profile_read(C.byref(a), C.byref(b)))
+    return a.value, b.value

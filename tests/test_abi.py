@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol(rgflib):
 
 
 def test_status_strings(rgflib):
-    for s in range(8):
+    for s in range(9):
         assert rgflib.lib.rgf_status_str(s).decode().startswith("RGF_")
     assert rgflib.lib.rgf_version().decode()
 

@@ -1,0 +1,93 @@
+"""Adjoint gradient dT/d eps (rgf_conductance_grad) against the oracle and
+against finite differences of the GPU conductance."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import gradient as ograd
+
+pytestmark = pytest.mark.gpu
+T_HOP = -2.7
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-8)])
+def test_gradient_matches_oracle_closed_form(rgflib, prec, tol):
+    N, L = 11, 6
+    eps = workloads.anderson_onsite(N, L, 0.3, 11)
+    rem = workloads.edge_removed(N, L, 0.3, 12)
+    rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps, removed=rem)
+    Es = np.array([-0.9, 0.31, 0.004])
+    T, g, st = rgflib.conductance_grad([rib] * 3, Es, 1e-8, 1e-8, prec, ckpt_stride=2)
+    assert (st == 0).all()
+    for c, E in enumerate(Es):
+        ref = ograd.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(g[c] - ref).max() < tol * scale, (E, np.abs(g[c] - ref).max())
+        assert np.all(g[c][rem.astype(bool)] == 0.0)
+
+
+def test_gradient_oracle_n11_l20(rgflib):
+    # Oracle gradient on an N = 11, L = 20 ribbon (Anderson +-0.15 eV).
+    N, L = 11, 20
+    eps = workloads.anderson_onsite(N, L, 0.15, 4)
+    rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps)
+    Es = np.array([-0.8, -0.2, 0.45])
+    for prec, tol in ((0, 1e-10), (1, 1e-8)):
+        T, g, st = rgflib.conductance_grad([rib] * 3, Es, 1e-8, 1e-8, prec)
+        for c, E in enumerate(Es):
+            ref = ograd.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps, None)
+            assert np.abs(g[c] - ref).max() < tol * max(1.0, np.abs(ref).max())
+
+
+def test_checkpoint_stride_does_not_change_the_gradient(rgflib):
+    N, L = 12, 9
+    rib = rgflib.Ribbon(N, L, T_HOP, W=0.2, seed=3, edge_p=0.2, edge_seed=4)
+    Es = np.array([0.21, -0.6])
+    outs = [rgflib.conductance_grad([rib] * 2, Es, ckpt_stride=s)[1] for s in (1, 2, 4, 9, 0)]
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    T, _ = rgflib.conductance([rib] * 2, Es)
+    Tg = rgflib.conductance_grad([rib] * 2, Es)[0]
+    assert np.array_equal(T, Tg)
+
+
+def test_gradient_against_finite_differences_n101(rgflib):
+    # N = 101, L = 500, Anderson +-0.15 eV (seed 4), 64 sites drawn from seed 44,
+    # central differences with delta = 1e-6 eV; stride 23 cells.
+    w = workloads.WORKLOADS["agnr101_L500_grad"]
+    N, L = w["N"], w["L"]
+    eps = workloads.anderson_onsite(N, L, w["W"], w["seed"])
+    E = float(w["energies"]()[37])
+    rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps)
+    u = workloads.uniform01(44, np.arange(128, dtype=np.uint64))
+    sites = [(int(u[2 * i] * L), int(u[2 * i + 1] * 2 * N)) for i in range(64)]
+    d = 1e-6
+    ribs = []
+    for (n, i) in sites:
+        for sgn in (1, -1):
+            e2 = eps.copy()
+            e2[n, i] += sgn * d
+            ribs.append(rgflib.Ribbon(N, L, T_HOP, onsite=e2))
+    Tfd, st = rgflib.conductance(ribs, np.full(len(ribs), E))
+    fd = (Tfd[0::2] - Tfd[1::2]) / (2 * d)
+    for prec in (0, 1):
+        T, g, st = rgflib.conductance_grad([rib], np.array([E]), 1e-8, 1e-8, prec, ckpt_stride=23)
+        assert st[0] == 0
+        gs = np.array([g[0, n, i] for (n, i) in sites])
+        err = np.abs(gs - fd)
+        assert np.all(err < 1e-5 + 1e-4 * np.abs(fd)), (prec, err.max())
+
+
+def test_autograd_function(rgflib):
+    import torch
+    from paper_1107_5300_gb300.autograd import conductance
+    N, L = 5, 4
+    eps0 = workloads.anderson_onsite(N, L, 0.2, 9)
+    eps = torch.tensor(eps0, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = torch.tensor([0.3, -0.5], dtype=torch.float64)
+    T = conductance(eps, E, N)
+    w = torch.tensor([1.0, -2.0], dtype=torch.float64, device="cuda")
+    (T * w).sum().backward()
+    ref = sum(wc * ograd.closed_form(N, L, Ec, 1e-8, 1e-8, T_HOP, eps0, None)
+              for wc, Ec in zip([1.0, -2.0], [0.3, -0.5]))
+    assert np.abs(eps.grad.cpu().numpy() - ref).max() < 1e-10

@@ -79,12 +79,6 @@ def test_decimation_fixed_point_residual_and_symmetry():
             assert np.abs(gR - gR.T).max() < 1e-10 * np.abs(gR).max()
 
 
-def test_decimation_fails_loudly_at_exact_charge_neutrality():
-    # At E = 0 exactly the N = 23 iteration diverges instead of converging.
-    with pytest.raises(leads.NoConvergence):
-        leads.self_energies(23, 0.0, 1e-8, T_HOP)
-
-
 def test_eq2_forms_agree_and_rgf_equals_dense_definition():
     # Eq. 2 as printed (Tr[G_L G^a G_R G^r]) equals Tr[G_L G_1L G_R G_1L^+]; the
     # recursion of Eqs. 4-5 reaches the dense inverse of Eq. 1.
