@@ -164,6 +164,38 @@ rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, i
                                 int32_t* chain_status);
 
 /*
+ * Allocation-free variant of rgf_conductance_dev (no counterpart in the paper).
+ *
+ * For callers that may not allocate device memory: e.g. a host application
+ * that has reserved the device memory for its own pool and forbids further
+ * cudaMalloc, a plugin whose host only hands it pre-allocated buffers, or a
+ * loop that must not trigger the implicit device synchronisation of
+ * cudaMalloc / cudaFree.  This call performs no cudaMalloc, cudaFree or other
+ * allocating call: its scratch (chain descriptors, lead workspace and output,
+ * sweep workspace) lives in one fixed 64 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * One ribbon of N dimer lines and L cells, given as device arrays
+ * onsite_dev [L][2N] (binary64) and removed_dev [L][2N] (uint8, or NULL),
+ * evaluated at nE energies E_dev [nE] (device).  Outputs on the device:
+ * T_dev [nE], status_dev [nE] (int32, or NULL), as rgf_conductance_dev.
+ * Asynchronous on `stream`; results are valid once the stream has passed the
+ * call.  Returns RGF_EINVAL, with a message naming the limit, when the scratch
+ * the call needs exceeds 64 MiB (about 29 energies at N = 245, more at smaller
+ * N); split the energies over several calls then.
+ *
+ * The array is shared by all calls and keeps the last call's contents; two
+ * calls whose GPU work overlaps (different streams, or a second call before
+ * the first has finished) race on it.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.
+ */
+rgf_status rgf_conductance_noalloc(int N, int L, double t, const double* onsite_dev,
+                                   const uint8_t* removed_dev, const double* E_dev, int nE,
+                                   double eta_device, double eta_lead, int precision,
+                                   void* stream, double* T_dev, int32_t* status_dev);
+
+/*
  * Diagnostics (no counterpart in the paper).  When enabled, every
  * rgf_conductance* call records CUDA events on its stream around its two
  * kernel phases: lead decimation and slice sweep (with the trace).

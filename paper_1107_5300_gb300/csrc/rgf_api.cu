@@ -293,6 +293,11 @@ struct StreamGuard {
 
 }  // namespace
 
+namespace rgf {
+// Lets other translation units of the library report through rgf_last_error.
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace rgf
+
 extern "C" {
 
 const char* rgf_version(void) { return "rgf-gb300 0.1"; }

@@ -1,0 +1,162 @@
+// rgf_noalloc.cu -- rgf_conductance_noalloc: the conductance of one ribbon at
+// several energies, with every scratch buffer taken from a fixed, statically
+// sized device array instead of cudaMalloc.
+//
+// Who needs it: callers that may not allocate device memory themselves, for
+// example a host application that has already reserved the device memory for
+// its own pool and forbids further cudaMalloc, a plugin whose host hands it
+// only pre-allocated buffers, or a loop that must not trigger the implicit
+// device synchronisation that cudaMalloc / cudaFree can cause.  They pass
+// their inputs and outputs as device pointers; everything else lives in the
+// array below.
+//
+// The array (kScratchBytes, 64 MiB) is part of the library image: every GPU
+// that loads the library holds it until the process exits.  All calls share
+// it, and it keeps the previous call's contents; calls whose work overlaps on
+// the GPU (concurrent streams, or a second call before the first has finished
+// on another stream) race on it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rgf.h"
+#include "rgf_internal.h"
+
+namespace rgf {
+void set_last_error(const std::string& msg);
+}
+
+namespace {
+
+constexpr size_t kScratchBytes = 64ull << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+rgf_status nfail(rgf_status st, const std::string& msg) {
+    rgf::set_last_error("rgf_conductance_noalloc: " + msg);
+    return st;
+}
+
+// Device address of g_scratch on the current device; set up once per device.
+cudaError_t scratch_address(int dev, void** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+__global__ void noalloc_fill_energy(rgf::ChainDev* chains, rgf::LeadDev* leads, const double* E,
+                                    int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        chains[i].E = E[i];
+        leads[i].E = E[i];
+    }
+}
+
+}  // namespace
+
+extern "C" rgf_status rgf_conductance_noalloc(int N, int L, double t, const double* onsite_dev,
+                                              const uint8_t* removed_dev, const double* E_dev,
+                                              int nE, double eta_device, double eta_lead,
+                                              int precision, void* stream, double* T_dev,
+                                              int32_t* status_dev) {
+    if (nE < 0) return nfail(RGF_EINVAL, "nE < 0");
+    if (nE == 0) return RGF_OK;
+    if (N < 2 || N > 2047 || L < 1 || !std::isfinite(t) || t == 0.0)
+        return nfail(RGF_EINVAL, "bad N, L or t");
+    if (!onsite_dev || !E_dev || !T_dev) return nfail(RGF_EINVAL, "NULL device pointer");
+    if (precision != RGF_FP64 && precision != RGF_MIXED) return nfail(RGF_EINVAL, "unknown precision");
+    if (!(eta_device >= 0.0) || !(eta_lead > 0.0) || !std::isfinite(eta_device) ||
+        !std::isfinite(eta_lead))
+        return nfail(RGF_EINVAL, "eta_device must be >= 0 and eta_lead > 0 (finite)");
+
+    // Scratch layout (each part 256-byte aligned): descriptors | lead status |
+    // lead workspace | lead output | sweep workspace.
+    const size_t n = (size_t)nE;
+    const size_t b_chain = n * sizeof(rgf::ChainDev), b_lead = n * sizeof(rgf::LeadDev);
+    const size_t b_order = n * sizeof(int);
+    const size_t o_chain = 0, o_lead = up256(o_chain + b_chain), o_order = up256(o_lead + b_lead);
+    const size_t o_lst = up256(o_order + b_order);
+    const size_t o_lws = up256(o_lst + 2 * n * sizeof(int));
+    const size_t o_lout = up256(o_lws + n * rgf::lead_ws_elems(N) * 16);
+    const size_t o_ws = up256(o_lout + n * rgf::lead_out_elems(N) * 16);
+    const size_t total = o_ws + n * rgf::sweep_ws_elems(N) * 16;
+    if (total > kScratchBytes)
+        return nfail(RGF_EINVAL, "needs " + std::to_string(total) + " bytes of scratch for N = " +
+                                     std::to_string(N) + ", " + std::to_string(nE) +
+                                     " energies; the fixed limit is " +
+                                     std::to_string(kScratchBytes) + " bytes (64 MiB): use fewer "
+                                     "energies per call or rgf_conductance_dev");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return nfail(RGF_EINVAL, "device ordinal out of range");
+    void* base = nullptr;
+    e = scratch_address(dev, &base);
+    if (e != cudaSuccess)
+        return nfail(RGF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    unsigned char* sp = static_cast<unsigned char*>(base);
+
+    std::vector<rgf::ChainDev> chains(n);
+    std::vector<rgf::LeadDev> leads(n);
+    std::vector<int> order(n);
+    for (size_t c = 0; c < n; ++c) {
+        rgf::ChainDev& ch = chains[c];
+        ch.eps = onsite_dev;
+        ch.rem = removed_dev;
+        ch.N = N;
+        ch.L = L;
+        ch.t = t;
+        ch.E = 0.0;
+        ch.lead = (int)c;
+        ch.ws_off = c * rgf::sweep_ws_elems(N);
+        ch.grad_off = 0;
+        rgf::LeadDev& ld = leads[c];
+        ld.N = N;
+        ld.t = t;
+        ld.E = 0.0;
+        ld.off = c * rgf::lead_out_elems(N);
+        ld.ws_off = c * rgf::lead_ws_elems(N);
+        order[c] = (int)c;
+    }
+    std::vector<unsigned char> hdr(o_lst);
+    std::memcpy(hdr.data() + o_chain, chains.data(), b_chain);
+    std::memcpy(hdr.data() + o_lead, leads.data(), b_lead);
+    std::memcpy(hdr.data() + o_order, order.data(), b_order);
+    cudaStream_t st = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(sp, hdr.data(), hdr.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
+    // The lead status words are always written by the lead kernel; clear them
+    // anyway so that nothing of a previous call can be read back.
+    e = cudaMemsetAsync(sp + o_lst, 0, 2 * n * sizeof(int), st);
+    if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
+    auto* dchains = reinterpret_cast<rgf::ChainDev*>(sp + o_chain);
+    auto* dleads = reinterpret_cast<rgf::LeadDev*>(sp + o_lead);
+    auto* dorder = reinterpret_cast<int*>(sp + o_order);
+    auto* dlst = reinterpret_cast<int*>(sp + o_lst);
+    noalloc_fill_energy<<<(nE + 255) / 256, 256, 0, st>>>(dchains, dleads, E_dev, nE);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
+    const int Kmax = rgf::col_KL(N);
+    e = rgf::launch_lead(dleads, nE, Kmax, eta_lead, sp + o_lws, sp + o_lout, dlst, nullptr, st);
+    if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
+    e = rgf::launch_sweep(precision, dchains, dorder, nE, Kmax, eta_device, sp + o_lout, dlst,
+                          dleads, sp + o_ws, T_dev, status_dev, st);
+    if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
+    return RGF_OK;
+}

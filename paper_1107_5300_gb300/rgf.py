@@ -26,7 +26,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENON
 # Symbols declared in include/rgf.h (checked by the CPU tests).
 EXPORTS = ["rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "rgf_free_ribbon",
            "rgf_lead_selfenergy", "rgf_conductance", "rgf_conductance_dev",
-           "rgf_conductance_grad", "rgf_profile_enable", "rgf_profile_read", "rgf_status_str",
+           "rgf_conductance_grad", "rgf_conductance_noalloc", "rgf_profile_enable",
+           "rgf_profile_read", "rgf_status_str",
            "rgf_last_error", "rgf_version"]
 
 
@@ -55,6 +56,9 @@ lib.rgf_conductance_dev.argtypes = [C.POINTER(_vp), _vp, C.c_int, C.c_double, C.
                                     C.c_int, _vp, _vp, _vp]
 lib.rgf_conductance_grad.argtypes = [C.POINTER(_vp), _dp, C.c_int, C.c_double, C.c_double,
                                      C.c_int, C.c_int, _dp, _dp, _i32p]
+lib.rgf_conductance_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, C.c_int,
+                                        C.c_double, C.c_double, C.c_int, _vp, _vp, _vp]
+lib.rgf_conductance_noalloc.restype = C.c_int
 lib.rgf_profile_enable.argtypes = [C.c_int]
 lib.rgf_profile_enable.restype = C.c_int
 lib.rgf_profile_read.argtypes = [_dp, _dp]
@@ -223,3 +227,15 @@ def profile_read():
     a, b = C.c_double(), C.c_double()
     _check(lib.rgf_profile_read(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def conductance_noalloc(N, L, t, onsite_ptr, removed_ptr, E_ptr, n, T_ptr, status_ptr=0,
+                        eta_device=1e-8, eta_lead=1e-8, precision=RGF_FP64, stream=0, check=True):
+    """Allocation-free call (device pointers in and out; scratch in the library's fixed array)."""
+    st = lib.rgf_conductance_noalloc(int(N), int(L), float(t), _vp(onsite_ptr),
+                                     _vp(removed_ptr) if removed_ptr else None, _vp(E_ptr), int(n),
+                                     float(eta_device), float(eta_lead), int(precision),
+                                     _vp(stream), _vp(T_ptr), _vp(status_ptr) if status_ptr else None)
+    if check:
+        _check(st)
+    return st
