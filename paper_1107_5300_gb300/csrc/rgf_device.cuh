@@ -127,99 +127,159 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
 }
 
 // ---------------------------------------------------------------------------
-// Gauss-Jordan inverse with partial (row) pivoting.
+// Blocked Gauss-Jordan inverse with partial (row) pivoting.
 //   A (K x K, leading dim lda) is destroyed; A^-1 is written to G (ldg).
-//   Pivot j: pick the row p >= j with the largest |A[p][j]|, swap rows j and p,
-//   scale the pivot row by 1/A[j][j] (kept in its column j), eliminate column
-//   j from every other row (storing -A[i][j]/A[j][j] in column j).  The row
-//   swaps are undone at the end by a column permutation applied while copying
-//   into G.  The pivot reciprocal is formed in binary64.
+//   Pivots are taken in blocks of b columns.  For a block starting at j0 the
+//   K x b panel A[:, j0:j0+b] is copied to shared memory and reduced there by
+//   the unblocked in-place steps (pick the row p >= j with the largest
+//   |A[p][j]|, swap rows j and p -- in the panel and in the rest of the matrix
+//   --, scale the pivot row by 1/A[j][j] keeping 1/A[j][j] in column j,
+//   eliminate column j from every other row keeping -A[i][j]/A[j][j] in
+//   column j).  The reduced panel is then exactly the block's accumulated row
+//   transform T restricted to its pivot columns (T is the identity outside
+//   them), so every other column is updated in one rank-b step
+//       A[i][l] <- [i not a pivot row] A[i][l] + sum_jj Panel[i][jj] A[j0+jj][l],
+//   reading and writing each element once per block instead of once per pivot.
+//   The row swaps are undone at the end by a column permutation applied while
+//   copying into G.  Pivot reciprocals are formed in binary64.
 // Returns a flag: bit 0 = zero pivot, or a pivot below 64 u sqrt(amax2) with
 // amax2 = max |A_ij|^2 supplied by the caller (0 disables the test); bit 1 =
 // non-finite pivot.
 // ---------------------------------------------------------------------------
 template <class R>
 struct GJSmem {
-    cx<R>* rowbuf;   // [Kmax]
-    cx<R>* colbuf;   // [Kmax]
-    cx<R>* colval;   // [Kmax] next pivot column (fresh values)
-    double* colabs;  // [Kmax]
+    cx<R>* rowbuf;   // [bmax]   scaled pivot row of the panel
+    cx<R>* colbuf;   // [Kmax]   pivot column of the panel
+    cx<R>* panel;    // [Kmax][bmax]
+    cx<R>* prow;     // [bmax][Kmax] pivot rows outside the panel
     int* perm;       // [Kmax]
     int* idx;        // [Kmax]
     int* ctl;        // [4]: pivot row, flag
     zd* inv;         // [1]
+    int bmax;        // panel width
 };
 
 template <class R>
 __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __restrict__ G, int ldg,
                              GJSmem<R> s, double amax2 = 0.0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < K; i += NT) {
-        cx<R> v = A[(size_t)i * lda];
-        s.colval[i] = v;
-        s.colabs[i] = cabs2(v);
-    }
-    if (tid == 0) s.ctl[1] = 0;
-    // pivots below 64 u max|A| mean a numerically singular slice (bit 0)
+    const int bm = s.bmax;
+    cx<R>* Pn = s.panel;
+    cx<R>* MR = s.prow;
     const double tiny2 = amax2 * (64.0 * Unit<R>::u) * (64.0 * Unit<R>::u);
-    __syncthreads();
-    for (int j = 0; j < K; ++j) {
-        if (warp == 0) {
-            double best = -1.0;
-            int bi = j;
-            for (int i = j + lane; i < K; i += 32) {
-                double v = s.colabs[i];
-                if (v > best || isnan(v)) { best = isnan(v) ? INFINITY : v; bi = i; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (lane == 0) {
-                zd pz = to_z(s.colval[bi]);
-                double d = pz.re * pz.re + pz.im * pz.im;
-                int flag = s.ctl[1];
-                if (!isfinite(d)) { flag |= 2; d = 1.0; pz = {1.0, 0.0}; }
-                else if (!(d > 0.0)) { flag |= 1; d = 1.0; pz = {1.0, 0.0}; }
-                else if (d < tiny2) { flag |= 1; }
-                s.ctl[1] = flag;
-                s.ctl[0] = bi;
-                s.perm[j] = bi;
-                *s.inv = zd{pz.re / d, -pz.im / d};
-            }
+    if (tid == 0) s.ctl[1] = 0;
+    for (int j0 = 0; j0 < K; j0 += bm) {
+        const int bb = min(bm, K - j0);
+        for (int e = tid; e < K * bb; e += NT) {
+            int i = e / bb, jj = e % bb;
+            Pn[i * bm + jj] = A[(size_t)i * lda + j0 + jj];
         }
         __syncthreads();
-        const int p = s.ctl[0];
-        const zd invz = *s.inv;
-        const cx<R> invR = from_z<R>(invz.re, invz.im);
-        for (int k = tid; k < K; k += NT) {
-            cx<R> rb = A[(size_t)p * lda + k];
-            if (p != j) A[(size_t)p * lda + k] = A[(size_t)j * lda + k];
-            s.rowbuf[k] = (k == j) ? invR : cmul(rb, invR);
-        }
-        for (int i = tid; i < K; i += NT) {
-            cx<R> v = czero<R>();
-            if (i != j) v = (i == p) ? A[(size_t)j * lda + j] : A[(size_t)i * lda + j];
-            s.colbuf[i] = v;
-        }
-        __syncthreads();
-        for (int i = warp; i < K; i += NWARP) {
-            cx<R>* row = A + (size_t)i * lda;
-            if (i == j) {
-                for (int k = lane; k < K; k += 32) row[k] = s.rowbuf[k];
-            } else {
-                const cx<R> ci = s.colbuf[i];
-                for (int k = lane; k < K; k += 32) {
-                    cx<R> a = (k == j) ? czero<R>() : row[k];
-                    a = cmac(a, ci, s.rowbuf[k], true);
-                    row[k] = a;
-                    if (k == j + 1 && i > j) {
-                        s.colval[i] = a;
-                        s.colabs[i] = cabs2(a);
-                    }
+        for (int jj = 0; jj < bb; ++jj) {
+            const int j = j0 + jj;
+            if (warp == 0) {
+                double best = -1.0;
+                int bi = j;
+                for (int i = j + lane; i < K; i += 32) {
+                    double v = cabs2(Pn[i * bm + jj]);
+                    if (v > best || isnan(v)) { best = isnan(v) ? INFINITY : v; bi = i; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                if (lane == 0) {
+                    zd pz = to_z(Pn[bi * bm + jj]);
+                    double d = pz.re * pz.re + pz.im * pz.im;
+                    int flag = s.ctl[1];
+                    if (!isfinite(d)) { flag |= 2; d = 1.0; pz = {1.0, 0.0}; }
+                    else if (!(d > 0.0)) { flag |= 1; d = 1.0; pz = {1.0, 0.0}; }
+                    else if (d < tiny2) { flag |= 1; }
+                    s.ctl[1] = flag;
+                    s.ctl[0] = bi;
+                    s.perm[j] = bi;
+                    *s.inv = zd{pz.re / d, -pz.im / d};
                 }
             }
+            __syncthreads();
+            const int p = s.ctl[0];
+            if (p != j) {
+                for (int l = tid; l < K; l += NT) {
+                    if (l >= j0 && l < j0 + bb) {
+                        int ll = l - j0;
+                        cx<R> a = Pn[j * bm + ll];
+                        Pn[j * bm + ll] = Pn[p * bm + ll];
+                        Pn[p * bm + ll] = a;
+                    } else {
+                        cx<R> a = A[(size_t)j * lda + l];
+                        A[(size_t)j * lda + l] = A[(size_t)p * lda + l];
+                        A[(size_t)p * lda + l] = a;
+                    }
+                }
+                __syncthreads();
+            }
+            const zd invz = *s.inv;
+            const cx<R> invR = from_z<R>(invz.re, invz.im);
+            for (int l = tid; l < bb; l += NT)
+                s.rowbuf[l] = (l == jj) ? invR : cmul(Pn[j * bm + l], invR);
+            for (int i = tid; i < K; i += NT) s.colbuf[i] = (i == j) ? czero<R>() : Pn[i * bm + jj];
+            __syncthreads();
+            for (int e = tid; e < K * bb; e += NT) {
+                const int i = e / bb, l = e % bb;
+                if (i == j) {
+                    Pn[i * bm + l] = s.rowbuf[l];
+                } else {
+                    cx<R> a = (l == jj) ? czero<R>() : Pn[i * bm + l];
+                    Pn[i * bm + l] = cmac(a, s.colbuf[i], s.rowbuf[l], true);
+                }
+            }
+            __syncthreads();
+        }
+        // Pivot rows outside the panel, then the rank-bb update of all other columns.
+        const int Kc = K - bb;   // columns outside the panel
+        for (int e = tid; e < bb * Kc; e += NT) {
+            int jj = e / Kc, c = e % Kc;
+            int l = c < j0 ? c : c + bb;
+            MR[jj * K + c] = A[(size_t)(j0 + jj) * lda + l];
+        }
+        __syncthreads();
+        const int Kh = (K + 1) >> 1, Ch = (Kc + 1) >> 1;
+        for (int tt = tid; tt < Kh * Ch; tt += NT) {
+            const int i0 = 2 * (tt / Ch), c0 = 2 * (tt % Ch);
+            const bool ok_i1 = i0 + 1 < K, ok_c1 = c0 + 1 < Kc;
+            const int l0 = c0 < j0 ? c0 : c0 + bb;
+            const int l1 = (c0 + 1) < j0 ? c0 + 1 : c0 + 1 + bb;
+            const bool r0 = i0 >= j0 && i0 < j0 + bb, r1 = (i0 + 1) >= j0 && (i0 + 1) < j0 + bb;
+            cx<R> a00 = czero<R>(), a01 = czero<R>(), a10 = czero<R>(), a11 = czero<R>();
+            if (!r0) {
+                a00 = A[(size_t)i0 * lda + l0];
+                if (ok_c1) a01 = A[(size_t)i0 * lda + l1];
+            }
+            if (ok_i1 && !r1) {
+                a10 = A[(size_t)(i0 + 1) * lda + l0];
+                if (ok_c1) a11 = A[(size_t)(i0 + 1) * lda + l1];
+            }
+            for (int jj = 0; jj < bb; ++jj) {
+                const cx<R> p0 = Pn[i0 * bm + jj];
+                const cx<R> p1 = ok_i1 ? Pn[(i0 + 1) * bm + jj] : czero<R>();
+                const cx<R> m0 = MR[jj * K + c0];
+                const cx<R> m1 = ok_c1 ? MR[jj * K + c0 + 1] : czero<R>();
+                a00 = cmac(a00, p0, m0, false);
+                a01 = cmac(a01, p0, m1, false);
+                a10 = cmac(a10, p1, m0, false);
+                a11 = cmac(a11, p1, m1, false);
+            }
+            A[(size_t)i0 * lda + l0] = a00;
+            if (ok_c1) A[(size_t)i0 * lda + l1] = a01;
+            if (ok_i1) {
+                A[(size_t)(i0 + 1) * lda + l0] = a10;
+                if (ok_c1) A[(size_t)(i0 + 1) * lda + l1] = a11;
+            }
+        }
+        for (int e = tid; e < K * bb; e += NT) {
+            int i = e / bb, jj = e % bb;
+            A[(size_t)i * lda + j0 + jj] = Pn[i * bm + jj];
         }
         __syncthreads();
     }

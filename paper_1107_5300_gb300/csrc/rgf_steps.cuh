@@ -23,17 +23,28 @@ struct SweepSmem {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Panel width of the blocked Gauss-Jordan for a largest column size Kmax:
+// the widest of 16, 8, 4, 2 whose panel and pivot-row buffers fit next to the
+// rest of the shared memory.
+__host__ __device__ inline int gj_panel_width(int Kmax) {
+    int b = 16;
+    while (b > 2 && (size_t)2 * Kmax * b * 16 + (size_t)Kmax * 64 + 20000 > 220 * 1024) b >>= 1;
+    return b;
+}
+
 template <class R>
 __device__ SweepSmem<R> carve(unsigned char* base, int Kmax) {
     SweepSmem<R> s;
     size_t o = 0;
     auto take = [&](size_t bytes) { unsigned char* p = base + o; o += align16(bytes); return p; };
-    s.gj.rowbuf = (cx<R>*)take((size_t)Kmax * 16);
+    const int bm = gj_panel_width(Kmax);
+    s.gj.bmax = bm;
+    s.gj.panel = (cx<R>*)take((size_t)Kmax * bm * 16);
+    s.gj.prow = (cx<R>*)take((size_t)Kmax * bm * 16);
+    s.gj.rowbuf = (cx<R>*)take((size_t)bm * 16);
     s.gj.colbuf = (cx<R>*)take((size_t)Kmax * 16);
-    s.gj.colval = (cx<R>*)take((size_t)Kmax * 16);
     s.gemm = (cx<R>*)take(2 * 8 * 64 * 16);
     s.gj.inv = (zd*)take(16);
-    s.gj.colabs = (double*)take((size_t)Kmax * 8);
     s.eps = (double*)take((size_t)Kmax * 8);
     s.red = (double*)take(NWARP * 8);
     s.gj.perm = (int*)take((size_t)Kmax * 4);

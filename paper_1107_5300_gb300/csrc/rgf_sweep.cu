@@ -25,15 +25,18 @@
 namespace rgf {
 
 size_t sweep_smem_bytes(int Kmax) {
+    const int bm = gj_panel_width(Kmax);
     size_t b = 0;
-    b += 3 * align16((size_t)Kmax * 16);   // rowbuf, colbuf, colval
-    b += align16(2 * 8 * 64 * 16);         // gemm tiles
-    b += align16(16);                      // inv
-    b += align16((size_t)Kmax * 8) * 2;    // colabs, eps
-    b += align16(NWARP * 8);               // red
-    b += align16((size_t)Kmax * 4) * 2;    // perm, idx
-    b += align16(16);                      // ctl
-    b += align16((size_t)Kmax) * 3;        // kc, kp, kn
+    b += 2 * align16((size_t)Kmax * bm * 16);   // panel, pivot rows
+    b += align16((size_t)bm * 16);              // rowbuf
+    b += align16((size_t)Kmax * 16);            // colbuf
+    b += align16(2 * 8 * 64 * 16);              // gemm tiles
+    b += align16(16);                           // inv
+    b += align16((size_t)Kmax * 8);             // eps
+    b += align16(NWARP * 8);                    // red
+    b += align16((size_t)Kmax * 4) * 2;         // perm, idx
+    b += align16(16);                           // ctl
+    b += align16((size_t)Kmax) * 3;             // kc, kp, kn
     return b;
 }
 
