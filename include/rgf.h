@@ -181,7 +181,7 @@ rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, i
  * T_dev [nE], status_dev [nE] (int32, or NULL), as rgf_conductance_dev.
  * Asynchronous on `stream`; results are valid once the stream has passed the
  * call.  Returns RGF_EINVAL, with a message naming the limit, when the scratch
- * the call needs exceeds 64 MiB (about 29 energies at N = 245, more at smaller
+ * the call needs exceeds 64 MiB (about 25 energies at N = 245, more at smaller
  * N); split the energies over several calls then.
  *
  * The array is shared by all calls and keeps the last call's contents; two

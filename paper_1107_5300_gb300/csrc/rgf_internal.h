@@ -44,10 +44,11 @@ inline size_t lead_out_elems(int N) {
     size_t KL = (size_t)col_KL(N), KR = (size_t)col_KR(N);
     return 2 * (KL * KL + KR * KR);
 }
-// Sweep workspace of one chain: X, G, P, Y (each KL x KL).
+// Sweep workspace of one chain: X, G0, G1, P, Y (each KL x KL) and one
+// element for the flag handed between the two blocks of a chain.
 inline size_t sweep_ws_elems(int N) {
     size_t KL = (size_t)col_KL(N);
-    return 4 * KL * KL;
+    return 5 * KL * KL + 1;
 }
 
 // Shared memory of the sweep / lead kernels for a largest column size Kmax.

@@ -120,33 +120,17 @@ __device__ inline void load_col(const ChainCtx& c, int k, uint8_t* km, double* e
 template <class R>
 __device__ __forceinline__ cx<R> ld_z(const zd* p) { return from_z<R>(p->re, p->im); }
 
-// One forward column step k (matrices row-major with leading dimension KL):
-//   Y    = Pprev W_k                  (KL x K; skipped at k = 0)
-//   X    = A_k                        (K x K)
-//   Gout = A_k^-1                     (Gauss-Jordan; Gout may alias Gprev)
-//   Pout = Y Gout  (or Gout at k = 0) (Pout may alias Pprev)
-// Expects s.kc / s.eps for column k and s.kp for column k-1 loaded.  Returns
-// the Gauss-Jordan flag.
+// The two halves of one forward column step k (row-major, leading dimension KL):
+//   inv_column:   X = A_k (K x K), Gout = A_k^-1 (Gauss-Jordan; Gout may alias
+//                 Gprev).  Needs s.kc / s.eps of column k and s.kp of column
+//                 k-1.  Returns the Gauss-Jordan flag.
+//   strip_column: Y = Pprev W_k (KL x K), Pout = Y Gk  (Pout = Gk at k = 0;
+//                 Pout may alias Pprev).  Needs s.kc and s.kp.
 template <class R>
-__device__ int fwd_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout,
-                          const cx<R>* Pprev, cx<R>* Pout, cx<R>* X, cx<R>* Y,
+__device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout, cx<R>* X,
                           SweepSmem<R>& s) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int KL = c.KL, ct = k & 3, K = col_size(c, k), Kp = col_size(c, k - 1);
-    if (k > 0) {
-        for (int r = warp; r < KL; r += NWARP)
-            for (int l = lane; l < K; l += 32) {
-                cx<R> v = czero<R>();
-                if (s.kc[l]) {
-                    int a0, a1;
-                    col_src(ct, l, Kp, a0, a1);
-                    if (a0 >= 0 && s.kp[a0]) v = cadd(v, Pprev[(size_t)r * KL + a0]);
-                    if (a1 >= 0 && s.kp[a1]) v = cadd(v, Pprev[(size_t)r * KL + a1]);
-                    v = cscale(v, c.t);
-                }
-                Y[(size_t)r * KL + l] = v;
-            }
-    }
     double amax2 = 0.0;
     for (int i = warp; i < K; i += NWARP) {
         int a0 = -1, a1 = -1;
@@ -181,14 +165,43 @@ __device__ int fwd_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
         }
     }
     amax2 = block_max(amax2, s.red);
-    const int flag = cta_gj_invert<R>(X, K, KL, Gout, KL, s.gj, amax2);
+    return cta_gj_invert<R>(X, K, KL, Gout, KL, s.gj, amax2);
+}
+
+template <class R>
+__device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx<R>* Pprev,
+                             cx<R>* Pout, cx<R>* Y, SweepSmem<R>& s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int KL = c.KL, ct = k & 3, K = col_size(c, k), Kp = col_size(c, k - 1);
     if (k == 0) {
         for (int i = warp; i < K; i += NWARP)
-            for (int l = lane; l < K; l += 32) Pout[(size_t)i * KL + l] = Gout[(size_t)i * KL + l];
+            for (int l = lane; l < K; l += 32) Pout[(size_t)i * KL + l] = Gk[(size_t)i * KL + l];
         __syncthreads();
-    } else {
-        cta_gemm<R, false, false>(KL, K, K, Y, KL, Gout, KL, Pout, KL, GEMM_SET, s.gemm);
+        return;
     }
+    for (int r = warp; r < KL; r += NWARP)
+        for (int l = lane; l < K; l += 32) {
+            cx<R> v = czero<R>();
+            if (s.kc[l]) {
+                int a0, a1;
+                col_src(ct, l, Kp, a0, a1);
+                if (a0 >= 0 && s.kp[a0]) v = cadd(v, Pprev[(size_t)r * KL + a0]);
+                if (a1 >= 0 && s.kp[a1]) v = cadd(v, Pprev[(size_t)r * KL + a1]);
+                v = cscale(v, c.t);
+            }
+            Y[(size_t)r * KL + l] = v;
+        }
+    __syncthreads();
+    cta_gemm<R, false, false>(KL, K, K, Y, KL, Gk, KL, Pout, KL, GEMM_SET, s.gemm);
+}
+
+// One whole forward column step (both halves) on one block.
+template <class R>
+__device__ int fwd_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout,
+                          const cx<R>* Pprev, cx<R>* Pout, cx<R>* X, cx<R>* Y,
+                          SweepSmem<R>& s) {
+    const int flag = inv_column<R>(c, k, Gprev, Gout, X, s);
+    strip_column<R>(c, k, Gout, Pprev, Pout, Y, s);
     return flag;
 }
 

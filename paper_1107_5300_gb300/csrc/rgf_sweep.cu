@@ -20,6 +20,12 @@
 // V^T g V is a gather-and-contract over at most 4 entries of g_{k-1} per entry.
 // Removed atoms become identity rows/columns with zero couplings (an exact
 // equivalence to dropping them).
+//
+// Each chain runs on a cluster of two blocks (two SMs): block 0 builds and
+// inverts column k+1 while block 1 applies the strip product of column k; a
+// cluster barrier per column hands g_k over through a double buffer in L2.
+#include <cooperative_groups.h>
+
 #include "rgf_steps.cuh"
 
 namespace rgf {
@@ -46,34 +52,78 @@ sweep_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order,
              int Kmax, double eta_d, const zd* __restrict__ leadout,
              const int* __restrict__ lead_status, const LeadDev* __restrict__ leads,
              cx<R>* __restrict__ ws, double* __restrict__ Tout, int32_t* __restrict__ status) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SweepSmem<R> s = carve<R>(smem_raw, Kmax);
-    const int ci = order[blockIdx.x];
+    const int role = (int)cluster.block_rank();      // 0: inverse, 1: strip
+    const int ci = order[blockIdx.x >> 1];
     const ChainDev ch = chains[ci];
     const int lst = lead_state(lead_status, ch.lead);
-    if (lst != ST_OK) {
-        if (threadIdx.x == 0) { Tout[ci] = NAN; if (status) status[ci] = lst; }
+    if (lst != ST_OK) {            // both blocks of the cluster leave here
+        if (role == 1 && threadIdx.x == 0) { Tout[ci] = NAN; if (status) status[ci] = lst; }
         return;
     }
     const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d);
     const size_t B = (size_t)c.KL * c.KL;
     cx<R>* X = ws + ch.ws_off;
-    cx<R>* G = X + B;
-    cx<R>* P = G + B;
-    cx<R>* Y = P + B;
-    int flag = 0;
-    for (int k = 0; k < c.ncol; ++k) {
-        load_col(c, k, s.kc, s.eps);
-        load_col(c, k - 1, s.kp, nullptr);
-        __syncthreads();
-        flag |= fwd_column<R>(c, k, G, G, P, P, X, Y, s);
+    cx<R>* Gb[2] = {X + B, X + 2 * B};
+    cx<R>* P = X + 3 * B;
+    cx<R>* Y = X + 4 * B;
+    int* flag_slot = reinterpret_cast<int*>(X + 5 * B);
+    if (role == 0) {
+        int flag = 0;
+        for (int k = 0; k < c.ncol; ++k) {
+            load_col(c, k, s.kc, s.eps);
+            load_col(c, k - 1, s.kp, nullptr);
+            __syncthreads();
+            flag |= inv_column<R>(c, k, Gb[(k + 1) & 1], Gb[k & 1], X, s);
+            cluster.sync();        // g_k ready; block 1 is done with g_{k-1}
+        }
+        if (threadIdx.x == 0) *flag_slot = flag;
+        cluster.sync();
+    } else {
+        for (int k = 0; k < c.ncol; ++k) {
+            cluster.sync();
+            load_col(c, k, s.kc, nullptr);
+            load_col(c, k - 1, s.kp, nullptr);
+            __syncthreads();
+            strip_column<R>(c, k, Gb[k & 1], P, P, Y, s);
+        }
+        cluster.sync();
+        const int flag = *(volatile int*)flag_slot;
+        const double T = trace_T<R>(c, P, X, Gb[0], Y, s);
+        if (threadIdx.x == 0) {
+            const int st = chain_status(c, flag, T);
+            Tout[ci] = (st == ST_OK) ? T : NAN;
+            if (status) status[ci] = st;
+        }
     }
-    const double T = trace_T<R>(c, P, X, G, Y, s);
-    if (threadIdx.x == 0) {
-        const int st = chain_status(c, flag, T);
-        Tout[ci] = (st == ST_OK) ? T : NAN;
-        if (status) status[ci] = st;
-    }
+}
+
+template <class R>
+static cudaError_t launch_sweep_t(const ChainDev* chains, const int* order, int nchains, int Kmax,
+                                  double eta_device, const zd* leadout, const int* lead_status,
+                                  const LeadDev* leads, cx<R>* ws, double* T, int32_t* status,
+                                  cudaStream_t st) {
+    const size_t smem = sweep_smem_bytes(Kmax);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * nchains, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<R>, chains, order, nchains, Kmax, eta_device,
+                              leadout, lead_status, leads, ws, T, status);
 }
 
 cudaError_t launch_sweep(int precision, const ChainDev* chains, const int* order, int nchains,
@@ -81,23 +131,14 @@ cudaError_t launch_sweep(int precision, const ChainDev* chains, const int* order
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    size_t smem = sweep_smem_bytes(Kmax);
     cudaError_t e;
-    if (precision == 0) {
-        e = cudaFuncSetAttribute(sweep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        sweep_kernel<double><<<nchains, NT, smem, st>>>(chains, order, nchains, Kmax, eta_device,
-                                                       (const zd*)leadout, lead_status, leads,
-                                                       (zd*)ws, T, status);
-    } else {
-        e = cudaFuncSetAttribute(sweep_kernel<df32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        sweep_kernel<df32><<<nchains, NT, smem, st>>>(chains, order, nchains, Kmax, eta_device,
-                                                     (const zd*)leadout, lead_status, leads,
-                                                     (zf*)ws, T, status);
-    }
+    if (precision == 0)
+        e = launch_sweep_t<double>(chains, order, nchains, Kmax, eta_device, (const zd*)leadout,
+                                   lead_status, leads, (zd*)ws, T, status, st);
+    else
+        e = launch_sweep_t<df32>(chains, order, nchains, Kmax, eta_device, (const zd*)leadout,
+                                 lead_status, leads, (zf*)ws, T, status, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
