@@ -145,6 +145,14 @@ __device__ __forceinline__ double cabs2(zf a) {
     return r * r + i * i;
 }
 
+// |a|^2 in binary32 (pivot search only; overflow to inf still orders correctly
+// against finite values and the winner is rechecked in binary64).
+__device__ __forceinline__ float cabs2f(zd a) {
+    float r = (float)a.re, i = (float)a.im;
+    return r * r + i * i;
+}
+__device__ __forceinline__ float cabs2f(zf a) { return a.re.hi * a.re.hi + a.im.hi * a.im.hi; }
+
 __device__ __forceinline__ bool cfinite(zd a) { return isfinite(a.re) && isfinite(a.im); }
 __device__ __forceinline__ bool cfinite(zf a) { return isfinite(a.re.hi) && isfinite(a.im.hi); }
 

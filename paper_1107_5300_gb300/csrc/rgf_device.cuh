@@ -135,10 +135,15 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
 //   |A[p][j]|, swap rows j and p -- in the panel and in the rest of the matrix
 //   --, scale the pivot row by 1/A[j][j] keeping 1/A[j][j] in column j,
 //   eliminate column j from every other row keeping -A[i][j]/A[j][j] in
-//   column j).  The reduced panel is then exactly the block's accumulated row
-//   transform T restricted to its pivot columns (T is the identity outside
-//   them), so every other column is updated in one rank-b step
-//       A[i][l] <- [i not a pivot row] A[i][l] + sum_jj Panel[i][jj] A[j0+jj][l],
+//   column j), recording for each step its multipliers c_jj[i] (column j at
+//   row i just before step jj) and its pivot reciprocal.  The columns outside
+//   the panel then receive the same b steps in two passes:
+//     pivot rows (forward substitution, then the later steps' eliminations)
+//       x_jj = (A[j0+jj][l] - sum_{jj' < jj} c_jj'[j0+jj] x_jj') / p_jj
+//       A[j0+jj][l] = x_jj - sum_{jj' > jj} c_jj'[j0+jj] x_jj'
+//     every other row (one rank-b update)
+//       A[i][l] -= sum_jj c_jj[i] x_jj
+//   -- the arithmetic of the unblocked algorithm in a different association,
 //   reading and writing each element once per block instead of once per pivot.
 //   The row swaps are undone at the end by a column permutation applied while
 //   copying into G.  Pivot reciprocals are formed in binary64.
@@ -150,8 +155,10 @@ template <class R>
 struct GJSmem {
     cx<R>* rowbuf;   // [bmax]   scaled pivot row of the panel
     cx<R>* colbuf;   // [Kmax]   pivot column of the panel
-    cx<R>* panel;    // [Kmax][bmax]
-    cx<R>* prow;     // [bmax][Kmax] pivot rows outside the panel
+    cx<R>* panel;    // [Kmax][bmax]  working panel
+    cx<R>* mult;     // [Kmax][bmax]  multipliers c_jj[i]
+    cx<R>* xrow;     // [bmax][Kmax]  substituted pivot rows outside the panel
+    cx<R>* pinv;     // [bmax]   pivot reciprocals
     int* perm;       // [Kmax]
     int* idx;        // [Kmax]
     int* ctl;        // [4]: pivot row, flag
@@ -165,7 +172,8 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bm = s.bmax;
     cx<R>* Pn = s.panel;
-    cx<R>* MR = s.prow;
+    cx<R>* Cm = s.mult;
+    cx<R>* Xr = s.xrow;
     const double tiny2 = amax2 * (64.0 * Unit<R>::u) * (64.0 * Unit<R>::u);
     if (tid == 0) s.ctl[1] = 0;
     for (int j0 = 0; j0 < K; j0 += bm) {
@@ -178,14 +186,14 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         for (int jj = 0; jj < bb; ++jj) {
             const int j = j0 + jj;
             if (warp == 0) {
-                double best = -1.0;
+                float best = -1.0f;
                 int bi = j;
                 for (int i = j + lane; i < K; i += 32) {
-                    double v = cabs2(Pn[i * bm + jj]);
+                    float v = cabs2f(Pn[i * bm + jj]);
                     if (v > best || isnan(v)) { best = isnan(v) ? INFINITY : v; bi = i; }
                 }
                 for (int o = 16; o > 0; o >>= 1) {
-                    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    float ob = __shfl_xor_sync(0xffffffffu, best, o);
                     int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
                 }
@@ -217,13 +225,24 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                         A[(size_t)p * lda + l] = a;
                     }
                 }
+                // earlier multipliers follow their rows
+                for (int l = tid; l < jj; l += NT) {
+                    cx<R> a = Cm[j * bm + l];
+                    Cm[j * bm + l] = Cm[p * bm + l];
+                    Cm[p * bm + l] = a;
+                }
                 __syncthreads();
             }
             const zd invz = *s.inv;
             const cx<R> invR = from_z<R>(invz.re, invz.im);
             for (int l = tid; l < bb; l += NT)
                 s.rowbuf[l] = (l == jj) ? invR : cmul(Pn[j * bm + l], invR);
-            for (int i = tid; i < K; i += NT) s.colbuf[i] = (i == j) ? czero<R>() : Pn[i * bm + jj];
+            for (int i = tid; i < K; i += NT) {
+                const cx<R> c = (i == j) ? czero<R>() : Pn[i * bm + jj];
+                s.colbuf[i] = c;
+                Cm[i * bm + jj] = c;
+            }
+            if (tid == 0) s.pinv[jj] = invR;
             __syncthreads();
             for (int e = tid; e < K * bb; e += NT) {
                 const int i = e / bb, l = e % bb;
@@ -236,43 +255,56 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
             }
             __syncthreads();
         }
-        // Pivot rows outside the panel, then the rank-bb update of all other columns.
-        const int Kc = K - bb;   // columns outside the panel
-        for (int e = tid; e < bb * Kc; e += NT) {
-            int jj = e / Kc, c = e % Kc;
-            int l = c < j0 ? c : c + bb;
-            MR[jj * K + c] = A[(size_t)(j0 + jj) * lda + l];
+        // Columns outside the panel: pivot rows by substitution ...
+        const int Kc = K - bb;
+        for (int c = tid; c < Kc; c += NT) {
+            const int l = c < j0 ? c : c + bb;
+            for (int jj = 0; jj < bb; ++jj) {
+                cx<R> x = A[(size_t)(j0 + jj) * lda + l];
+                for (int q = 0; q < jj; ++q) x = cmac(x, Cm[(j0 + jj) * bm + q], Xr[q * K + c], true);
+                Xr[jj * K + c] = cmul(x, s.pinv[jj]);
+            }
+            for (int jj = 0; jj < bb; ++jj) {
+                cx<R> y = Xr[jj * K + c];
+                for (int q = jj + 1; q < bb; ++q) y = cmac(y, Cm[(j0 + jj) * bm + q], Xr[q * K + c], true);
+                A[(size_t)(j0 + jj) * lda + l] = y;
+            }
         }
         __syncthreads();
+        // ... then one rank-bb update of every other row.
         const int Kh = (K + 1) >> 1, Ch = (Kc + 1) >> 1;
         for (int tt = tid; tt < Kh * Ch; tt += NT) {
             const int i0 = 2 * (tt / Ch), c0 = 2 * (tt % Ch);
             const bool ok_i1 = i0 + 1 < K, ok_c1 = c0 + 1 < Kc;
             const int l0 = c0 < j0 ? c0 : c0 + bb;
             const int l1 = (c0 + 1) < j0 ? c0 + 1 : c0 + 1 + bb;
-            const bool r0 = i0 >= j0 && i0 < j0 + bb, r1 = (i0 + 1) >= j0 && (i0 + 1) < j0 + bb;
+            const bool r0 = i0 >= j0 && i0 < j0 + bb;
+            const bool r1 = !ok_i1 || ((i0 + 1) >= j0 && (i0 + 1) < j0 + bb);
+            if (r0 && r1) continue;
             cx<R> a00 = czero<R>(), a01 = czero<R>(), a10 = czero<R>(), a11 = czero<R>();
             if (!r0) {
                 a00 = A[(size_t)i0 * lda + l0];
                 if (ok_c1) a01 = A[(size_t)i0 * lda + l1];
             }
-            if (ok_i1 && !r1) {
+            if (!r1) {
                 a10 = A[(size_t)(i0 + 1) * lda + l0];
                 if (ok_c1) a11 = A[(size_t)(i0 + 1) * lda + l1];
             }
             for (int jj = 0; jj < bb; ++jj) {
-                const cx<R> p0 = Pn[i0 * bm + jj];
-                const cx<R> p1 = ok_i1 ? Pn[(i0 + 1) * bm + jj] : czero<R>();
-                const cx<R> m0 = MR[jj * K + c0];
-                const cx<R> m1 = ok_c1 ? MR[jj * K + c0 + 1] : czero<R>();
-                a00 = cmac(a00, p0, m0, false);
-                a01 = cmac(a01, p0, m1, false);
-                a10 = cmac(a10, p1, m0, false);
-                a11 = cmac(a11, p1, m1, false);
+                const cx<R> p0 = r0 ? czero<R>() : Cm[i0 * bm + jj];
+                const cx<R> p1 = r1 ? czero<R>() : Cm[(i0 + 1) * bm + jj];
+                const cx<R> m0 = Xr[jj * K + c0];
+                const cx<R> m1 = ok_c1 ? Xr[jj * K + c0 + 1] : czero<R>();
+                a00 = cmac(a00, p0, m0, true);
+                a01 = cmac(a01, p0, m1, true);
+                a10 = cmac(a10, p1, m0, true);
+                a11 = cmac(a11, p1, m1, true);
             }
-            A[(size_t)i0 * lda + l0] = a00;
-            if (ok_c1) A[(size_t)i0 * lda + l1] = a01;
-            if (ok_i1) {
+            if (!r0) {
+                A[(size_t)i0 * lda + l0] = a00;
+                if (ok_c1) A[(size_t)i0 * lda + l1] = a01;
+            }
+            if (!r1) {
                 A[(size_t)(i0 + 1) * lda + l0] = a10;
                 if (ok_c1) A[(size_t)(i0 + 1) * lda + l1] = a11;
             }

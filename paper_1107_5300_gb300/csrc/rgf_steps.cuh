@@ -28,7 +28,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 // rest of the shared memory.
 __host__ __device__ inline int gj_panel_width(int Kmax) {
     int b = 16;
-    while (b > 2 && (size_t)2 * Kmax * b * 16 + (size_t)Kmax * 64 + 20000 > 220 * 1024) b >>= 1;
+    while (b > 2 && (size_t)3 * Kmax * b * 16 + (size_t)Kmax * 64 + 20000 > 220 * 1024) b >>= 1;
     return b;
 }
 
@@ -40,8 +40,10 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax) {
     const int bm = gj_panel_width(Kmax);
     s.gj.bmax = bm;
     s.gj.panel = (cx<R>*)take((size_t)Kmax * bm * 16);
-    s.gj.prow = (cx<R>*)take((size_t)Kmax * bm * 16);
+    s.gj.mult = (cx<R>*)take((size_t)Kmax * bm * 16);
+    s.gj.xrow = (cx<R>*)take((size_t)Kmax * bm * 16);
     s.gj.rowbuf = (cx<R>*)take((size_t)bm * 16);
+    s.gj.pinv = (cx<R>*)take((size_t)bm * 16);
     s.gj.colbuf = (cx<R>*)take((size_t)Kmax * 16);
     s.gemm = (cx<R>*)take(2 * 8 * 64 * 16);
     s.gj.inv = (zd*)take(16);
@@ -160,7 +162,7 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
                 v = csub(v, sig);
             }
             X[(size_t)i * KL + l] = v;
-            const double a2 = cabs2(v);
+            const double a2 = (double)cabs2f(v);
             amax2 = (a2 > amax2 || isnan(a2)) ? a2 : amax2;
         }
     }

@@ -33,8 +33,8 @@ namespace rgf {
 size_t sweep_smem_bytes(int Kmax) {
     const int bm = gj_panel_width(Kmax);
     size_t b = 0;
-    b += 2 * align16((size_t)Kmax * bm * 16);   // panel, pivot rows
-    b += align16((size_t)bm * 16);              // rowbuf
+    b += 3 * align16((size_t)Kmax * bm * 16);   // panel, multipliers, pivot rows
+    b += 2 * align16((size_t)bm * 16);          // rowbuf, pivot reciprocals
     b += align16((size_t)Kmax * 16);            // colbuf
     b += align16(2 * 8 * 64 * 16);              // gemm tiles
     b += align16(16);                           // inv
