@@ -5,6 +5,8 @@
 // __syncthreads().  The block size is RGF_NT threads.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "rgf_common.cuh"
 
 #ifndef RGF_NT
@@ -15,6 +17,19 @@ namespace rgf {
 
 constexpr int NT = RGF_NT;
 constexpr int NWARP = NT / 32;
+
+// The blocks that share one chain: block `rank` of a cluster of C.  Work on
+// columns (or rows) is split into C contiguous ranges; cl_sync() is a cluster
+// barrier (a block barrier when C = 1).
+struct Team {
+    int rank, C;
+    __device__ int lo(int n) const { return (int)(((long long)n * rank) / C); }
+    __device__ int hi(int n) const { return (int)(((long long)n * (rank + 1)) / C); }
+};
+__device__ __forceinline__ void cl_sync(const Team& tm) {
+    if (tm.C > 1) cooperative_groups::this_cluster().sync();
+    else __syncthreads();
+}
 
 // ---------------------------------------------------------------------------
 // Block reductions
@@ -147,6 +162,10 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
 //   reading and writing each element once per block instead of once per pivot.
 //   The row swaps are undone at the end by a column permutation applied while
 //   copying into G.  Pivot reciprocals are formed in binary64.
+//   With a team of C blocks (one cluster) every block reduces the panel (the
+//   same data, the same result) and updates only its own range of columns;
+//   the copy-out is split by rows.  G is complete after the caller's next
+//   cluster barrier.
 // Returns a flag: bit 0 = zero pivot, or a pivot below 64 u sqrt(amax2) with
 // amax2 = max |A_ij|^2 supplied by the caller (0 disables the test); bit 1 =
 // non-finite pivot.
@@ -156,6 +175,7 @@ struct GJSmem {
     cx<R>* rowbuf;   // [bmax]   scaled pivot row of the panel
     cx<R>* colbuf;   // [Kmax]   pivot column of the panel
     cx<R>* panel;    // [Kmax][bmax]  working panel
+    cx<R>* panel2;   // [Kmax][bmax]  second panel buffer
     cx<R>* mult;     // [Kmax][bmax]  multipliers c_jj[i]
     cx<R>* xrow;     // [bmax][Kmax]  substituted pivot rows outside the panel
     cx<R>* pinv;     // [bmax]   pivot reciprocals
@@ -168,19 +188,23 @@ struct GJSmem {
 
 template <class R>
 __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __restrict__ G, int ldg,
-                             GJSmem<R> s, double amax2 = 0.0) {
+                             GJSmem<R> s, double amax2 = 0.0, Team tm = Team{0, 1}) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int bm = s.bmax;
     cx<R>* Pn = s.panel;
     cx<R>* Cm = s.mult;
     cx<R>* Xr = s.xrow;
     const double tiny2 = amax2 * (64.0 * Unit<R>::u) * (64.0 * Unit<R>::u);
+    const int clo = tm.lo(K), chi = tm.hi(K);     // this block's columns
+    const int rlo = tm.lo(K), rhi = tm.hi(K);     // this block's rows (copy-out)
     if (tid == 0) s.ctl[1] = 0;
     for (int j0 = 0; j0 < K; j0 += bm) {
         const int bb = min(bm, K - j0);
+        cx<R>* Pa = s.panel;            // panel, current
+        cx<R>* Pb = s.panel2;           // panel, next
         for (int e = tid; e < K * bb; e += NT) {
             int i = e / bb, jj = e % bb;
-            Pn[i * bm + jj] = A[(size_t)i * lda + j0 + jj];
+            Pa[i * bm + jj] = A[(size_t)i * lda + j0 + jj];
         }
         __syncthreads();
         for (int jj = 0; jj < bb; ++jj) {
@@ -189,7 +213,7 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                 float best = -1.0f;
                 int bi = j;
                 for (int i = j + lane; i < K; i += 32) {
-                    float v = cabs2f(Pn[i * bm + jj]);
+                    float v = cabs2f(Pa[i * bm + jj]);
                     if (v > best || isnan(v)) { best = isnan(v) ? INFINITY : v; bi = i; }
                 }
                 for (int o = 16; o > 0; o >>= 1) {
@@ -197,87 +221,88 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                     int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
                 }
+                // every lane knows the pivot row bi: all form its reciprocal,
+                // lanes < bb scale one entry of the pivot row each
+                zd pz = to_z(Pa[bi * bm + jj]);
+                double d = pz.re * pz.re + pz.im * pz.im;
+                int bad = 0;
+                if (!isfinite(d)) { bad = 2; d = 1.0; pz = {1.0, 0.0}; }
+                else if (!(d > 0.0)) { bad = 1; d = 1.0; pz = {1.0, 0.0}; }
+                else if (d < tiny2) { bad = 1; }
+                const zd iz = zd{pz.re / d, -pz.im / d};
+                const cx<R> invR = from_z<R>(iz.re, iz.im);
+                if (lane < bb) s.rowbuf[lane] = (lane == jj) ? invR : cmul(Pa[bi * bm + lane], invR);
                 if (lane == 0) {
-                    zd pz = to_z(Pn[bi * bm + jj]);
-                    double d = pz.re * pz.re + pz.im * pz.im;
-                    int flag = s.ctl[1];
-                    if (!isfinite(d)) { flag |= 2; d = 1.0; pz = {1.0, 0.0}; }
-                    else if (!(d > 0.0)) { flag |= 1; d = 1.0; pz = {1.0, 0.0}; }
-                    else if (d < tiny2) { flag |= 1; }
-                    s.ctl[1] = flag;
+                    s.ctl[1] |= bad;
                     s.ctl[0] = bi;
                     s.perm[j] = bi;
-                    *s.inv = zd{pz.re / d, -pz.im / d};
+                    *s.inv = iz;
+                    s.pinv[jj] = invR;
                 }
             }
             __syncthreads();
+            // One pass: row swap j <-> p folded in as an index remap, pivot row
+            // scaled (rowbuf), column jj eliminated from every other row (old -> new).
             const int p = s.ctl[0];
-            if (p != j) {
-                for (int l = tid; l < K; l += NT) {
-                    if (l >= j0 && l < j0 + bb) {
-                        int ll = l - j0;
-                        cx<R> a = Pn[j * bm + ll];
-                        Pn[j * bm + ll] = Pn[p * bm + ll];
-                        Pn[p * bm + ll] = a;
-                    } else {
-                        cx<R> a = A[(size_t)j * lda + l];
-                        A[(size_t)j * lda + l] = A[(size_t)p * lda + l];
-                        A[(size_t)p * lda + l] = a;
-                    }
-                }
-                // earlier multipliers follow their rows
-                for (int l = tid; l < jj; l += NT) {
-                    cx<R> a = Cm[j * bm + l];
-                    Cm[j * bm + l] = Cm[p * bm + l];
-                    Cm[p * bm + l] = a;
-                }
-                __syncthreads();
-            }
-            const zd invz = *s.inv;
-            const cx<R> invR = from_z<R>(invz.re, invz.im);
-            for (int l = tid; l < bb; l += NT)
-                s.rowbuf[l] = (l == jj) ? invR : cmul(Pn[j * bm + l], invR);
-            for (int i = tid; i < K; i += NT) {
-                const cx<R> c = (i == j) ? czero<R>() : Pn[i * bm + jj];
-                s.colbuf[i] = c;
-                Cm[i * bm + jj] = c;
-            }
-            if (tid == 0) s.pinv[jj] = invR;
-            __syncthreads();
             for (int e = tid; e < K * bb; e += NT) {
                 const int i = e / bb, l = e % bb;
+                const int si = (i == j) ? p : ((i == p) ? j : i);
+                const cx<R> r = s.rowbuf[l];
                 if (i == j) {
-                    Pn[i * bm + l] = s.rowbuf[l];
+                    Pb[i * bm + l] = r;
                 } else {
-                    cx<R> a = (l == jj) ? czero<R>() : Pn[i * bm + l];
-                    Pn[i * bm + l] = cmac(a, s.colbuf[i], s.rowbuf[l], true);
+                    const cx<R> m = Pa[si * bm + jj];
+                    const cx<R> a = (l == jj) ? czero<R>() : Pa[si * bm + l];
+                    Pb[i * bm + l] = cmac(a, m, r, true);
+                    if (l == jj) Cm[i * bm + jj] = m;
                 }
             }
+            if (tid == 0) Cm[j * bm + jj] = czero<R>();
+            if (p != j)                  // earlier multipliers follow their rows
+                for (int q = tid; q < jj; q += NT) {
+                    cx<R> a = Cm[j * bm + q];
+                    Cm[j * bm + q] = Cm[p * bm + q];
+                    Cm[p * bm + q] = a;
+                }
             __syncthreads();
+            cx<R>* t = Pa; Pa = Pb; Pb = t;
         }
-        // Columns outside the panel: pivot rows by substitution ...
-        const int Kc = K - bb;
-        for (int c = tid; c < Kc; c += NT) {
-            const int l = c < j0 ? c : c + bb;
+        // This block's columns outside the panel: the block's row swaps, then
+        // the pivot rows by substitution (one thread per column) ...
+        const int ps = max(j0, clo), pe = min(j0 + bb, chi);
+        const int pskip = max(0, pe - ps);
+        const int nown = (chi - clo) - pskip;            // own columns outside the panel
+        auto own_col = [&](int c) { int l = clo + c; return (l < ps) ? l : l + pskip; };
+        for (int c = tid; c < nown; c += NT) {
+            const int l = own_col(c);
             for (int jj = 0; jj < bb; ++jj) {
-                cx<R> x = A[(size_t)(j0 + jj) * lda + l];
-                for (int q = 0; q < jj; ++q) x = cmac(x, Cm[(j0 + jj) * bm + q], Xr[q * K + c], true);
-                Xr[jj * K + c] = cmul(x, s.pinv[jj]);
+                const int j = j0 + jj, p = s.perm[j];
+                if (p != j) {
+                    cx<R> a = A[(size_t)j * lda + l];
+                    A[(size_t)j * lda + l] = A[(size_t)p * lda + l];
+                    A[(size_t)p * lda + l] = a;
+                }
             }
             for (int jj = 0; jj < bb; ++jj) {
-                cx<R> y = Xr[jj * K + c];
-                for (int q = jj + 1; q < bb; ++q) y = cmac(y, Cm[(j0 + jj) * bm + q], Xr[q * K + c], true);
+                cx<R> x = A[(size_t)(j0 + jj) * lda + l];
+                for (int q = 0; q < jj; ++q) x = cmac(x, Cm[(j0 + jj) * bm + q], Xr[q * K + l], true);
+                Xr[jj * K + l] = cmul(x, s.pinv[jj]);
+            }
+            for (int jj = 0; jj < bb; ++jj) {
+                cx<R> y = Xr[jj * K + l];
+                for (int q = jj + 1; q < bb; ++q) y = cmac(y, Cm[(j0 + jj) * bm + q], Xr[q * K + l], true);
                 A[(size_t)(j0 + jj) * lda + l] = y;
             }
         }
         __syncthreads();
+        Pn = Pa;                         // the reduced panel
         // ... then one rank-bb update of every other row.
-        const int Kh = (K + 1) >> 1, Ch = (Kc + 1) >> 1;
+        const int Kh = (K + 1) >> 1, Ch = (nown + 1) >> 1;
         for (int tt = tid; tt < Kh * Ch; tt += NT) {
             const int i0 = 2 * (tt / Ch), c0 = 2 * (tt % Ch);
-            const bool ok_i1 = i0 + 1 < K, ok_c1 = c0 + 1 < Kc;
-            const int l0 = c0 < j0 ? c0 : c0 + bb;
-            const int l1 = (c0 + 1) < j0 ? c0 + 1 : c0 + 1 + bb;
+            const bool ok_i1 = i0 + 1 < K, ok_c1 = c0 + 1 < nown;
+            const int l0 = own_col(c0);
+            const int l1 = ok_c1 ? own_col(c0 + 1) : l0;
             const bool r0 = i0 >= j0 && i0 < j0 + bb;
             const bool r1 = !ok_i1 || ((i0 + 1) >= j0 && (i0 + 1) < j0 + bb);
             if (r0 && r1) continue;
@@ -293,8 +318,8 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
             for (int jj = 0; jj < bb; ++jj) {
                 const cx<R> p0 = r0 ? czero<R>() : Cm[i0 * bm + jj];
                 const cx<R> p1 = r1 ? czero<R>() : Cm[(i0 + 1) * bm + jj];
-                const cx<R> m0 = Xr[jj * K + c0];
-                const cx<R> m1 = ok_c1 ? Xr[jj * K + c0 + 1] : czero<R>();
+                const cx<R> m0 = Xr[jj * K + l0];
+                const cx<R> m1 = ok_c1 ? Xr[jj * K + l1] : czero<R>();
                 a00 = cmac(a00, p0, m0, true);
                 a01 = cmac(a01, p0, m1, true);
                 a10 = cmac(a10, p1, m0, true);
@@ -309,11 +334,12 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                 if (ok_c1) A[(size_t)(i0 + 1) * lda + l1] = a11;
             }
         }
-        for (int e = tid; e < K * bb; e += NT) {
-            int i = e / bb, jj = e % bb;
+        // the reduced panel: this block's rows
+        for (int e = tid; e < (rhi - rlo) * bb; e += NT) {
+            int i = rlo + e / bb, jj = e % bb;
             A[(size_t)i * lda + j0 + jj] = Pn[i * bm + jj];
         }
-        __syncthreads();
+        cl_sync(tm);
     }
     if (tid == 0) {
         for (int c = 0; c < K; ++c) s.idx[c] = c;
@@ -323,7 +349,7 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         }
     }
     __syncthreads();
-    for (int i = warp; i < K; i += NWARP) {
+    for (int i = rlo + warp; i < rhi; i += NWARP) {
         const cx<R>* row = A + (size_t)i * lda;
         cx<R>* grow = G + (size_t)i * ldg;
         for (int c = lane; c < K; c += 32) grow[c] = row[s.idx[c]];

@@ -19,6 +19,7 @@ struct SweepSmem {
     uint8_t* kn;     // keep mask of the next column (adjoint)
     double* eps;
     double* red;
+    double* clmax;   // this block's partial max |A|^2, read by the team
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -28,7 +29,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 // rest of the shared memory.
 __host__ __device__ inline int gj_panel_width(int Kmax) {
     int b = 16;
-    while (b > 2 && (size_t)3 * Kmax * b * 16 + (size_t)Kmax * 64 + 20000 > 220 * 1024) b >>= 1;
+    while (b > 2 && (size_t)4 * Kmax * b * 16 + (size_t)Kmax * 64 + 20000 > 220 * 1024) b >>= 1;
     return b;
 }
 
@@ -40,6 +41,7 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax) {
     const int bm = gj_panel_width(Kmax);
     s.gj.bmax = bm;
     s.gj.panel = (cx<R>*)take((size_t)Kmax * bm * 16);
+    s.gj.panel2 = (cx<R>*)take((size_t)Kmax * bm * 16);
     s.gj.mult = (cx<R>*)take((size_t)Kmax * bm * 16);
     s.gj.xrow = (cx<R>*)take((size_t)Kmax * bm * 16);
     s.gj.rowbuf = (cx<R>*)take((size_t)bm * 16);
@@ -49,6 +51,7 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax) {
     s.gj.inv = (zd*)take(16);
     s.eps = (double*)take((size_t)Kmax * 8);
     s.red = (double*)take(NWARP * 8);
+    s.clmax = (double*)take(16);
     s.gj.perm = (int*)take((size_t)Kmax * 4);
     s.gj.idx = (int*)take((size_t)Kmax * 4);
     s.gj.ctl = (int*)take(16);
@@ -130,11 +133,11 @@ __device__ __forceinline__ cx<R> ld_z(const zd* p) { return from_z<R>(p->re, p->
 //                 Pout may alias Pprev).  Needs s.kc and s.kp.
 template <class R>
 __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout, cx<R>* X,
-                          SweepSmem<R>& s) {
+                          SweepSmem<R>& s, Team tm = Team{0, 1}) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int KL = c.KL, ct = k & 3, K = col_size(c, k), Kp = col_size(c, k - 1);
     double amax2 = 0.0;
-    for (int i = warp; i < K; i += NWARP) {
+    for (int i = tm.lo(K) + warp; i < tm.hi(K); i += NWARP) {
         int a0 = -1, a1 = -1;
         if (k > 0) col_src(ct, i, Kp, a0, a1);
         const bool ki = s.kc[i];
@@ -167,21 +170,32 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
         }
     }
     amax2 = block_max(amax2, s.red);
-    return cta_gj_invert<R>(X, K, KL, Gout, KL, s.gj, amax2);
+    if (tm.C > 1) {
+        if (threadIdx.x == 0) *s.clmax = amax2;
+        cl_sync(tm);                      // A_k complete; partial maxima visible
+        auto cluster = cooperative_groups::this_cluster();
+        for (int r = 0; r < tm.C; ++r) {
+            const double v = *cluster.map_shared_rank(s.clmax, r);
+            amax2 = (v > amax2 || isnan(v)) ? v : amax2;
+        }
+    }
+    return cta_gj_invert<R>(X, K, KL, Gout, KL, s.gj, amax2, tm);
 }
 
+// Strip half; with a team, Y is built by rows and the product by columns, and
+// Pout is complete after the caller's next cluster barrier.
 template <class R>
 __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx<R>* Pprev,
-                             cx<R>* Pout, cx<R>* Y, SweepSmem<R>& s) {
+                             cx<R>* Pout, cx<R>* Y, SweepSmem<R>& s, Team tm = Team{0, 1}) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int KL = c.KL, ct = k & 3, K = col_size(c, k), Kp = col_size(c, k - 1);
     if (k == 0) {
-        for (int i = warp; i < K; i += NWARP)
+        for (int i = tm.lo(K) + warp; i < tm.hi(K); i += NWARP)
             for (int l = lane; l < K; l += 32) Pout[(size_t)i * KL + l] = Gk[(size_t)i * KL + l];
         __syncthreads();
         return;
     }
-    for (int r = warp; r < KL; r += NWARP)
+    for (int r = tm.lo(KL) + warp; r < tm.hi(KL); r += NWARP)
         for (int l = lane; l < K; l += 32) {
             cx<R> v = czero<R>();
             if (s.kc[l]) {
@@ -193,11 +207,13 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
             }
             Y[(size_t)r * KL + l] = v;
         }
-    __syncthreads();
-    cta_gemm<R, false, false>(KL, K, K, Y, KL, Gk, KL, Pout, KL, GEMM_SET, s.gemm);
+    cl_sync(tm);                          // Y complete (Pprev no longer read)
+    const int lo = tm.lo(K), n = tm.hi(K) - lo;
+    if (n > 0) cta_gemm<R, false, false>(KL, n, K, Y, KL, Gk + lo, KL, Pout + lo, KL, GEMM_SET, s.gemm);
+    else __syncthreads();
 }
 
-// One whole forward column step (both halves) on one block.
+// One whole forward column step on one block (used by the adjoint).
 template <class R>
 __device__ int fwd_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout,
                           const cx<R>* Pprev, cx<R>* Pout, cx<R>* X, cx<R>* Y,

@@ -21,9 +21,15 @@
 // Removed atoms become identity rows/columns with zero couplings (an exact
 // equivalence to dropping them).
 //
-// Each chain runs on a cluster of two blocks (two SMs): block 0 builds and
-// inverts column k+1 while block 1 applies the strip product of column k; a
-// cluster barrier per column hands g_k over through a double buffer in L2.
+// Each chain runs on a cluster of C blocks (C SMs; C = 1, 2, 4 or 8, the
+// largest with chains x C <= SMs).  Two schedules:
+//   C = 2  pipeline: block 0 builds and inverts column k+1 while block 1
+//          applies the strip product of column k; one cluster barrier per
+//          column hands g_k over through a double buffer in L2.
+//   else   team: every phase is shared -- the A_k build and the copy-out of
+//          g_k by rows, the Gauss-Jordan panel redundantly (same data, same
+//          result), its substitution and rank-b update by columns, the strip
+//          product by columns; cluster barriers order the phases.
 #include <cooperative_groups.h>
 
 #include "rgf_steps.cuh"
@@ -33,13 +39,14 @@ namespace rgf {
 size_t sweep_smem_bytes(int Kmax) {
     const int bm = gj_panel_width(Kmax);
     size_t b = 0;
-    b += 3 * align16((size_t)Kmax * bm * 16);   // panel, multipliers, pivot rows
+    b += 4 * align16((size_t)Kmax * bm * 16);   // 2 panels, multipliers, pivot rows
     b += 2 * align16((size_t)bm * 16);          // rowbuf, pivot reciprocals
     b += align16((size_t)Kmax * 16);            // colbuf
     b += align16(2 * 8 * 64 * 16);              // gemm tiles
     b += align16(16);                           // inv
     b += align16((size_t)Kmax * 8);             // eps
     b += align16(NWARP * 8);                    // red
+    b += align16(16);                           // clmax
     b += align16((size_t)Kmax * 4) * 2;         // perm, idx
     b += align16(16);                           // ctl
     b += align16((size_t)Kmax) * 3;             // kc, kp, kn
@@ -48,10 +55,54 @@ size_t sweep_smem_bytes(int Kmax) {
 
 template <class R>
 __global__ void __launch_bounds__(NT, 1)
-sweep_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
+sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
              int Kmax, double eta_d, const zd* __restrict__ leadout,
              const int* __restrict__ lead_status, const LeadDev* __restrict__ leads,
              cx<R>* __restrict__ ws, double* __restrict__ Tout, int32_t* __restrict__ status) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SweepSmem<R> s = carve<R>(smem_raw, Kmax);
+    cg::cluster_group cluster = cg::this_cluster();
+    const Team tm{(int)cluster.block_rank(), (int)cluster.num_blocks()};
+    const int ci = order[blockIdx.x / tm.C];
+    const ChainDev ch = chains[ci];
+    const int lst = lead_state(lead_status, ch.lead);
+    if (lst != ST_OK) {            // every block of the cluster leaves here
+        if (tm.rank == 0 && threadIdx.x == 0) { Tout[ci] = NAN; if (status) status[ci] = lst; }
+        return;
+    }
+    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d);
+    const size_t B = (size_t)c.KL * c.KL;
+    cx<R>* X = ws + ch.ws_off;
+    cx<R>* G = X + B;
+    cx<R>* P = X + 2 * B;
+    cx<R>* Y = X + 3 * B;
+    int flag = 0;
+    for (int k = 0; k < c.ncol; ++k) {
+        load_col(c, k, s.kc, s.eps);
+        load_col(c, k - 1, s.kp, nullptr);
+        __syncthreads();
+        flag |= inv_column<R>(c, k, G, G, X, s, tm);
+        cl_sync(tm);               // g_k complete
+        strip_column<R>(c, k, G, P, P, Y, s, tm);
+        cl_sync(tm);               // P_k complete
+    }
+    if (tm.rank == 0) {
+        const double T = trace_T<R>(c, P, X, G, Y, s);
+        if (threadIdx.x == 0) {
+            const int st = chain_status(c, flag, T);
+            Tout[ci] = (st == ST_OK) ? T : NAN;
+            if (status) status[ci] = st;
+        }
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT, 1)
+sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
+                  int Kmax, double eta_d, const zd* __restrict__ leadout,
+                  const int* __restrict__ lead_status, const LeadDev* __restrict__ leads,
+                  cx<R>* __restrict__ ws, double* __restrict__ Tout, int32_t* __restrict__ status) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -107,23 +158,29 @@ static cudaError_t launch_sweep_t(const ChainDev* chains, const int* order, int 
                                   const LeadDev* leads, cx<R>* ws, double* T, int32_t* status,
                                   cudaStream_t st) {
     const size_t smem = sweep_smem_bytes(Kmax);
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    // Blocks per chain: the largest of 8, 4, 2, 1 with chains x C <= SMs.
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int C = 8;
+    while (C > 1 && (long long)nchains * C > nsm) C >>= 1;
+    auto kern = (C == 2) ? sweep_pipe_kernel<R> : sweep_team_kernel<R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * nchains, 1, 1);
+    cfg.gridDim = dim3(C * nchains, 1, 1);
     cfg.blockDim = dim3(NT, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, sweep_kernel<R>, chains, order, nchains, Kmax, eta_device,
-                              leadout, lead_status, leads, ws, T, status);
+    return cudaLaunchKernelEx(&cfg, kern, chains, order, nchains, Kmax, eta_device, leadout,
+                              lead_status, leads, ws, T, status);
 }
 
 cudaError_t launch_sweep(int precision, const ChainDev* chains, const int* order, int nchains,
