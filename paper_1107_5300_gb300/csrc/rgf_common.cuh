@@ -137,6 +137,25 @@ __device__ __forceinline__ zf cscale(zf a, double s) {
     df32 d = df_from_double(s);
     return {df_mul(a.re, d), df_mul(a.im, d)};
 }
+// Scale by a real constant already in double-float (no binary64 work).
+__device__ __forceinline__ zf cscale(zf a, df32 d) { return {df_mul(a.re, d), df_mul(a.im, d)}; }
+
+// 1/a in the working precision.  Binary64: one complex division.  Double-float:
+// d = |a|^2 in double-float, 1/d from the binary32 reciprocal of d.hi refined by
+// one Newton step r <- r + r (1 - d r) in double-float (doubles the ~24 correct
+// bits), then conj(a) / d -- all on the FP32 pipes.
+__device__ __forceinline__ zd crecip(zd a) {
+    const double d = a.re * a.re + a.im * a.im;
+    return {a.re / d, -a.im / d};
+}
+__device__ __forceinline__ zf crecip(zf a) {
+    const df32 d = df_add(df_mul(a.re, a.re), df_mul(a.im, a.im));
+    const float r0 = __frcp_rn(d.hi);
+    const df32 r0d = {r0, 0.0f};
+    const df32 e = df_sub(df32{1.0f, 0.0f}, df_mul(d, r0d));   // 1 - d r0
+    const df32 r = df_add(r0d, df_mul(r0d, e));
+    return {df_mul(a.re, r), df_neg(df_mul(a.im, r))};
+}
 
 // |a|^2 as a binary64 estimate (pivot selection only).
 __device__ __forceinline__ double cabs2(zd a) { return a.re * a.re + a.im * a.im; }

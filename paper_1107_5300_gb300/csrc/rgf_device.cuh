@@ -31,6 +31,15 @@ __device__ __forceinline__ void cl_sync(const Team& tm) {
     else __syncthreads();
 }
 
+// Broadcast of lane 0's complex value across the warp.
+__device__ __forceinline__ zd shfl0(zd v) {
+    return {__shfl_sync(0xffffffffu, v.re, 0), __shfl_sync(0xffffffffu, v.im, 0)};
+}
+__device__ __forceinline__ zf shfl0(zf v) {
+    return {{__shfl_sync(0xffffffffu, v.re.hi, 0), __shfl_sync(0xffffffffu, v.re.lo, 0)},
+            {__shfl_sync(0xffffffffu, v.im.hi, 0), __shfl_sync(0xffffffffu, v.im.lo, 0)}};
+}
+
 // ---------------------------------------------------------------------------
 // Block reductions
 // ---------------------------------------------------------------------------
@@ -131,9 +140,10 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
                     int gj = j0 + tx * 4 + c;
                     if (gj >= n) continue;
                     cx<R>* p = C + (size_t)gi * ldc + gj;
-                    if (mode == GEMM_SET) *p = acc[r][c];
-                    else if (mode == GEMM_ADD) *p = cadd(*p, acc[r][c]);
-                    else *p = csub(*p, acc[r][c]);
+                    const cx<R> v = acc[r][c];
+                    if (mode == GEMM_SET) *p = v;
+                    else if (mode == GEMM_ADD) *p = cadd(*p, v);
+                    else *p = csub(*p, v);
                 }
             }
         }
@@ -221,40 +231,44 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                     int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
                 }
-                // every lane knows the pivot row bi: all form its reciprocal,
-                // lanes < bb scale one entry of the pivot row each
-                zd pz = to_z(Pa[bi * bm + jj]);
-                double d = pz.re * pz.re + pz.im * pz.im;
-                int bad = 0;
-                if (!isfinite(d)) { bad = 2; d = 1.0; pz = {1.0, 0.0}; }
-                else if (!(d > 0.0)) { bad = 1; d = 1.0; pz = {1.0, 0.0}; }
-                else if (d < tiny2) { bad = 1; }
-                const zd iz = zd{pz.re / d, -pz.im / d};
-                const cx<R> invR = from_z<R>(iz.re, iz.im);
-                if (lane < bb) s.rowbuf[lane] = (lane == jj) ? invR : cmul(Pa[bi * bm + lane], invR);
+                // lane 0 checks the pivot and forms its reciprocal; lanes < bb
+                // then scale one entry of the pivot row each
+                cx<R> invR = czero<R>();
                 if (lane == 0) {
+                    cx<R> pv = Pa[bi * bm + jj];
+                    const double d = cabs2(pv);
+                    int bad = 0;
+                    if (!cfinite(pv) || !isfinite(d)) bad = 2;
+                    else if (!(d > 0.0)) bad = 1;
+                    else if (d < tiny2) bad = 1;
+                    if (bad) pv = from_z<R>(1.0, 0.0);
+                    invR = crecip(pv);
                     s.ctl[1] |= bad;
                     s.ctl[0] = bi;
                     s.perm[j] = bi;
-                    *s.inv = iz;
                     s.pinv[jj] = invR;
                 }
+                invR = shfl0(invR);
+                if (lane < bb) s.rowbuf[lane] = (lane == jj) ? invR : cmul(Pa[bi * bm + lane], invR);
             }
             __syncthreads();
             // One pass: row swap j <-> p folded in as an index remap, pivot row
             // scaled (rowbuf), column jj eliminated from every other row (old -> new).
+            // Threads: 16 columns x (NT / 16) rows per pass.
             const int p = s.ctl[0];
-            for (int e = tid; e < K * bb; e += NT) {
-                const int i = e / bb, l = e % bb;
-                const int si = (i == j) ? p : ((i == p) ? j : i);
+            const int l = tid & 15;
+            if (l < bb) {
                 const cx<R> r = s.rowbuf[l];
-                if (i == j) {
-                    Pb[i * bm + l] = r;
-                } else {
-                    const cx<R> m = Pa[si * bm + jj];
-                    const cx<R> a = (l == jj) ? czero<R>() : Pa[si * bm + l];
-                    Pb[i * bm + l] = cmac(a, m, r, true);
-                    if (l == jj) Cm[i * bm + jj] = m;
+                for (int i = tid >> 4; i < K; i += NT / 16) {
+                    const int si = (i == j) ? p : ((i == p) ? j : i);
+                    if (i == j) {
+                        Pb[i * bm + l] = r;
+                    } else {
+                        const cx<R> m = Pa[si * bm + jj];
+                        const cx<R> a = (l == jj) ? czero<R>() : Pa[si * bm + l];
+                        Pb[i * bm + l] = cmac(a, m, r, true);
+                        if (l == jj) Cm[i * bm + jj] = m;
+                    }
                 }
             }
             if (tid == 0) Cm[j * bm + jj] = czero<R>();
@@ -283,8 +297,9 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                     A[(size_t)p * lda + l] = a;
                 }
             }
+            for (int jj = 0; jj < bb; ++jj) Xr[jj * K + l] = A[(size_t)(j0 + jj) * lda + l];
             for (int jj = 0; jj < bb; ++jj) {
-                cx<R> x = A[(size_t)(j0 + jj) * lda + l];
+                cx<R> x = Xr[jj * K + l];
                 for (int q = 0; q < jj; ++q) x = cmac(x, Cm[(j0 + jj) * bm + q], Xr[q * K + l], true);
                 Xr[jj * K + l] = cmul(x, s.pinv[jj]);
             }

@@ -62,7 +62,8 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     cx<R>* ckpt = base + 12 * B;                       // nseg x (g, P)
     cx<R>* seg = ckpt + (size_t)nseg * 2 * B;          // (Sc + 1) x (g, P)
     double* grad = dT + ch.grad_off;
-    const double t = c.t, t2 = c.t2;
+    const auto t = Hop<R>::t(c);
+    const auto t2 = Hop<R>::t2(c);
 
     // Forward pass with checkpoints.
     int flag = 0;

@@ -67,6 +67,7 @@ struct ChainCtx {
     const uint8_t* rem;
     int N, L, M, KL, KR, ncol;
     double t, t2;
+    df32 tf, t2f;    // t and t^2 in double-float, converted once
     zd z;
     const zd *SigL, *SigR, *GamL, *GamR;
 };
@@ -84,6 +85,8 @@ __device__ inline ChainCtx make_ctx(const ChainDev& ch, const LeadDev& ld, const
     c.ncol = 4 * ch.L;
     c.t = ch.t;
     c.t2 = ch.t * ch.t;
+    c.tf = df_from_double(c.t);
+    c.t2f = df_from_double(c.t2);
     c.z = {ch.E, eta_d};
     c.SigL = leadout + ld.off;
     c.SigR = c.SigL + (size_t)c.KL * c.KL;
@@ -91,6 +94,17 @@ __device__ inline ChainCtx make_ctx(const ChainDev& ch, const LeadDev& ld, const
     c.GamR = c.GamL + (size_t)c.KL * c.KL;
     return c;
 }
+
+// The hopping t and t^2 in the working precision.
+template <class R> struct Hop;
+template <> struct Hop<double> {
+    static __device__ __forceinline__ double t(const ChainCtx& c) { return c.t; }
+    static __device__ __forceinline__ double t2(const ChainCtx& c) { return c.t2; }
+};
+template <> struct Hop<df32> {
+    static __device__ __forceinline__ df32 t(const ChainCtx& c) { return c.tf; }
+    static __device__ __forceinline__ df32 t2(const ChainCtx& c) { return c.t2f; }
+};
 
 __device__ __forceinline__ int col_size(const ChainCtx& c, int k) { return ((k & 3) < 2) ? c.KL : c.KR; }
 
@@ -158,7 +172,7 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
                     if (ka0 && kb1) sig = cadd(sig, Gprev[(size_t)a0 * KL + b1]);
                     if (ka1 && kb0) sig = cadd(sig, Gprev[(size_t)a1 * KL + b0]);
                     if (ka1 && kb1) sig = cadd(sig, Gprev[(size_t)a1 * KL + b1]);
-                    sig = cscale(sig, c.t2);
+                    sig = cscale(sig, Hop<R>::t2(c));
                 }
                 if (k == c.ncol - 1) sig = cadd(sig, ld_z<R>(c.SigR + (size_t)i * c.KR + l));
                 v = (i == l) ? from_z<R>(c.z.re - s.eps[i], c.z.im) : czero<R>();
@@ -203,7 +217,7 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
                 col_src(ct, l, Kp, a0, a1);
                 if (a0 >= 0 && s.kp[a0]) v = cadd(v, Pprev[(size_t)r * KL + a0]);
                 if (a1 >= 0 && s.kp[a1]) v = cadd(v, Pprev[(size_t)r * KL + a1]);
-                v = cscale(v, c.t);
+                v = cscale(v, Hop<R>::t(c));
             }
             Y[(size_t)r * KL + l] = v;
         }
