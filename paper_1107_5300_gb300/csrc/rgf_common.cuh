@@ -140,13 +140,14 @@ __device__ __forceinline__ zf cscale(zf a, double s) {
 // Scale by a real constant already in double-float (no binary64 work).
 __device__ __forceinline__ zf cscale(zf a, df32 d) { return {df_mul(a.re, d), df_mul(a.im, d)}; }
 
-// 1/a in the working precision.  Binary64: one complex division.  Double-float:
+// 1/a in the working precision.  Binary64: conj(a) times one reciprocal of
+// |a|^2.  Double-float:
 // d = |a|^2 in double-float, 1/d from the binary32 reciprocal of d.hi refined by
 // one Newton step r <- r + r (1 - d r) in double-float (doubles the ~24 correct
 // bits), then conj(a) / d -- all on the FP32 pipes.
 __device__ __forceinline__ zd crecip(zd a) {
-    const double d = a.re * a.re + a.im * a.im;
-    return {a.re / d, -a.im / d};
+    const double r = 1.0 / (a.re * a.re + a.im * a.im);
+    return {a.re * r, -a.im * r};
 }
 __device__ __forceinline__ zf crecip(zf a) {
     const df32 d = df_add(df_mul(a.re, a.re), df_mul(a.im, a.im));

@@ -171,7 +171,12 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
 //   -- the arithmetic of the unblocked algorithm in a different association,
 //   reading and writing each element once per block instead of once per pivot.
 //   The row swaps are undone at the end by a column permutation applied while
-//   copying into G.  Pivot reciprocals are formed in binary64.
+//   copying into G.  Pivot reciprocals are formed in the working precision
+//   (a Newton step on the binary32 reciprocal for double-float).  The pivot
+//   search is folded into the previous pass: the threads that produce the
+//   next pivot column rank its candidates by |a|^2 (binary32) and row index
+//   with a shared-memory atomic maximum.  The pivot test runs in binary32 and
+//   falls back to binary64 near its limits.
 //   With a team of C blocks (one cluster) every block reduces the panel (the
 //   same data, the same result) and updates only its own range of columns;
 //   the copy-out is split by rows.  G is complete after the caller's next
@@ -180,6 +185,16 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
 // amax2 = max |A_ij|^2 supplied by the caller (0 disables the test); bit 1 =
 // non-finite pivot.
 // ---------------------------------------------------------------------------
+// Ranking key of a pivot candidate: |a|^2 in binary32 (NaN ranked as +inf)
+// in the high word, the complement of the row in the low word -- the largest
+// key is the largest magnitude and, among equal magnitudes, the lowest row.
+template <class R>
+__device__ __forceinline__ unsigned long long pivot_key(cx<R> v, int i) {
+    float m = cabs2f(v);
+    if (isnan(m)) m = INFINITY;
+    return ((unsigned long long)__float_as_uint(m) << 32) | (0xFFFFFFFFu - (unsigned)i);
+}
+
 template <class R>
 struct GJSmem {
     cx<R>* rowbuf;   // [bmax]   scaled pivot row of the panel
@@ -192,6 +207,7 @@ struct GJSmem {
     int* perm;       // [Kmax]
     int* idx;        // [Kmax]
     int* ctl;        // [4]: pivot row, flag
+    unsigned long long* key;   // [3]  pivot keys, one per pass, rotating
     zd* inv;         // [1]
     int bmax;        // panel width
 };
@@ -207,70 +223,97 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
     const double tiny2 = amax2 * (64.0 * Unit<R>::u) * (64.0 * Unit<R>::u);
     const int clo = tm.lo(K), chi = tm.hi(K);     // this block's columns
     const int rlo = tm.lo(K), rhi = tm.hi(K);     // this block's rows (copy-out)
+    const float tiny2f = (float)tiny2;
     if (tid == 0) s.ctl[1] = 0;
+    if (tid < 3) s.key[tid] = 0ull;
+    __syncthreads();
     for (int j0 = 0; j0 < K; j0 += bm) {
         const int bb = min(bm, K - j0);
         cx<R>* Pa = s.panel;            // panel, current
         cx<R>* Pb = s.panel2;           // panel, next
+        unsigned long long kmax = 0ull;
         for (int e = tid; e < K * bb; e += NT) {
             int i = e / bb, jj = e % bb;
-            Pa[i * bm + jj] = A[(size_t)i * lda + j0 + jj];
+            const cx<R> v = A[(size_t)i * lda + j0 + jj];
+            Pa[i * bm + jj] = v;
+            if (jj == 0 && i >= j0) kmax = max(kmax, pivot_key(v, i));
         }
+        if (kmax) atomicMax(&s.key[j0 % 3], kmax);
         __syncthreads();
         for (int jj = 0; jj < bb; ++jj) {
             const int j = j0 + jj;
             if (warp == 0) {
-                float best = -1.0f;
-                int bi = j;
-                for (int i = j + lane; i < K; i += 32) {
-                    float v = cabs2f(Pa[i * bm + jj]);
-                    if (v > best || isnan(v)) { best = isnan(v) ? INFINITY : v; bi = i; }
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-                }
-                // lane 0 checks the pivot and forms its reciprocal; lanes < bb
+                // lane 0 takes the pivot row from the key the previous pass
+                // left, checks the pivot and forms its reciprocal; lanes < bb
                 // then scale one entry of the pivot row each
                 cx<R> invR = czero<R>();
+                int bi = 0;
                 if (lane == 0) {
+                    const unsigned long long kj = s.key[j % 3];
+                    bi = (int)(0xFFFFFFFFu - (unsigned)(kj & 0xFFFFFFFFull));
                     cx<R> pv = Pa[bi * bm + jj];
-                    const double d = cabs2(pv);
                     int bad = 0;
-                    if (!cfinite(pv) || !isfinite(d)) bad = 2;
-                    else if (!(d > 0.0)) bad = 1;
-                    else if (d < tiny2) bad = 1;
+                    const float df = cabs2f(pv);
+                    if (!cfinite(pv)) {
+                        bad = 2;
+                    } else if (!(df >= 1e-30f && df <= 1e30f && df >= 2.0f * tiny2f)) {
+                        const double d = cabs2(pv);       // borderline: decide in binary64
+                        if (!isfinite(d)) bad = 2;
+                        else if (!(d > 0.0)) bad = 1;
+                        else if (d < tiny2) bad = 1;
+                    }
                     if (bad) pv = from_z<R>(1.0, 0.0);
                     invR = crecip(pv);
                     s.ctl[1] |= bad;
                     s.ctl[0] = bi;
                     s.perm[j] = bi;
                     s.pinv[jj] = invR;
+                    s.key[(j + 2) % 3] = 0ull;   // read one pass ago, filled next pass
                 }
                 invR = shfl0(invR);
+                bi = __shfl_sync(0xffffffffu, bi, 0);
                 if (lane < bb) s.rowbuf[lane] = (lane == jj) ? invR : cmul(Pa[bi * bm + lane], invR);
             }
             __syncthreads();
             // One pass: row swap j <-> p folded in as an index remap, pivot row
-            // scaled (rowbuf), column jj eliminated from every other row (old -> new).
-            // Threads: 16 columns x (NT / 16) rows per pass.
+            // scaled (rowbuf), column jj eliminated from every other row (old ->
+            // new), and the candidates for the next pivot ranked on the fly.
+            // Threads: 16 columns x (NT / 16) rows, four rows per round (loads
+            // first, then the arithmetic).
             const int p = s.ctl[0];
             const int l = tid & 15;
+            kmax = 0ull;
             if (l < bb) {
                 const cx<R> r = s.rowbuf[l];
-                for (int i = tid >> 4; i < K; i += NT / 16) {
-                    const int si = (i == j) ? p : ((i == p) ? j : i);
-                    if (i == j) {
-                        Pb[i * bm + l] = r;
-                    } else {
-                        const cx<R> m = Pa[si * bm + jj];
-                        const cx<R> a = (l == jj) ? czero<R>() : Pa[si * bm + l];
-                        Pb[i * bm + l] = cmac(a, m, r, true);
-                        if (l == jj) Cm[i * bm + jj] = m;
+                constexpr int RS = NT / 16;
+                for (int i0 = tid >> 4; i0 < K; i0 += 4 * RS) {
+                    cx<R> mv[4], av[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = i0 + u * RS;
+                        const int si = (i == j) ? p : ((i == p) ? j : i);
+                        if (i < K && i != j) {
+                            mv[u] = Pa[si * bm + jj];
+                            av[u] = (l == jj) ? czero<R>() : Pa[si * bm + l];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = i0 + u * RS;
+                        if (i >= K) continue;
+                        if (i == j) {
+                            Pb[i * bm + l] = r;
+                        } else {
+                            const cx<R> v = cmac(av[u], mv[u], r, true);
+                            Pb[i * bm + l] = v;
+                            if (l == jj) Cm[i * bm + jj] = mv[u];
+                            if (l == jj + 1 && i > j) kmax = max(kmax, pivot_key(v, i));
+                        }
                     }
                 }
             }
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, 16));
+            if (lane == jj + 1 && kmax) atomicMax(&s.key[(j + 1) % 3], kmax);
             if (tid == 0) Cm[j * bm + jj] = czero<R>();
             if (p != j)                  // earlier multipliers follow their rows
                 for (int q = tid; q < jj; q += NT) {

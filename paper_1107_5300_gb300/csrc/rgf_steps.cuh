@@ -55,6 +55,7 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax) {
     s.gj.perm = (int*)take((size_t)Kmax * 4);
     s.gj.idx = (int*)take((size_t)Kmax * 4);
     s.gj.ctl = (int*)take(16);
+    s.gj.key = (unsigned long long*)take(32);
     s.kc = (uint8_t*)take((size_t)Kmax);
     s.kp = (uint8_t*)take((size_t)Kmax);
     s.kn = (uint8_t*)take((size_t)Kmax);

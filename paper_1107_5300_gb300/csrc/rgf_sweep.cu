@@ -49,6 +49,7 @@ size_t sweep_smem_bytes(int Kmax) {
     b += align16(16);                           // clmax
     b += align16((size_t)Kmax * 4) * 2;         // perm, idx
     b += align16(16);                           // ctl
+    b += align16(32);                           // pivot keys
     b += align16((size_t)Kmax) * 3;             // kc, kp, kn
     return b;
 }
