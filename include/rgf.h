@@ -164,6 +164,26 @@ rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, i
                                 int32_t* chain_status);
 
 /*
+ * Complex matrix product C = A B on the tcgen05 tensor cores: the dense
+ * product the recursion forms at every slice (Eqs. 4-5; the paper's CGEMM
+ * calls), here by exact bfloat16 digit slicing of double-float operands
+ * (Ozaki scheme: 7 signed base-256 digits per real value, per-row and
+ * per-column power-of-two scales), binary32 tensor-core accumulation that is
+ * exact for the three leading digit levels, and double-float recombination.
+ * The binary64 inputs are first rounded to double-float (48-bit significand).
+ * Accuracy per entry: a few units of 2^-48 times k max_j |A_mj| max_j |B_jn|.
+ *   A: device [m][lda], lda >= k;  B: device [k][ldb], ldb >= n;
+ *   C: device [m][ldc], ldc >= n;  complex binary64, interleaved (re, im),
+ *   row-major, leading dimensions in complex elements; C must not overlap
+ *   A or B.  Inputs are caller-owned and unchanged.
+ * Runs on `stream` and waits for it before returning.
+ * Errors: RGF_EINVAL (negative size, short leading dimension, NULL pointer),
+ * RGF_ECUDA, RGF_ETIMEOUT (a tensor-core completion wait gave up; C invalid).
+ */
+rgf_status rgf_zgemm_tc(int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                        double* C, int ldc, void* stream);
+
+/*
  * Allocation-free variant of rgf_conductance_dev (no counterpart in the paper).
  *
  * For callers that may not allocate device memory: e.g. a host application

@@ -1,0 +1,108 @@
+// rgf_tcgemm.cu -- rgf_zgemm_tc: the tensor-core complex product of the RGF
+// step (rgf_tc.cuh) as a stand-alone entry point, C = A B for binary64
+// complex matrices in device memory.  One 512-thread block per 128 rows of C.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "rgf.h"
+#include "rgf_tc.cuh"
+
+namespace rgf {
+
+void set_last_error(const std::string& msg);
+
+namespace {
+
+// Accessors of the binary64 operands (rounded to double-float on load) and
+// of the output (the sum of the groups of 128 inner entries).
+struct Z64Op {
+    const zd* A;
+    int lda;
+    const zd* B;
+    int ldb;
+    zd* C;
+    int ldc;
+    int m0;
+    __device__ zf a(int m, int k) const {
+        const zd v = A[(size_t)(m0 + m) * lda + k];
+        return from_z<df32>(v.re, v.im);
+    }
+    __device__ zf b(int k, int n) const {
+        const zd v = B[(size_t)k * ldb + n];
+        return from_z<df32>(v.re, v.im);
+    }
+    __device__ void out(int m, int n, int part, df32 v, bool first) const {
+        double* p = reinterpret_cast<double*>(C + (size_t)(m0 + m) * ldc + n) + part;
+        const double x = (double)v.hi + (double)v.lo;
+        *p = first ? x : *p + x;
+    }
+};
+
+// Dynamic shared memory of the kernel: the tensor-core area, raised so that
+// only one block fits on an SM (each block holds all 512 TMEM columns).
+constexpr size_t kSmem = tc::smem_bytes() > 120 * 1024 ? tc::smem_bytes() : 120 * 1024;
+
+__global__ void __launch_bounds__(NT, 1)
+zgemm_tc_kernel(int m, int n, int k, const zd* __restrict__ A, int lda, const zd* __restrict__ B,
+                int ldb, zd* __restrict__ C, int ldc, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const tc::Smem s = tc::carve(smem_raw);
+    uint32_t phase = tc::setup(s);
+    Z64Op op{A, lda, B, ldb, C, ldc, (int)blockIdx.x * 128};
+    tc::zgemm(op, min(128, m - op.m0), n, k, s, phase);
+    if (threadIdx.x == 0 && *(volatile int*)s.err) atomicExch(err, 1);
+    tc::teardown(s);
+}
+
+}  // namespace
+}  // namespace rgf
+
+extern "C" rgf_status rgf_zgemm_tc(int m, int n, int k, const double* A, int lda, const double* B,
+                                   int ldb, double* C, int ldc, void* stream) {
+    using namespace rgf;
+    if (m < 0 || n < 0 || k < 0 || lda < (k > 0 ? k : 1) || ldb < (n > 0 ? n : 1) ||
+        ldc < (n > 0 ? n : 1) || (m > 0 && n > 0 && (!C || (k > 0 && (!A || !B))))) {
+        set_last_error("rgf_zgemm_tc: bad sizes or NULL pointer");
+        return RGF_EINVAL;
+    }
+    if (m == 0 || n == 0) return RGF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (k == 0) {
+        e = cudaMemset2DAsync(C, (size_t)ldc * 16, 0, (size_t)n * 16, (size_t)m, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("rgf_zgemm_tc: ") + cudaGetErrorString(e));
+            return RGF_ECUDA;
+        }
+        return RGF_OK;
+    }
+    int* derr = nullptr;
+    int herr = 0;
+    e = cudaMallocAsync(&derr, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmem);
+    if (e == cudaSuccess) {
+        zgemm_tc_kernel<<<(m + 127) / 128, NT, kSmem, st>>>(m, n, k, (const zd*)A, lda,
+                                                            (const zd*)B, ldb, (zd*)C, ldc, derr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (derr) {
+        cudaError_t f = cudaFreeAsync(derr, st);
+        if (e == cudaSuccess) e = f;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("rgf_zgemm_tc: ") + cudaGetErrorString(e));
+        return RGF_ECUDA;
+    }
+    if (herr) {
+        set_last_error("rgf_zgemm_tc: a tensor-core completion wait gave up");
+        return RGF_ETIMEOUT;
+    }
+    return RGF_OK;
+}

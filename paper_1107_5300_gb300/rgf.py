@@ -26,7 +26,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENON
 # Symbols declared in include/rgf.h (checked by the CPU tests).
 EXPORTS = ["rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "rgf_free_ribbon",
            "rgf_lead_selfenergy", "rgf_conductance", "rgf_conductance_dev",
-           "rgf_conductance_grad", "rgf_conductance_noalloc", "rgf_profile_enable",
+           "rgf_conductance_grad", "rgf_conductance_noalloc", "rgf_zgemm_tc", "rgf_profile_enable",
            "rgf_profile_read", "rgf_status_str",
            "rgf_last_error", "rgf_version"]
 
@@ -59,6 +59,9 @@ lib.rgf_conductance_grad.argtypes = [C.POINTER(_vp), _dp, C.c_int, C.c_double, C
 lib.rgf_conductance_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, C.c_int,
                                         C.c_double, C.c_double, C.c_int, _vp, _vp, _vp]
 lib.rgf_conductance_noalloc.restype = C.c_int
+lib.rgf_zgemm_tc.argtypes = [C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int,
+                             _vp]
+lib.rgf_zgemm_tc.restype = C.c_int
 lib.rgf_profile_enable.argtypes = [C.c_int]
 lib.rgf_profile_enable.restype = C.c_int
 lib.rgf_profile_read.argtypes = [_dp, _dp]
@@ -236,6 +239,15 @@ def conductance_noalloc(N, L, t, onsite_ptr, removed_ptr, E_ptr, n, T_ptr, statu
                                      _vp(removed_ptr) if removed_ptr else None, _vp(E_ptr), int(n),
                                      float(eta_device), float(eta_lead), int(precision),
                                      _vp(stream), _vp(T_ptr), _vp(status_ptr) if status_ptr else None)
+    if check:
+        _check(st)
+    return st
+
+
+def zgemm_tc(A_ptr, B_ptr, C_ptr, m, n, k, lda=None, ldb=None, ldc=None, stream=0, check=True):
+    """C = A B on the tensor cores (device pointers to complex128 row-major data)."""
+    st = lib.rgf_zgemm_tc(int(m), int(n), int(k), _vp(A_ptr), int(lda or max(k, 1)), _vp(B_ptr),
+                          int(ldb or max(n, 1)), _vp(C_ptr), int(ldc or max(n, 1)), _vp(stream))
     if check:
         _check(st)
     return st
