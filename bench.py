@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "tc", "fp64"])
     ap.add_argument("--workload", default="agnr245_L4000_anderson")
     ap.add_argument("--cells", type=int, default=0, help="override L (profiling runs)")
     ap.add_argument("--energies", type=int, default=0, help="use only the first n energies")
@@ -204,7 +204,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1107_5300_gb300 import rgf
 
-    prec = rgf.RGF_MIXED if args.precision == "mixed" else rgf.RGF_FP64
+    prec = {"mixed": rgf.RGF_MIXED, "tc": rgf.RGF_MIXED_TC, "fp64": rgf.RGF_FP64}[args.precision]
     w, N, L, eps, rem, Es, seed = workload_arrays(args, rank)
     n = Es.size
     stream = torch.cuda.Stream()
@@ -264,7 +264,7 @@ def main():
 
     # Parity of this arm against the FP64 GPU path on the same ribbon (untimed).
     parity = None
-    if not args.no_check and prec == rgf.RGF_MIXED:
+    if not args.no_check and prec != rgf.RGF_FP64:
         T64, s64 = rgf.conductance(ribs, Es, 1e-8, 1e-8, rgf.RGF_FP64, check=False)
         both = ok & (s64 == 0)
         d = np.abs(T - T64)
@@ -294,7 +294,7 @@ def main():
     fl = flops_per_cell(N) * float(ok.sum()) * L
     sweep_s = statistics.mean(ms_sweep) / 1e3
     smax = float(peaks.get("sm_max_mhz", 2070.0))
-    if prec == rgf.RGF_MIXED:
+    if prec in (rgf.RGF_MIXED, rgf.RGF_MIXED_TC):
         # double-float arithmetic on the FP32 pipes: 54 FP32 instructions per
         # complex multiply-add (8 algorithmic flops); 152 SMs x 128 lanes.
         peak = 152 * 128 * smax * 1e6 * 8.0 / 54.0 / 1e12
@@ -312,7 +312,7 @@ def main():
             traffic = None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": f"sweep_kernel<{'df32' if prec else 'double'}>",
+            "kernel": {0: "sweep_kernel<double>", 1: "sweep_kernel<df32>", 2: "sweep_kernel<df32,tc>"}[prec],
             "peak_source": f"derived from unit counts and sm_max_mhz={smax:.0f} ({peaks_src})",
             "ms_sweep": statistics.mean(ms_sweep), "ms_lead": statistics.mean(ms_lead)}
 
@@ -328,7 +328,7 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f32x2" if prec == rgf.RGF_MIXED else "f64", "data": "synthetic",
+               "dtype": "f64" if prec == rgf.RGF_FP64 else "f32x2", "data": "synthetic",
                "config": {"workload": args.workload, "N": N, "M": 2 * N, "L": L, "energies": int(n),
                           "chains_ok": int(ok.sum()), "W_eV": w["W"], "eta_eV": 1e-8,
                           "precision": args.precision, "l2": "flushed (256 MB write) between steps",

@@ -15,7 +15,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#ifndef RGF_NT
+#define RGF_NT 512
+#endif
+
 namespace rgf {
+
+// Threads per block of the slice kernels (and warps).
+constexpr int NT = RGF_NT;
+constexpr int NWARP = NT / 32;
 
 // ---------------------------------------------------------------------------
 // double-float

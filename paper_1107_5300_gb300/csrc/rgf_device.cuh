@@ -7,16 +7,12 @@
 
 #include <cooperative_groups.h>
 
-#include "rgf_common.cuh"
+#include <type_traits>
 
-#ifndef RGF_NT
-#define RGF_NT 512
-#endif
+#include "rgf_common.cuh"
+#include "rgf_tc.cuh"
 
 namespace rgf {
-
-constexpr int NT = RGF_NT;
-constexpr int NWARP = NT / 32;
 
 // The blocks that share one chain: block `rank` of a cluster of C.  Work on
 // columns (or rows) is split into C contiguous ranges; cl_sync() is a cluster
@@ -210,6 +206,29 @@ struct GJSmem {
     unsigned long long* key;   // [3]  pivot keys, one per pass, rotating
     zd* inv;         // [1]
     int bmax;        // panel width
+    tc::State* tcs;  // tensor-core state for the rank-b update, or nullptr
+};
+
+// The rank-b update of cta_gj_invert as a tensor-core product over one tile
+// of up to 128 rows: A[i][l] -= sum_jj c_jj[i] x_jj[l] for the block's own
+// columns l outside the panel (column c of the product -> l = own_col(c)) and
+// every row i outside the panel.
+struct GJUpdateOp {
+    const zf* Cm;    // multipliers [K][bm]
+    const zf* Xr;    // substituted pivot rows [bm][K]
+    zf* A;
+    int bm, K, lda, r0, j0, bb, clo, ps, pskip;
+    __device__ int col(int c) const { const int l = clo + c; return l < ps ? l : l + pskip; }
+    __device__ zf a(int m, int k) const { return Cm[(r0 + m) * bm + k]; }
+    __device__ zf b(int k, int n) const { return Xr[k * K + col(n)]; }
+    __device__ void out(int m, int n, int part, df32 v, bool) const {
+        const int i = r0 + m;
+        if (i >= j0 && i < j0 + bb) return;
+        float* p = reinterpret_cast<float*>(A + (size_t)i * lda + col(n)) + 2 * part;
+        const df32 x = df_sub(df32{p[0], p[1]}, v);
+        p[0] = x.hi;
+        p[1] = x.lo;
+    }
 };
 
 template <class R>
@@ -354,8 +373,20 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         }
         __syncthreads();
         Pn = Pa;                         // the reduced panel
-        // ... then one rank-bb update of every other row.
-        const int Kh = (K + 1) >> 1, Ch = (nown + 1) >> 1;
+        // ... then one rank-bb update of every other row: on the tensor cores
+        // (double-float operands, exact digit slicing) or on the FP32 / FP64
+        // pipes.
+        bool tc_done = false;
+        if constexpr (std::is_same<R, df32>::value) {
+            if (s.tcs && nown > 0) {
+                for (int r0 = 0; r0 < K; r0 += 128) {
+                    GJUpdateOp op{Cm, Xr, A, bm, K, lda, r0, j0, bb, clo, ps, pskip};
+                    tc::zgemm(op, min(128, K - r0), nown, bb, s.tcs->s, s.tcs->phase);
+                }
+                tc_done = true;
+            }
+        }
+        const int Kh = (K + 1) >> 1, Ch = tc_done ? 0 : (nown + 1) >> 1;
         for (int tt = tid; tt < Kh * Ch; tt += NT) {
             const int i0 = 2 * (tt / Ch), c0 = 2 * (tt % Ch);
             const bool ok_i1 = i0 + 1 < K, ok_c1 = c0 + 1 < nown;

@@ -51,8 +51,9 @@ inline size_t sweep_ws_elems(int N) {
     return 5 * KL * KL + 1;
 }
 
-// Shared memory of the sweep / lead kernels for a largest column size Kmax.
-size_t sweep_smem_bytes(int Kmax);
+// Shared memory of the sweep / lead kernels for a largest column size Kmax
+// (tc: with the tensor-core area of the RGF_MIXED_TC path).
+size_t sweep_smem_bytes(int Kmax, bool tc = false);
 
 // Kernel launchers (return cudaGetLastError() after the launch).
 // One block per lead problem computes both leads; lead_status / lead_iters

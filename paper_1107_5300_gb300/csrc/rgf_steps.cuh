@@ -20,25 +20,33 @@ struct SweepSmem {
     double* eps;
     double* red;
     double* clmax;   // this block's partial max |A|^2, read by the team
+    tc::State* tcs;  // tensor-core state for the strip product, or nullptr
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Shared memory set aside for the tensor-core area (operand tiles, scales,
+// mbarrier) when the contractions run on the tensor cores.
+__host__ __device__ constexpr size_t tc_reserve(bool tc) { return tc ? tc::smem_bytes() + 1024 : 0; }
+
 // Panel width of the blocked Gauss-Jordan for a largest column size Kmax:
 // the widest of 16, 8, 4, 2 whose panel and pivot-row buffers fit next to the
-// rest of the shared memory.
-__host__ __device__ inline int gj_panel_width(int Kmax) {
+// rest of the shared memory (and the tensor-core area, if any).
+__host__ __device__ inline int gj_panel_width(int Kmax, bool tc = false) {
     int b = 16;
-    while (b > 2 && (size_t)4 * Kmax * b * 16 + (size_t)Kmax * 64 + 20000 > 220 * 1024) b >>= 1;
+    while (b > 2 && (size_t)4 * Kmax * b * 16 + (size_t)Kmax * 64 + 20000 + tc_reserve(tc) > 220 * 1024)
+        b >>= 1;
     return b;
 }
 
 template <class R>
-__device__ SweepSmem<R> carve(unsigned char* base, int Kmax) {
+__device__ SweepSmem<R> carve(unsigned char* base, int Kmax, bool tc = false) {
     SweepSmem<R> s;
     size_t o = 0;
     auto take = [&](size_t bytes) { unsigned char* p = base + o; o += align16(bytes); return p; };
-    const int bm = gj_panel_width(Kmax);
+    const int bm = gj_panel_width(Kmax, tc);
+    s.gj.tcs = nullptr;
+    s.tcs = nullptr;
     s.gj.bmax = bm;
     s.gj.panel = (cx<R>*)take((size_t)Kmax * bm * 16);
     s.gj.panel2 = (cx<R>*)take((size_t)Kmax * bm * 16);
@@ -140,6 +148,23 @@ __device__ inline void load_col(const ChainCtx& c, int k, uint8_t* km, double* e
 template <class R>
 __device__ __forceinline__ cx<R> ld_z(const zd* p) { return from_z<R>(p->re, p->im); }
 
+// The strip product Pout = Y Gk (columns lo.. of Gk and Pout) as a
+// tensor-core product over one tile of up to 128 rows of Y.
+struct StripOp {
+    const zf* Y;
+    const zf* G;
+    zf* P;
+    int KL, lo, r0;
+    __device__ zf a(int m, int k) const { return Y[(size_t)(r0 + m) * KL + k]; }
+    __device__ zf b(int k, int n) const { return G[(size_t)k * KL + lo + n]; }
+    __device__ void out(int m, int n, int part, df32 v, bool first) const {
+        float* p = reinterpret_cast<float*>(P + (size_t)(r0 + m) * KL + lo + n) + 2 * part;
+        if (!first) v = df_add(df32{p[0], p[1]}, v);
+        p[0] = v.hi;
+        p[1] = v.lo;
+    }
+};
+
 // The two halves of one forward column step k (row-major, leading dimension KL):
 //   inv_column:   X = A_k (K x K), Gout = A_k^-1 (Gauss-Jordan; Gout may alias
 //                 Gprev).  Needs s.kc / s.eps of column k and s.kp of column
@@ -224,8 +249,20 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
         }
     cl_sync(tm);                          // Y complete (Pprev no longer read)
     const int lo = tm.lo(K), n = tm.hi(K) - lo;
-    if (n > 0) cta_gemm<R, false, false>(KL, n, K, Y, KL, Gk + lo, KL, Pout + lo, KL, GEMM_SET, s.gemm);
-    else __syncthreads();
+    if (n <= 0) {
+        __syncthreads();
+        return;
+    }
+    if constexpr (std::is_same<R, df32>::value) {
+        if (s.tcs) {
+            for (int r0 = 0; r0 < KL; r0 += 128) {
+                StripOp op{Y, Gk, Pout, KL, lo, r0};
+                tc::zgemm(op, min(128, KL - r0), n, K, s.tcs->s, s.tcs->phase);
+            }
+            return;
+        }
+    }
+    cta_gemm<R, false, false>(KL, n, K, Y, KL, Gk + lo, KL, Pout + lo, KL, GEMM_SET, s.gemm);
 }
 
 // One whole forward column step on one block (used by the adjoint).
@@ -272,6 +309,7 @@ __device__ double trace_T(const ChainCtx& c, const cx<R>* P, cx<R>* Cz, cx<R>* X
 // Status word of a finished chain from the Gauss-Jordan flags and T.
 __device__ inline int chain_status(const ChainCtx& c, int flag, double T) {
     const double nch = (double)channels(c.N, c.t, c.z.re);
+    if (flag & 4) return ST_ETIMEOUT;
     if ((flag & 2) || !isfinite(T)) return ST_ENONFINITE;
     if (flag & 1) return ST_ESINGULAR;
     if (T < -1e-6 || T > nch + 1e-6) return ST_EBOUNDS;

@@ -30,14 +30,21 @@
 //          g_k by rows, the Gauss-Jordan panel redundantly (same data, same
 //          result), its substitution and rank-b update by columns, the strip
 //          product by columns; cluster barriers order the phases.
+// With TC (precision RGF_MIXED_TC) the two dense contractions of a column
+// step -- the Gauss-Jordan rank-b updates and the strip product -- run on the
+// tcgen05 tensor cores by exact digit slicing of their double-float operands
+// (rgf_tc.cuh); every block then holds the SM's TMEM for the whole launch.
 #include <cooperative_groups.h>
 
 #include "rgf_steps.cuh"
 
 namespace rgf {
 
-size_t sweep_smem_bytes(int Kmax) {
-    const int bm = gj_panel_width(Kmax);
+// Shared memory of the sweep itself (panels, buffers, masks) for a largest
+// column size Kmax; with tc the panel width leaves room for the tensor-core
+// area, which follows at the next 1024-byte boundary.
+__host__ __device__ size_t sweep_base_bytes(int Kmax, bool tc) {
+    const int bm = gj_panel_width(Kmax, tc);
     size_t b = 0;
     b += 4 * align16((size_t)Kmax * bm * 16);   // 2 panels, multipliers, pivot rows
     b += 2 * align16((size_t)bm * 16);          // rowbuf, pivot reciprocals
@@ -53,16 +60,31 @@ size_t sweep_smem_bytes(int Kmax) {
     b += align16((size_t)Kmax) * 3;             // kc, kp, kn
     return b;
 }
+__host__ __device__ inline size_t tc_offset(int Kmax) { return (sweep_base_bytes(Kmax, true) + 1023) & ~(size_t)1023; }
 
+size_t sweep_smem_bytes(int Kmax, bool tc) {
+    return tc ? tc_offset(Kmax) + tc::smem_bytes() : sweep_base_bytes(Kmax, false);
+}
+
+// Sets up the tensor-core area behind the sweep's shared memory (TMEM
+// allocation, mbarrier; every thread) and points the sweep's contractions at it.
 template <class R>
+__device__ void tc_attach(unsigned char* smem_raw, int Kmax, SweepSmem<R>& s, tc::State& st) {
+    st.s = tc::carve(smem_raw + tc_offset(Kmax));
+    st.phase = tc::setup(st.s);
+    s.gj.tcs = &st;
+    s.tcs = &st;
+}
+
+template <class R, bool TC>
 __global__ void __launch_bounds__(NT, 1)
 sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
              int Kmax, double eta_d, const zd* __restrict__ leadout,
              const int* __restrict__ lead_status, const LeadDev* __restrict__ leads,
              cx<R>* __restrict__ ws, double* __restrict__ Tout, int32_t* __restrict__ status) {
     namespace cg = cooperative_groups;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SweepSmem<R> s = carve<R>(smem_raw, Kmax);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    SweepSmem<R> s = carve<R>(smem_raw, Kmax, TC);
     cg::cluster_group cluster = cg::this_cluster();
     const Team tm{(int)cluster.block_rank(), (int)cluster.num_blocks()};
     const int ci = order[blockIdx.x / tm.C];
@@ -78,6 +100,8 @@ sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
     cx<R>* G = X + B;
     cx<R>* P = X + 2 * B;
     cx<R>* Y = X + 3 * B;
+    tc::State tst;
+    if constexpr (TC) tc_attach<R>(smem_raw, Kmax, s, tst);
     int flag = 0;
     for (int k = 0; k < c.ncol; ++k) {
         load_col(c, k, s.kc, s.eps);
@@ -87,6 +111,10 @@ sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
         cl_sync(tm);               // g_k complete
         strip_column<R>(c, k, G, P, P, Y, s, tm);
         cl_sync(tm);               // P_k complete
+    }
+    if constexpr (TC) {
+        if (*(volatile int*)tst.s.err) flag |= 4;
+        tc::teardown(tst.s);
     }
     if (tm.rank == 0) {
         const double T = trace_T<R>(c, P, X, G, Y, s);
@@ -98,7 +126,7 @@ sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
     }
 }
 
-template <class R>
+template <class R, bool TC>
 __global__ void __launch_bounds__(NT, 1)
 sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
                   int Kmax, double eta_d, const zd* __restrict__ leadout,
@@ -106,8 +134,8 @@ sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
                   cx<R>* __restrict__ ws, double* __restrict__ Tout, int32_t* __restrict__ status) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SweepSmem<R> s = carve<R>(smem_raw, Kmax);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    SweepSmem<R> s = carve<R>(smem_raw, Kmax, TC);
     const int role = (int)cluster.block_rank();      // 0: inverse, 1: strip
     const int ci = order[blockIdx.x >> 1];
     const ChainDev ch = chains[ci];
@@ -123,6 +151,8 @@ sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
     cx<R>* P = X + 3 * B;
     cx<R>* Y = X + 4 * B;
     int* flag_slot = reinterpret_cast<int*>(X + 5 * B);
+    tc::State tst;
+    if constexpr (TC) tc_attach<R>(smem_raw, Kmax, s, tst);
     if (role == 0) {
         int flag = 0;
         for (int k = 0; k < c.ncol; ++k) {
@@ -131,6 +161,10 @@ sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
             __syncthreads();
             flag |= inv_column<R>(c, k, Gb[(k + 1) & 1], Gb[k & 1], X, s);
             cluster.sync();        // g_k ready; block 1 is done with g_{k-1}
+        }
+        if constexpr (TC) {
+            if (*(volatile int*)tst.s.err) flag |= 4;
+            tc::teardown(tst.s);
         }
         if (threadIdx.x == 0) *flag_slot = flag;
         cluster.sync();
@@ -142,8 +176,13 @@ sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
             __syncthreads();
             strip_column<R>(c, k, Gb[k & 1], P, P, Y, s);
         }
+        int tflag = 0;
+        if constexpr (TC) {
+            if (*(volatile int*)tst.s.err) tflag = 4;
+            tc::teardown(tst.s);
+        }
         cluster.sync();
-        const int flag = *(volatile int*)flag_slot;
+        const int flag = *(volatile int*)flag_slot | tflag;
         const double T = trace_T<R>(c, P, X, Gb[0], Y, s);
         if (threadIdx.x == 0) {
             const int st = chain_status(c, flag, T);
@@ -153,19 +192,19 @@ sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
     }
 }
 
-template <class R>
+template <class R, bool TC>
 static cudaError_t launch_sweep_t(const ChainDev* chains, const int* order, int nchains, int Kmax,
                                   double eta_device, const zd* leadout, const int* lead_status,
                                   const LeadDev* leads, cx<R>* ws, double* T, int32_t* status,
                                   cudaStream_t st) {
-    const size_t smem = sweep_smem_bytes(Kmax);
+    const size_t smem = sweep_smem_bytes(Kmax, TC);
     // Blocks per chain: the largest of 8, 4, 2, 1 with chains x C <= SMs.
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int C = 8;
     while (C > 1 && (long long)nchains * C > nsm) C >>= 1;
-    auto kern = (C == 2) ? sweep_pipe_kernel<R> : sweep_team_kernel<R>;
+    auto kern = (C == 2) ? sweep_pipe_kernel<R, TC> : sweep_team_kernel<R, TC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -191,11 +230,17 @@ cudaError_t launch_sweep(int precision, const ChainDev* chains, const int* order
     if (nchains <= 0) return cudaSuccess;
     cudaError_t e;
     if (precision == 0)
-        e = launch_sweep_t<double>(chains, order, nchains, Kmax, eta_device, (const zd*)leadout,
-                                   lead_status, leads, (zd*)ws, T, status, st);
+        e = launch_sweep_t<double, false>(chains, order, nchains, Kmax, eta_device,
+                                          (const zd*)leadout, lead_status, leads, (zd*)ws, T,
+                                          status, st);
+    else if (precision == 2)
+        e = launch_sweep_t<df32, true>(chains, order, nchains, Kmax, eta_device,
+                                       (const zd*)leadout, lead_status, leads, (zf*)ws, T, status,
+                                       st);
     else
-        e = launch_sweep_t<df32>(chains, order, nchains, Kmax, eta_device, (const zd*)leadout,
-                                 lead_status, leads, (zf*)ws, T, status, st);
+        e = launch_sweep_t<df32, false>(chains, order, nchains, Kmax, eta_device,
+                                        (const zd*)leadout, lead_status, leads, (zf*)ws, T,
+                                        status, st);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

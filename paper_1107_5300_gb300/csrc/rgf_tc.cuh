@@ -39,7 +39,7 @@
 
 #include <cuda_bf16.h>
 
-#include "rgf_device.cuh"
+#include "rgf_common.cuh"
 
 namespace rgf {
 namespace tc {
@@ -63,6 +63,13 @@ struct Smem {
     unsigned long long* bar;   // MMA completion mbarrier
     uint32_t* tslot;      // TMEM base address (written by tcgen05.alloc)
     int* err;             // sticky: an MMA wait gave up
+};
+
+// Per-thread view of the tensor-core area plus the mbarrier phase this
+// thread expects next (every thread waits on every commit).
+struct State {
+    Smem s;
+    uint32_t phase;
 };
 
 __host__ __device__ constexpr size_t smem_bytes() {

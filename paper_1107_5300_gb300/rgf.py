@@ -19,7 +19,7 @@ lib = C.CDLL(str(_LIB_PATH))
 
 (RGF_OK, RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA, RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE,
  RGF_ETIMEOUT, RGF_EBOUNDS) = range(9)
-RGF_FP64, RGF_MIXED = 0, 1
+RGF_FP64, RGF_MIXED, RGF_MIXED_TC = 0, 1, 2
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENONFINITE", "ETIMEOUT",
                 "EBOUNDS"]
 

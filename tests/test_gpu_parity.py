@@ -66,7 +66,7 @@ def test_pristine_n11_energy_grid_fp64(rgflib):
     assert np.all(np.abs(T[nz] - 1.0) < 1e-5)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("N,L,W,p", [(2, 5, 0.3, 0.0), (3, 4, 0.2, 0.0), (5, 1, 0.25, 0.3),
                                      (11, 3, 0.25, 0.3), (12, 17, 0.4, 0.25), (23, 9, 0.25, 0.2),
                                      (64, 6, 0.1, 0.05), (150, 3, 0.25, 0.05)])
@@ -82,7 +82,7 @@ def test_disordered_rough_ribbons(rgflib, N, L, W, p, prec):
         assert abs(t - ref) < tol * max(1.0, abs(ref)), (N, L, e, t, ref)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_pristine_quantised_without_device_absorption(rgflib, prec):
     for N in (5, 12, 17):
         Es = np.array([0.15, -0.6, 1.4, -2.3])
@@ -103,10 +103,40 @@ def test_batched_uneven_chains_one_call(rgflib):
         ribs.append(rgflib.Ribbon(N, L, T_HOP, onsite=eps, removed=rem))
         Es.append(E)
         refs.append(_oracle_T(N, L, E, 1e-8, 1e-8, eps, rem))
-    for prec, tol in ((0, 1e-9), (1, 1e-7)):
+    for prec, tol in ((0, 1e-9), (1, 1e-7), (2, 1e-7)):
         T, st = rgflib.conductance(ribs, np.array(Es), 1e-8, 1e-8, prec)
         assert (st == 0).all()
         assert np.max(np.abs(T - np.array(refs))) < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_two_block_pipeline_schedule(rgflib, prec):
+    # 48 chains: two blocks per chain (inverse on one SM, strip product on the
+    # other), the schedule of the full-size workload
+    N, L = 40, 3
+    eps = workloads.anderson_onsite(N, L, 0.25, 77)
+    rem = workloads.edge_removed(N, L, 0.1, 78)
+    Es = np.linspace(-0.9, 0.9, 48) + 1e-3
+    T, st = _run(rgflib, N, L, Es, eps, rem, prec)
+    tol = 1e-9 if prec == 0 else 1e-7
+    assert (st == 0).all()
+    for e, t in zip(Es[::5], T[::5]):
+        ref = _oracle_T(N, L, e, 1e-8, 1e-8, eps, rem)
+        assert abs(t - ref) < tol * max(1.0, abs(ref)), (e, t, ref)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_columns_wider_than_one_tensor_tile(rgflib, prec):
+    # KL = 150 > 128 orbitals per column: the tensor-core products tile the rows
+    # and split the inner dimension into exact accumulation groups
+    N, L = 299, 2
+    eps = workloads.anderson_onsite(N, L, 0.2, 91)
+    Es = np.array([-0.35, 0.05, 0.6])
+    T, st = _run(rgflib, N, L, Es, eps, None, prec)
+    assert (st == 0).all()
+    for e, t in zip(Es, T):
+        ref = _oracle_T(N, L, e, 1e-8, 1e-8, eps, None)
+        assert abs(t - ref) < 1e-7 * max(1.0, abs(ref)), (e, t, ref)
 
 
 def test_failed_chain_does_not_spoil_the_batch(rgflib):
