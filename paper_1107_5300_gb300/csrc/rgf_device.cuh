@@ -149,33 +149,42 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
 
 // ---------------------------------------------------------------------------
 // Blocked Gauss-Jordan inverse with partial (row) pivoting.
-//   A (K x K, leading dim lda) is destroyed; A^-1 is written to G (ldg).
+//   A (K x K, leading dim lda, row-major on entry) is destroyed; A^-1 is written
+//   to G (row-major, ldg).  The elimination runs on W = A^T, which the
+//   row-major input already is when read column-major (W(i, l) = A[l*lda + i]):
+//   the columns of W are contiguous, so every column-wise phase below reads
+//   and writes contiguous memory.  The copy-out transposes back:
+//   A^-1 = (W^-1)^T.
 //   Pivots are taken in blocks of b columns.  For a block starting at j0 the
-//   K x b panel A[:, j0:j0+b] is copied to shared memory and reduced there by
+//   K x b panel W[:, j0:j0+b] is copied to shared memory and reduced there by
 //   the unblocked in-place steps (pick the row p >= j with the largest
-//   |A[p][j]|, swap rows j and p -- in the panel and in the rest of the matrix
-//   --, scale the pivot row by 1/A[j][j] keeping 1/A[j][j] in column j,
-//   eliminate column j from every other row keeping -A[i][j]/A[j][j] in
+//   |W[p][j]|, swap rows j and p -- in the panel and in the rest of the matrix
+//   --, scale the pivot row by 1/W[j][j] keeping 1/W[j][j] in column j,
+//   eliminate column j from every other row keeping -W[i][j]/W[j][j] in
 //   column j), recording for each step its multipliers c_jj[i] (column j at
 //   row i just before step jj) and its pivot reciprocal.  The columns outside
 //   the panel then receive the same b steps in two passes:
 //     pivot rows (forward substitution, then the later steps' eliminations)
-//       x_jj = (A[j0+jj][l] - sum_{jj' < jj} c_jj'[j0+jj] x_jj') / p_jj
-//       A[j0+jj][l] = x_jj - sum_{jj' > jj} c_jj'[j0+jj] x_jj'
+//       x_jj = (W[j0+jj][l] - sum_{jj' < jj} c_jj'[j0+jj] x_jj') / p_jj
+//       W[j0+jj][l] = x_jj - sum_{jj' > jj} c_jj'[j0+jj] x_jj'
 //     every other row (one rank-b update)
-//       A[i][l] -= sum_jj c_jj[i] x_jj
+//       W[i][l] -= sum_jj c_jj[i] x_jj
 //   -- the arithmetic of the unblocked algorithm in a different association,
 //   reading and writing each element once per block instead of once per pivot.
-//   The row swaps are undone at the end by a column permutation applied while
-//   copying into G.  Pivot reciprocals are formed in the working precision
-//   (a Newton step on the binary32 reciprocal for double-float).  The pivot
-//   search is folded into the previous pass: the threads that produce the
-//   next pivot column rank its candidates by |a|^2 (binary32) and row index
-//   with a shared-memory atomic maximum.  The pivot test runs in binary32 and
-//   falls back to binary64 near its limits.
+//   The substitution runs over all (pivot row, column) pairs of the block at
+//   once -- the forward part right-looking, one block barrier per pivot, the
+//   sums in the order above -- after the block's row swaps are applied to each
+//   column as one permutation.  The row swaps are undone at the end by a
+//   column permutation applied while copying into G.  Pivot reciprocals are
+//   formed in the working precision (a Newton step on the binary32
+//   reciprocal for double-float).  The pivot search is folded into the
+//   previous pass: the threads that produce the next pivot column rank its
+//   candidates by |a|^2 (binary32) and row index with a shared-memory atomic
+//   maximum.  The pivot test runs in binary32 and falls back to binary64 near
+//   its limits.
 //   With a team of C blocks (one cluster) every block reduces the panel (the
 //   same data, the same result) and updates only its own range of columns;
-//   the copy-out is split by rows.  G is complete after the caller's next
+//   the copy-out is split by rows of G.  G is complete after the caller's next
 //   cluster barrier.
 // Returns a flag: bit 0 = zero pivot, or a pivot below 64 u sqrt(amax2) with
 // amax2 = max |A_ij|^2 supplied by the caller (0 disables the test); bit 1 =
@@ -197,11 +206,12 @@ struct GJSmem {
     cx<R>* colbuf;   // [Kmax]   pivot column of the panel
     cx<R>* panel;    // [Kmax][bmax]  working panel
     cx<R>* panel2;   // [Kmax][bmax]  second panel buffer
-    cx<R>* mult;     // [Kmax][bmax]  multipliers c_jj[i]
+    cx<R>* mult;     // [bmax][Kmax]  multipliers c_jj[i] at mult[jj*K + i]
     cx<R>* xrow;     // [bmax][Kmax]  substituted pivot rows outside the panel
     cx<R>* pinv;     // [bmax]   pivot reciprocals
     int* perm;       // [Kmax]
-    int* idx;        // [Kmax]
+    int* idx;        // [Kmax]   row labels during the sweep, column order at the end
+    int* pm;         // [2 bmax + 1]  rows displaced by a panel's swaps: count, rows, sources
     int* ctl;        // [4]: pivot row, flag
     unsigned long long* key;   // [3]  pivot keys, one per pass, rotating
     zd* inv;         // [1]
@@ -210,24 +220,30 @@ struct GJSmem {
 };
 
 // The rank-b update of cta_gj_invert as a tensor-core product over one tile
-// of up to 128 rows: A[i][l] -= sum_jj c_jj[i] x_jj[l] for the block's own
+// of up to 128 rows: W[i][l] -= sum_jj c_jj[i] x_jj[l] for the block's own
 // columns l outside the panel (column c of the product -> l = own_col(c)) and
-// every row i outside the panel.
+// every row i outside the panel.  The multipliers and pivot rows are read from
+// shared memory (byte offsets into the dynamic shared memory); W is
+// column-major, so the 32 rows a warp drains are contiguous.
 struct GJUpdateOp {
-    const zf* Cm;    // multipliers [K][bm]
-    const zf* Xr;    // substituted pivot rows [bm][K]
+    int cm_off;      // multipliers [bm][K]
+    int xr_off;      // substituted pivot rows [bm][K]
     zf* A;
-    int bm, K, lda, r0, j0, bb, clo, ps, pskip;
+    int K, lda, r0, j0, bb, clo, ps, pskip;
     __device__ int col(int c) const { const int l = clo + c; return l < ps ? l : l + pskip; }
-    __device__ zf a(int m, int k) const { return Cm[(r0 + m) * bm + k]; }
-    __device__ zf b(int k, int n) const { return Xr[k * K + col(n)]; }
-    __device__ void out(int m, int n, int part, df32 v, bool) const {
+    __device__ zf a(int m, int k) const {
+        return reinterpret_cast<const zf*>(rgf_dyn_smem + cm_off)[k * K + r0 + m];
+    }
+    __device__ zf b(int k, int n) const {
+        return reinterpret_cast<const zf*>(rgf_dyn_smem + xr_off)[k * K + col(n)];
+    }
+    __device__ void out(int m, int n, df32 re, df32 im, bool) const {
         const int i = r0 + m;
         if (i >= j0 && i < j0 + bb) return;
-        float* p = reinterpret_cast<float*>(A + (size_t)i * lda + col(n)) + 2 * part;
-        const df32 x = df_sub(df32{p[0], p[1]}, v);
-        p[0] = x.hi;
-        p[1] = x.lo;
+        float4* p = reinterpret_cast<float4*>(A + (size_t)col(n) * lda + i);
+        const float4 x = *p;
+        const df32 r = df_sub(df32{x.x, x.y}, re), q = df_sub(df32{x.z, x.w}, im);
+        *p = make_float4(r.hi, r.lo, q.hi, q.lo);
     }
 };
 
@@ -240,11 +256,12 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
     cx<R>* Cm = s.mult;
     cx<R>* Xr = s.xrow;
     const double tiny2 = amax2 * (64.0 * Unit<R>::u) * (64.0 * Unit<R>::u);
-    const int clo = tm.lo(K), chi = tm.hi(K);     // this block's columns
-    const int rlo = tm.lo(K), rhi = tm.hi(K);     // this block's rows (copy-out)
+    const int clo = tm.lo(K), chi = tm.hi(K);     // this block's columns of W
+    const int rlo = tm.lo(K), rhi = tm.hi(K);     // this block's rows of G (copy-out)
     const float tiny2f = (float)tiny2;
     if (tid == 0) s.ctl[1] = 0;
     if (tid < 3) s.key[tid] = 0ull;
+    for (int i = tid; i < K; i += NT) s.idx[i] = i;
     __syncthreads();
     for (int j0 = 0; j0 < K; j0 += bm) {
         const int bb = min(bm, K - j0);
@@ -252,8 +269,8 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         cx<R>* Pb = s.panel2;           // panel, next
         unsigned long long kmax = 0ull;
         for (int e = tid; e < K * bb; e += NT) {
-            int i = e / bb, jj = e % bb;
-            const cx<R> v = A[(size_t)i * lda + j0 + jj];
+            const int i = e % K, jj = e / K;
+            const cx<R> v = A[(size_t)(j0 + jj) * lda + i];
             Pa[i * bm + jj] = v;
             if (jj == 0 && i >= j0) kmax = max(kmax, pivot_key(v, i));
         }
@@ -325,7 +342,7 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                         } else {
                             const cx<R> v = cmac(av[u], mv[u], r, true);
                             Pb[i * bm + l] = v;
-                            if (l == jj) Cm[i * bm + jj] = mv[u];
+                            if (l == jj) Cm[jj * K + i] = mv[u];
                             if (l == jj + 1 && i > j) kmax = max(kmax, pivot_key(v, i));
                         }
                     }
@@ -333,45 +350,82 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
             }
             kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, 16));
             if (lane == jj + 1 && kmax) atomicMax(&s.key[(j + 1) % 3], kmax);
-            if (tid == 0) Cm[j * bm + jj] = czero<R>();
+            if (tid == 0) Cm[jj * K + j] = czero<R>();
             if (p != j)                  // earlier multipliers follow their rows
                 for (int q = tid; q < jj; q += NT) {
-                    cx<R> a = Cm[j * bm + q];
-                    Cm[j * bm + q] = Cm[p * bm + q];
-                    Cm[p * bm + q] = a;
+                    cx<R> a = Cm[q * K + j];
+                    Cm[q * K + j] = Cm[q * K + p];
+                    Cm[q * K + p] = a;
                 }
             __syncthreads();
             cx<R>* t = Pa; Pa = Pb; Pb = t;
         }
-        // This block's columns outside the panel: the block's row swaps, then
-        // the pivot rows by substitution (one thread per column) ...
+        // The block's row swaps as one permutation: idx[r] = the row whose
+        // content row r holds after the swaps (identity outside the touched
+        // rows); pm lists the displaced rows outside the panel and their sources.
+        if (tid == 0) {
+            int n = 0;
+            for (int jj = 0; jj < bb; ++jj) {
+                const int j = j0 + jj, p = s.perm[j];
+                if (p != j) {
+                    const int a = s.idx[j]; s.idx[j] = s.idx[p]; s.idx[p] = a;
+                    if (p >= j0 + bb) s.pm[1 + n++] = p;
+                }
+            }
+            for (int t = 0; t < n; ++t) s.pm[1 + bm + t] = s.idx[s.pm[1 + t]];
+            s.pm[0] = n;
+        }
+        __syncthreads();
+        // This block's columns outside the panel: the swaps, then the pivot
+        // rows by substitution, one column per 16-lane half-warp ...
         const int ps = max(j0, clo), pe = min(j0 + bb, chi);
         const int pskip = max(0, pe - ps);
         const int nown = (chi - clo) - pskip;            // own columns outside the panel
         auto own_col = [&](int c) { int l = clo + c; return (l < ps) ? l : l + pskip; };
-        for (int c = tid; c < nown; c += NT) {
-            const int l = own_col(c);
-            for (int jj = 0; jj < bb; ++jj) {
-                const int j = j0 + jj, p = s.perm[j];
-                if (p != j) {
-                    cx<R> a = A[(size_t)j * lda + l];
-                    A[(size_t)j * lda + l] = A[(size_t)p * lda + l];
-                    A[(size_t)p * lda + l] = a;
+        {
+            // pivot rows after the swaps into Xr (x_0 scaled); tasks (r, c) with
+            // r fastest so that a warp reads contiguous rows of one column
+            for (int e = tid; e < bb * nown; e += NT) {
+                const int r = e % bb, c = e / bb, l = own_col(c);
+                cx<R> v = A[(size_t)l * lda + s.idx[j0 + r]];
+                if (r == 0) v = cmul(v, s.pinv[0]);
+                Xr[r * K + l] = v;
+            }
+            __syncthreads();
+            // rows outside the panel that took a panel row's content (the
+            // sources are panel rows, unchanged until the stores below)
+            const int npm = s.pm[0];
+            for (int e = tid; e < npm * nown; e += NT) {
+                const int t = e % npm, c = e / npm;
+                cx<R>* colp = A + (size_t)own_col(c) * lda;
+                colp[s.pm[1 + t]] = colp[s.pm[1 + bm + t]];
+            }
+            // forward substitution, right-looking: after step q every later
+            // pivot row has subtracted c_q x_q (the sums keep their order), and
+            // row q + 1 is final and scaled
+            for (int q = 0; q + 1 < bb; ++q) {
+                const int nr = bb - 1 - q;
+                for (int e = tid; e < nr * nown; e += NT) {
+                    const int r = q + 1 + e / nown, c = e % nown, l = own_col(c);
+                    cx<R> a = cmac(Xr[r * K + l], Cm[q * K + j0 + r], Xr[q * K + l], true);
+                    if (r == q + 1) a = cmul(a, s.pinv[r]);
+                    Xr[r * K + l] = a;
                 }
+                __syncthreads();
             }
-            for (int jj = 0; jj < bb; ++jj) Xr[jj * K + l] = A[(size_t)(j0 + jj) * lda + l];
-            for (int jj = 0; jj < bb; ++jj) {
-                cx<R> x = Xr[jj * K + l];
-                for (int q = 0; q < jj; ++q) x = cmac(x, Cm[(j0 + jj) * bm + q], Xr[q * K + l], true);
-                Xr[jj * K + l] = cmul(x, s.pinv[jj]);
-            }
-            for (int jj = 0; jj < bb; ++jj) {
-                cx<R> y = Xr[jj * K + l];
-                for (int q = jj + 1; q < bb; ++q) y = cmac(y, Cm[(j0 + jj) * bm + q], Xr[q * K + l], true);
-                A[(size_t)(j0 + jj) * lda + l] = y;
+            // the later steps' eliminations of the pivot rows, into W
+            for (int e = tid; e < bb * nown; e += NT) {
+                const int r = e % bb, c = e / bb, l = own_col(c);
+                cx<R> y = Xr[r * K + l];
+                for (int q = r + 1; q < bb; ++q) y = cmac(y, Cm[q * K + j0 + r], Xr[q * K + l], true);
+                A[(size_t)l * lda + j0 + r] = y;
             }
         }
         __syncthreads();
+        if (tid == 0) {                  // labels back to the identity
+            for (int jj = 0; jj < bb; ++jj) s.idx[j0 + jj] = j0 + jj;
+            for (int t = 0; t < s.pm[0]; ++t) s.idx[s.pm[1 + t]] = s.pm[1 + t];
+        }
         Pn = Pa;                         // the reduced panel
         // ... then one rank-bb update of every other row: on the tensor cores
         // (double-float operands, exact digit slicing) or on the FP32 / FP64
@@ -379,34 +433,37 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         bool tc_done = false;
         if constexpr (std::is_same<R, df32>::value) {
             if (s.tcs && nown > 0) {
+                const int cm_off = tc::dyn_off(Cm), xr_off = tc::dyn_off(Xr);
                 for (int r0 = 0; r0 < K; r0 += 128) {
-                    GJUpdateOp op{Cm, Xr, A, bm, K, lda, r0, j0, bb, clo, ps, pskip};
-                    tc::zgemm(op, min(128, K - r0), nown, bb, s.tcs->s, s.tcs->phase);
+                    const GJUpdateOp op{cm_off, xr_off, A, K, lda, r0, j0, bb, clo, ps, pskip};
+                    s.tcs->phase = tc::zgemm(op, min(128, K - r0), nown, bb, s.tcs->ar, s.tcs->phase);
                 }
                 tc_done = true;
             }
         }
         const int Kh = (K + 1) >> 1, Ch = tc_done ? 0 : (nown + 1) >> 1;
         for (int tt = tid; tt < Kh * Ch; tt += NT) {
-            const int i0 = 2 * (tt / Ch), c0 = 2 * (tt % Ch);
+            const int i0 = 2 * (tt % Kh), c0 = 2 * (tt / Kh);
             const bool ok_i1 = i0 + 1 < K, ok_c1 = c0 + 1 < nown;
             const int l0 = own_col(c0);
             const int l1 = ok_c1 ? own_col(c0 + 1) : l0;
             const bool r0 = i0 >= j0 && i0 < j0 + bb;
             const bool r1 = !ok_i1 || ((i0 + 1) >= j0 && (i0 + 1) < j0 + bb);
             if (r0 && r1) continue;
+            cx<R>* c0p = A + (size_t)l0 * lda;
+            cx<R>* c1p = A + (size_t)l1 * lda;
             cx<R> a00 = czero<R>(), a01 = czero<R>(), a10 = czero<R>(), a11 = czero<R>();
             if (!r0) {
-                a00 = A[(size_t)i0 * lda + l0];
-                if (ok_c1) a01 = A[(size_t)i0 * lda + l1];
+                a00 = c0p[i0];
+                if (ok_c1) a01 = c1p[i0];
             }
             if (!r1) {
-                a10 = A[(size_t)(i0 + 1) * lda + l0];
-                if (ok_c1) a11 = A[(size_t)(i0 + 1) * lda + l1];
+                a10 = c0p[i0 + 1];
+                if (ok_c1) a11 = c1p[i0 + 1];
             }
             for (int jj = 0; jj < bb; ++jj) {
-                const cx<R> p0 = r0 ? czero<R>() : Cm[i0 * bm + jj];
-                const cx<R> p1 = r1 ? czero<R>() : Cm[(i0 + 1) * bm + jj];
+                const cx<R> p0 = r0 ? czero<R>() : Cm[jj * K + i0];
+                const cx<R> p1 = r1 ? czero<R>() : Cm[jj * K + i0 + 1];
                 const cx<R> m0 = Xr[jj * K + l0];
                 const cx<R> m1 = ok_c1 ? Xr[jj * K + l1] : czero<R>();
                 a00 = cmac(a00, p0, m0, true);
@@ -415,18 +472,18 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                 a11 = cmac(a11, p1, m1, true);
             }
             if (!r0) {
-                A[(size_t)i0 * lda + l0] = a00;
-                if (ok_c1) A[(size_t)i0 * lda + l1] = a01;
+                c0p[i0] = a00;
+                if (ok_c1) c1p[i0] = a01;
             }
             if (!r1) {
-                A[(size_t)(i0 + 1) * lda + l0] = a10;
-                if (ok_c1) A[(size_t)(i0 + 1) * lda + l1] = a11;
+                c0p[i0 + 1] = a10;
+                if (ok_c1) c1p[i0 + 1] = a11;
             }
         }
-        // the reduced panel: this block's rows
+        // the reduced panel: this block's part of its rows
         for (int e = tid; e < (rhi - rlo) * bb; e += NT) {
-            int i = rlo + e / bb, jj = e % bb;
-            A[(size_t)i * lda + j0 + jj] = Pn[i * bm + jj];
+            const int i = rlo + e % (rhi - rlo), jj = e / (rhi - rlo);
+            A[(size_t)(j0 + jj) * lda + i] = Pn[i * bm + jj];
         }
         cl_sync(tm);
     }
@@ -438,10 +495,11 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         }
     }
     __syncthreads();
+    // G = (W^-1)^T with the row swaps undone: G[i][c] = W[c][idx[i]]
     for (int i = rlo + warp; i < rhi; i += NWARP) {
-        const cx<R>* row = A + (size_t)i * lda;
+        const cx<R>* col = A + (size_t)s.idx[i] * lda;
         cx<R>* grow = G + (size_t)i * ldg;
-        for (int c = lane; c < K; c += 32) grow[c] = row[s.idx[c]];
+        for (int c = lane; c < K; c += 32) grow[c] = col[c];
     }
     const int flag = s.ctl[1];
     __syncthreads();

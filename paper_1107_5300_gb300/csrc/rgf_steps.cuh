@@ -62,6 +62,7 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax, bool tc = false) {
     s.clmax = (double*)take(16);
     s.gj.perm = (int*)take((size_t)Kmax * 4);
     s.gj.idx = (int*)take((size_t)Kmax * 4);
+    s.gj.pm = (int*)take((size_t)(2 * bm + 1) * 4);
     s.gj.ctl = (int*)take(16);
     s.gj.key = (unsigned long long*)take(32);
     s.kc = (uint8_t*)take((size_t)Kmax);
@@ -157,11 +158,14 @@ struct StripOp {
     int KL, lo, r0;
     __device__ zf a(int m, int k) const { return Y[(size_t)(r0 + m) * KL + k]; }
     __device__ zf b(int k, int n) const { return G[(size_t)k * KL + lo + n]; }
-    __device__ void out(int m, int n, int part, df32 v, bool first) const {
-        float* p = reinterpret_cast<float*>(P + (size_t)(r0 + m) * KL + lo + n) + 2 * part;
-        if (!first) v = df_add(df32{p[0], p[1]}, v);
-        p[0] = v.hi;
-        p[1] = v.lo;
+    __device__ void out(int m, int n, df32 re, df32 im, bool first) const {
+        float4* p = reinterpret_cast<float4*>(P + (size_t)(r0 + m) * KL + lo + n);
+        if (!first) {
+            const float4 x = *p;
+            re = df_add(df32{x.x, x.y}, re);
+            im = df_add(df32{x.z, x.w}, im);
+        }
+        *p = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
 };
 
@@ -256,8 +260,8 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
     if constexpr (std::is_same<R, df32>::value) {
         if (s.tcs) {
             for (int r0 = 0; r0 < KL; r0 += 128) {
-                StripOp op{Y, Gk, Pout, KL, lo, r0};
-                tc::zgemm(op, min(128, KL - r0), n, K, s.tcs->s, s.tcs->phase);
+                const StripOp op{Y, Gk, Pout, KL, lo, r0};
+                s.tcs->phase = tc::zgemm(op, min(128, KL - r0), n, K, s.tcs->ar, s.tcs->phase);
             }
             return;
         }

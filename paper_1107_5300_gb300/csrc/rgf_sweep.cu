@@ -55,6 +55,7 @@ __host__ __device__ size_t sweep_base_bytes(int Kmax, bool tc) {
     b += align16(NWARP * 8);                    // red
     b += align16(16);                           // clmax
     b += align16((size_t)Kmax * 4) * 2;         // perm, idx
+    b += align16((size_t)(2 * bm + 1) * 4);     // displaced rows of a panel
     b += align16(16);                           // ctl
     b += align16(32);                           // pivot keys
     b += align16((size_t)Kmax) * 3;             // kc, kp, kn
@@ -70,8 +71,8 @@ size_t sweep_smem_bytes(int Kmax, bool tc) {
 // allocation, mbarrier; every thread) and points the sweep's contractions at it.
 template <class R>
 __device__ void tc_attach(unsigned char* smem_raw, int Kmax, SweepSmem<R>& s, tc::State& st) {
-    st.s = tc::carve(smem_raw + tc_offset(Kmax));
-    st.phase = tc::setup(st.s);
+    st.ar = tc::Area{(int)tc_offset(Kmax)};
+    st.phase = tc::setup(st.ar);
     s.gj.tcs = &st;
     s.tcs = &st;
 }
@@ -113,8 +114,8 @@ sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
         cl_sync(tm);               // P_k complete
     }
     if constexpr (TC) {
-        if (*(volatile int*)tst.s.err) flag |= 4;
-        tc::teardown(tst.s);
+        if (*(volatile int*)tst.ar.err()) flag |= 4;
+        tc::teardown(tst.ar);
     }
     if (tm.rank == 0) {
         const double T = trace_T<R>(c, P, X, G, Y, s);
@@ -163,8 +164,8 @@ sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
             cluster.sync();        // g_k ready; block 1 is done with g_{k-1}
         }
         if constexpr (TC) {
-            if (*(volatile int*)tst.s.err) flag |= 4;
-            tc::teardown(tst.s);
+            if (*(volatile int*)tst.ar.err()) flag |= 4;
+            tc::teardown(tst.ar);
         }
         if (threadIdx.x == 0) *flag_slot = flag;
         cluster.sync();
@@ -178,8 +179,8 @@ sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
         }
         int tflag = 0;
         if constexpr (TC) {
-            if (*(volatile int*)tst.s.err) tflag = 4;
-            tc::teardown(tst.s);
+            if (*(volatile int*)tst.ar.err()) tflag = 4;
+            tc::teardown(tst.ar);
         }
         cluster.sync();
         const int flag = *(volatile int*)flag_slot | tflag;

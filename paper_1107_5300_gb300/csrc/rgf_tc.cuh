@@ -25,12 +25,12 @@
 // the product is accurate to a few units of 2^-48 of (row max x column max x
 // inner dimension), the accuracy of the double-float arithmetic it replaces.
 //
-// Complex products use the real 2 x 2 block form
-//     [Re C | Im C] = A' B',  A'[m][2k] = Re A, A'[m][2k+1] = Im A,
-//     B'[2k][n] = Re B, B'[2k+1][n] = -Im B  (Re columns),
-//     B'[2k][n'] = Im B, B'[2k+1][n'] = Re B (Im columns),
+// Complex products use the real 2 x 2 block form C' = A' B' with
+//     A'[m][2k] = Re A[m][k],  A'[m][2k+1] = Im A[m][k],
+//     B'[2k][2n] = Re B[k][n], B'[2k+1][2n] = -Im B[k][n]      (C'[m][2n] = Re C),
+//     B'[2k][2n+1] = Im B[k][n], B'[2k+1][2n+1] = Re B[k][n]   (C'[m][2n+1] = Im C),
 // so one MMA chain (M = 128, N = 2 x columns, K = 16 per instruction, bf16 x
-// bf16 -> f32) gives both parts.  Operands are staged in shared memory by the
+// bf16 -> f32) gives both parts, side by side in TMEM.  Operands are staged in shared memory by the
 // threads that slice them (K-major, no swizzle: 8-row x 16-byte core
 // matrices, 128 B apart along K and 256 B apart along M/N); one elected
 // thread issues the MMAs and commits them to an mbarrier; the accumulators
@@ -52,50 +52,61 @@ constexpr int ACOLS = 2 * MAXC;      // TMEM columns per accumulator (5 x 96 <= 
 constexpr int KCH = 8;               // complex inner entries per chunk (16 real-block k)
 constexpr int KGRP = 128;            // complex inner entries per exact accumulation group
 
-struct Smem {
-    __nv_bfloat16* a;     // [S][TILE]  digit tiles of A'
-    __nv_bfloat16* b;     // [S][TILE]  digit tiles of B'
-    float* rsc;           // [128] row slicing scale 2^(7-e)
-    float* rfac;          // [128] row output factor 2^(e-7)
-    float* csc;           // [MAXC] column slicing scale
-    float* cfac;          // [MAXC] column output factor
-    unsigned* cmax;       // [MAXC] column maxima (binary32 bits)
-    unsigned long long* bar;   // MMA completion mbarrier
-    uint32_t* tslot;      // TMEM base address (written by tcgen05.alloc)
-    int* err;             // sticky: an MMA wait gave up
-};
+// Byte offsets inside the tensor-core area of shared memory.
+constexpr int OFF_A = 0;                          // [S][TILE] bf16 digit tiles of A'
+constexpr int OFF_B = OFF_A + S * TILE * 2;       // [S][TILE] bf16 digit tiles of B'
+constexpr int OFF_RSC = OFF_B + S * TILE * 2;     // [128] row slicing scales 2^(7-e)
+constexpr int OFF_RFAC = OFF_RSC + 128 * 4;       // [128] row output factors 2^(e-7)
+constexpr int OFF_CSC = OFF_RFAC + 128 * 4;       // [MAXC] column slicing scales
+constexpr int OFF_CFAC = OFF_CSC + MAXC * 4;      // [MAXC] column output factors
+constexpr int OFF_CMAX = OFF_CFAC + MAXC * 4;     // [MAXC] column maxima (binary32 bits)
+constexpr int OFF_BAR = OFF_CMAX + MAXC * 4;      // MMA completion mbarrier (8 bytes)
+constexpr int OFF_TSLOT = OFF_BAR + 8;            // TMEM base address (tcgen05.alloc)
+constexpr int OFF_ERR = OFF_TSLOT + 4;            // sticky: an MMA wait gave up
+constexpr int BYTES = (OFF_ERR + 4 + 15) / 16 * 16;
+static_assert(OFF_BAR % 8 == 0 && BYTES % 16 == 0, "tensor-core area layout");
 
-// Per-thread view of the tensor-core area plus the mbarrier phase this
-// thread expects next (every thread waits on every commit).
-struct State {
-    Smem s;
-    uint32_t phase;
-};
+__host__ __device__ constexpr size_t smem_bytes() { return (size_t)BYTES; }
 
-__host__ __device__ constexpr size_t smem_bytes() {
-    return (size_t)2 * S * TILE * 2 + 2 * 128 * 4 + 3 * MAXC * 4 + 64;
-}
+}  // namespace tc
+}  // namespace rgf
 
-// Carves the tensor-core area from `base` (1024-byte aligned offsets inside).
-__device__ inline Smem carve(unsigned char* base) {
-    Smem s;
-    s.a = reinterpret_cast<__nv_bfloat16*>(base);
-    s.b = s.a + S * TILE;
-    float* f = reinterpret_cast<float*>(s.b + S * TILE);
-    s.rsc = f;
-    s.rfac = f + 128;
-    s.csc = f + 256;
-    s.cfac = s.csc + MAXC;
-    s.cmax = reinterpret_cast<unsigned*>(s.cfac + MAXC);
-    s.bar = reinterpret_cast<unsigned long long*>(s.cmax + MAXC);
-    s.tslot = reinterpret_cast<uint32_t*>(s.bar + 1);
-    s.err = reinterpret_cast<int*>(s.tslot + 1);
-    return s;
-}
+// The block's dynamic shared memory (every extern __shared__ array aliases it).
+extern __shared__ __align__(1024) unsigned char rgf_dyn_smem[];
+
+namespace rgf {
+namespace tc {
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+// Byte offset of a shared-memory pointer from the start of dynamic shared memory.
+__device__ __forceinline__ int dyn_off(const void* p) { return (int)(su32(p) - su32(rgf_dyn_smem)); }
+
+// The tensor-core area, `off` bytes into dynamic shared memory.  Passed by
+// value (one integer); every accessor is a shared-memory address.
+struct Area {
+    int off;
+    __device__ unsigned char* base() const { return rgf_dyn_smem + off; }
+    __device__ __nv_bfloat16* a() const { return reinterpret_cast<__nv_bfloat16*>(base() + OFF_A); }
+    __device__ __nv_bfloat16* b() const { return reinterpret_cast<__nv_bfloat16*>(base() + OFF_B); }
+    __device__ float* rsc() const { return reinterpret_cast<float*>(base() + OFF_RSC); }
+    __device__ float* rfac() const { return reinterpret_cast<float*>(base() + OFF_RFAC); }
+    __device__ float* csc() const { return reinterpret_cast<float*>(base() + OFF_CSC); }
+    __device__ float* cfac() const { return reinterpret_cast<float*>(base() + OFF_CFAC); }
+    __device__ unsigned* cmax() const { return reinterpret_cast<unsigned*>(base() + OFF_CMAX); }
+    __device__ unsigned long long* bar() const { return reinterpret_cast<unsigned long long*>(base() + OFF_BAR); }
+    __device__ uint32_t* tslot() const { return reinterpret_cast<uint32_t*>(base() + OFF_TSLOT); }
+    __device__ int* err() const { return reinterpret_cast<int*>(base() + OFF_ERR); }
+};
+
+// The area plus the mbarrier phase this thread expects next (every thread
+// waits on every commit, so every thread tracks the same phase).
+struct State {
+    Area ar;
+    uint32_t phase;
+};
 
 // Element offset of (row r, k) inside one 128 x 16 K-major tile.
 __device__ __forceinline__ int tile_off(int r, int k) {
@@ -160,16 +171,16 @@ __device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.
 // Allocates all 512 TMEM columns (warp 0) and initialises the mbarrier.  Must
 // be called by every thread of the block (it ends with a barrier); the block
 // must be the only one on its SM that uses TMEM.  Returns the initial phase.
-__device__ inline uint32_t setup(const Smem& s) {
+__device__ inline uint32_t setup(Area ar) {
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
-                     :: "r"(su32(s.tslot)) : "memory");
+                     :: "r"(su32(ar.tslot())) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(s.bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(ar.bar())) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *s.err = 0;
+        *ar.err() = 0;
     }
     fence_before();
     __syncthreads();
@@ -178,30 +189,30 @@ __device__ inline uint32_t setup(const Smem& s) {
 }
 
 // Releases TMEM.  Every thread; no MMA may be in flight.
-__device__ inline void teardown(const Smem& s) {
+__device__ inline void teardown(Area ar) {
     fence_before();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(*s.tslot) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(*ar.tslot()) : "memory");
 }
 
 // Waits (every thread) for the MMAs committed last; gives up after about a
 // second of device clock and sets the sticky error flag, after which later
-// waits return at once.
-__device__ inline void wait_mma(const Smem& s, uint32_t& phase) {
-    if (!*(volatile int*)s.err) {
-        bool done = try_wait(s.bar, phase);
+// waits return at once.  Returns the next phase.
+__device__ inline uint32_t wait_mma(Area ar, uint32_t phase) {
+    if (!*(volatile int*)ar.err()) {
+        bool done = try_wait(ar.bar(), phase);
         if (!done) {
             const long long t0 = clock64();
             while (!done) {
-                done = try_wait(s.bar, phase);
+                done = try_wait(ar.bar(), phase);
                 if (!done && clock64() - t0 > 2000000000ll) break;
             }
-            if (!done) *(volatile int*)s.err = 1;
+            if (!done) *(volatile int*)ar.err() = 1;
         }
     }
-    phase ^= 1u;
     fence_after();
+    return phase ^ 1u;
 }
 
 // The S signed base-256 digits of the double-float value (h, l) times the
@@ -262,18 +273,26 @@ __device__ __forceinline__ df32 combine(float a0, float a1, float a2, float a3, 
 }
 
 // C op= A B, A: M x Kc (M <= 128), B: Kc x N, complex double-float, through the
-// accessor object `op`:
-//   zf  op.a(m, k), op.b(k, n)                      operand entries
-//   void op.out(m, n, part, df32 v, bool first)     v = Re (part 0) or Im (part 1)
-//                                                   of (A B)[m][n] over one group
-//                                                   of up to 128 inner entries;
-//                                                   first = the first group.
+// accessor object `op` (passed by value):
+//   zf  op.a(m, k), op.b(k, n)                   operand entries
+//   void op.out(m, n, df32 re, df32 im, bool first)
+//                                                (A B)[m][n] over one group of up
+//                                                to 128 inner entries; first =
+//                                                the first group.
 // Called by every thread of the block (NT = 512); ends with a barrier.
+// Returns the next mbarrier phase.
 template <class Op>
-__device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, uint32_t& phase) {
+__device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, uint32_t phase) {
     static_assert(NT == 512, "zgemm assumes 512 threads");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t tmem = *s.tslot;
+    const uint32_t tmem = *ar.tslot();
+    float* rsc = ar.rsc();
+    float* rfac = ar.rfac();
+    float* csc = ar.csc();
+    float* cfac = ar.cfac();
+    unsigned* cmax = ar.cmax();
+    __nv_bfloat16* ta = ar.a();
+    __nv_bfloat16* tb = ar.b();
     for (int g0 = 0; g0 < Kc; g0 += KGRP) {
         const int kg = min(KGRP, Kc - g0);
         // row scales over this group
@@ -286,13 +305,13 @@ __device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, 
                 }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane == 0) scales(mx, s.rsc[m], s.rfac[m]);
+            if (lane == 0) scales(mx, rsc[m], rfac[m]);
         }
         for (int n0 = 0; n0 < N; n0 += MAXC) {
             const int nc = min(MAXC, N - n0);
             const int ncp = (nc + 7) & ~7;
-            const int NR = 2 * ncp;               // real output columns [Re ncp | Im ncp]
-            if (tid < MAXC) s.cmax[tid] = 0u;
+            const int NR = 2 * ncp;               // real output columns (Re, Im interleaved)
+            if (tid < MAXC) cmax[tid] = 0u;
             __syncthreads();
             if (tid < (NT / MAXC) * MAXC) {
                 const int c = tid % MAXC, ks = tid / MAXC;
@@ -302,10 +321,10 @@ __device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, 
                         const zf v = op.b(g0 + k, n0 + c);
                         mx = nmax(mx, nmax(fabsf(v.re.hi), fabsf(v.im.hi)));
                     }
-                if (c < nc) atomicMax(&s.cmax[c], __float_as_uint(mx));
+                if (c < nc) atomicMax(&cmax[c], __float_as_uint(mx));
             }
             __syncthreads();
-            if (tid < MAXC) scales(__uint_as_float(s.cmax[tid]), s.csc[tid], s.cfac[tid]);
+            if (tid < MAXC) scales(__uint_as_float(cmax[tid]), csc[tid], cfac[tid]);
             __syncthreads();
             uint32_t init = 0u;
             for (int k0 = 0; k0 < kg; k0 += KCH) {
@@ -316,7 +335,7 @@ __device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, 
                     float dr[S], di[S];
                     if (m < M && k0 + k < kg) {
                         const zf v = op.a(m, g0 + k0 + k);
-                        const float sc = s.rsc[m];
+                        const float sc = rsc[m];
                         digits(v.re.hi, v.re.lo, sc, dr);
                         digits(v.im.hi, v.im.lo, sc, di);
                     } else {
@@ -327,7 +346,7 @@ __device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, 
 #pragma unroll
                     for (int i = 0; i < S; ++i) {
                         const float w = dweight(i);
-                        *reinterpret_cast<__nv_bfloat162*>(s.a + i * TILE + o) =
+                        *reinterpret_cast<__nv_bfloat162*>(ta + i * TILE + o) =
                             __floats2bfloat162_rn(dr[i] * w, di[i] * w);
                     }
                 }
@@ -338,20 +357,20 @@ __device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, 
                         float dr[S], di[S];
                         if (c < nc && k0 + k < kg) {
                             const zf v = op.b(g0 + k0 + k, n0 + c);
-                            const float sc = s.csc[c];
+                            const float sc = csc[c];
                             digits(v.re.hi, v.re.lo, sc, dr);
                             digits(v.im.hi, v.im.lo, sc, di);
                         } else {
 #pragma unroll
                             for (int i = 0; i < S; ++i) { dr[i] = 0.0f; di[i] = 0.0f; }
                         }
-                        const int ore = tile_off(c, 2 * k), oim = tile_off(ncp + c, 2 * k);
+                        const int ore = tile_off(2 * c, 2 * k), oim = tile_off(2 * c + 1, 2 * k);
 #pragma unroll
                         for (int i = 0; i < S; ++i) {
                             const float w = dweight(i);
-                            *reinterpret_cast<__nv_bfloat162*>(s.b + i * TILE + ore) =
+                            *reinterpret_cast<__nv_bfloat162*>(tb + i * TILE + ore) =
                                 __floats2bfloat162_rn(dr[i] * w, -di[i] * w);
-                            *reinterpret_cast<__nv_bfloat162*>(s.b + i * TILE + oim) =
+                            *reinterpret_cast<__nv_bfloat162*>(tb + i * TILE + oim) =
                                 __floats2bfloat162_rn(di[i] * w, dr[i] * w);
                         }
                     }
@@ -366,20 +385,20 @@ __device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, 
 #pragma unroll
                         for (int i = 0; i <= l; ++i) {
                             const int j = l - i, acc = l < NACC - 1 ? l : NACC - 1;
-                            mma(tmem + (uint32_t)(ACOLS * acc), sdesc(s.a + i * TILE), sdesc(s.b + j * TILE), id,
-                                (init >> acc) & 1u);
+                            mma(tmem + (uint32_t)(ACOLS * acc), sdesc(ta + i * TILE), sdesc(tb + j * TILE),
+                                id, (init >> acc) & 1u);
                             init |= 1u << acc;
                         }
-                    commit(s.bar);
+                    commit(ar.bar());
                 }
-                wait_mma(s, phase);     // tiles may be rewritten; accumulators final
+                phase = wait_mma(ar, phase);   // tiles may be rewritten; accumulators final
                 init = (1u << NACC) - 1u;
             }
             // drain: warp w reads lanes 32 (w & 3) .. +31 (rows) and every
-            // fourth 8-column block starting at block w >> 2
+            // fourth 8-column block (4 complex columns) starting at block w >> 2
             {
                 const int q = warp & 3, m = 32 * q + lane;
-                const float rf = s.rfac[m];
+                const float rf = rfac[m];
                 for (int cb = warp >> 2; cb < NR / 8; cb += 4) {
                     float a0[8], a1[8], a2[8], a3[8], a4[8];
                     const uint32_t ad = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(8 * cb);
@@ -391,13 +410,14 @@ __device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, 
                     ld_wait();
                     if (m < M) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int col = 8 * cb + j;
-                            const int part = col >= ncp ? 1 : 0;
-                            const int c = col - part * ncp;
+                        for (int j = 0; j < 4; ++j) {
+                            const int c = 4 * cb + j;
                             if (c < nc) {
-                                const df32 v = combine(a0[j], a1[j], a2[j], a3[j], a4[j], rf * s.cfac[c]);
-                                op.out(m, n0 + c, part, v, g0 == 0);
+                                const float f = rf * cfac[c];
+                                const df32 re = combine(a0[2 * j], a1[2 * j], a2[2 * j], a3[2 * j], a4[2 * j], f);
+                                const df32 im = combine(a0[2 * j + 1], a1[2 * j + 1], a2[2 * j + 1],
+                                                        a3[2 * j + 1], a4[2 * j + 1], f);
+                                op.out(m, n0 + c, re, im, g0 == 0);
                             }
                         }
                     }
@@ -407,6 +427,7 @@ __device__ __noinline__ void zgemm(Op& op, int M, int N, int Kc, const Smem& s, 
             __syncthreads();            // accumulators read; next pass may overwrite
         }
     }
+    return phase;
 }
 
 }  // namespace tc

@@ -32,10 +32,10 @@ struct Z64Op {
         const zd v = B[(size_t)k * ldb + n];
         return from_z<df32>(v.re, v.im);
     }
-    __device__ void out(int m, int n, int part, df32 v, bool first) const {
-        double* p = reinterpret_cast<double*>(C + (size_t)(m0 + m) * ldc + n) + part;
-        const double x = (double)v.hi + (double)v.lo;
-        *p = first ? x : *p + x;
+    __device__ void out(int m, int n, df32 re, df32 im, bool first) const {
+        zd* p = C + (size_t)(m0 + m) * ldc + n;
+        const zd x = {(double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo};
+        *p = first ? x : cadd(*p, x);
     }
 };
 
@@ -46,13 +46,12 @@ constexpr size_t kSmem = tc::smem_bytes() > 120 * 1024 ? tc::smem_bytes() : 120 
 __global__ void __launch_bounds__(NT, 1)
 zgemm_tc_kernel(int m, int n, int k, const zd* __restrict__ A, int lda, const zd* __restrict__ B,
                 int ldb, zd* __restrict__ C, int ldc, int* __restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const tc::Smem s = tc::carve(smem_raw);
-    uint32_t phase = tc::setup(s);
-    Z64Op op{A, lda, B, ldb, C, ldc, (int)blockIdx.x * 128};
-    tc::zgemm(op, min(128, m - op.m0), n, k, s, phase);
-    if (threadIdx.x == 0 && *(volatile int*)s.err) atomicExch(err, 1);
-    tc::teardown(s);
+    const tc::Area ar{0};
+    uint32_t phase = tc::setup(ar);
+    const Z64Op op{A, lda, B, ldb, C, ldc, (int)blockIdx.x * 128};
+    phase = tc::zgemm(op, min(128, m - op.m0), n, k, ar, phase);
+    if (threadIdx.x == 0 && *(volatile int*)ar.err()) atomicExch(err, 1);
+    tc::teardown(ar);
 }
 
 }  // namespace
