@@ -237,13 +237,16 @@ struct GJUpdateOp {
     __device__ zf b(int k, int n) const {
         return reinterpret_cast<const zf*>(rgf_dyn_smem + xr_off)[k * K + col(n)];
     }
-    __device__ void out(int m, int n, df32 re, df32 im, bool) const {
+    static constexpr bool kColA = true;
+    using Old = float4;
+    __device__ float4 load(int m, int n, bool) const {
+        return *reinterpret_cast<const float4*>(A + (size_t)col(n) * lda + r0 + m);
+    }
+    __device__ void store(int m, int n, float4 x, df32 re, df32 im, bool) const {
         const int i = r0 + m;
         if (i >= j0 && i < j0 + bb) return;
-        float4* p = reinterpret_cast<float4*>(A + (size_t)col(n) * lda + i);
-        const float4 x = *p;
         const df32 r = df_sub(df32{x.x, x.y}, re), q = df_sub(df32{x.z, x.w}, im);
-        *p = make_float4(r.hi, r.lo, q.hi, q.lo);
+        *reinterpret_cast<float4*>(A + (size_t)col(n) * lda + i) = make_float4(r.hi, r.lo, q.hi, q.lo);
     }
 };
 

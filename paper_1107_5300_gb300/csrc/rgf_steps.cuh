@@ -25,17 +25,40 @@ struct SweepSmem {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Shared memory set aside for the tensor-core area (operand tiles, scales,
-// mbarrier) when the contractions run on the tensor cores.
-__host__ __device__ constexpr size_t tc_reserve(bool tc) { return tc ? tc::smem_bytes() + 1024 : 0; }
+// Shared-memory layout of the sweep for a largest column size Kmax and panel
+// width bm: the sweep's own buffers, then (with tc) the tensor-core area at the
+// next 1024-byte boundary.  With tc the staging tiles of the binary64 GEMM
+// (used only by the trace, after the last MMA) alias the tensor-core tiles.
+__host__ __device__ inline size_t sweep_base_bytes(int Kmax, int bm, bool tc) {
+    size_t b = 0;
+    b += 4 * align16((size_t)Kmax * bm * 16);   // 2 panels, multipliers, pivot rows
+    b += 2 * align16((size_t)bm * 16);          // rowbuf, pivot reciprocals
+    b += align16((size_t)Kmax * 16);            // colbuf
+    if (!tc) b += align16(2 * 8 * 64 * 16);     // gemm tiles
+    b += align16(16);                           // inv
+    b += align16((size_t)Kmax * 8);             // eps
+    b += align16(NWARP * 8);                    // red
+    b += align16(16);                           // clmax
+    b += align16((size_t)Kmax * 4) * 2;         // perm, idx
+    b += align16((size_t)(2 * bm + 1) * 4);     // displaced rows of a panel
+    b += align16(16);                           // ctl
+    b += align16(32);                           // pivot keys
+    b += align16((size_t)Kmax) * 3;             // kc, kp, kn
+    return b;
+}
+__host__ __device__ inline size_t tc_area_offset(int Kmax, int bm) {
+    return (sweep_base_bytes(Kmax, bm, true) + 1023) & ~(size_t)1023;
+}
+__host__ __device__ inline size_t sweep_total_bytes(int Kmax, int bm, bool tc) {
+    return tc ? tc_area_offset(Kmax, bm) + tc::smem_bytes() : sweep_base_bytes(Kmax, bm, false);
+}
 
 // Panel width of the blocked Gauss-Jordan for a largest column size Kmax:
-// the widest of 16, 8, 4, 2 whose panel and pivot-row buffers fit next to the
-// rest of the shared memory (and the tensor-core area, if any).
+// the widest of 16, 8, 4, 2 whose layout fits the 227 KB of shared memory a
+// block may use.
 __host__ __device__ inline int gj_panel_width(int Kmax, bool tc = false) {
     int b = 16;
-    while (b > 2 && (size_t)4 * Kmax * b * 16 + (size_t)Kmax * 64 + 20000 + tc_reserve(tc) > 220 * 1024)
-        b >>= 1;
+    while (b > 2 && sweep_total_bytes(Kmax, b, tc) > 232448) b >>= 1;
     return b;
 }
 
@@ -55,7 +78,7 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax, bool tc = false) {
     s.gj.rowbuf = (cx<R>*)take((size_t)bm * 16);
     s.gj.pinv = (cx<R>*)take((size_t)bm * 16);
     s.gj.colbuf = (cx<R>*)take((size_t)Kmax * 16);
-    s.gemm = (cx<R>*)take(2 * 8 * 64 * 16);
+    s.gemm = tc ? (cx<R>*)(base + tc_area_offset(Kmax, bm)) : (cx<R>*)take(2 * 8 * 64 * 16);
     s.gj.inv = (zd*)take(16);
     s.eps = (double*)take((size_t)Kmax * 8);
     s.red = (double*)take(NWARP * 8);
@@ -158,14 +181,18 @@ struct StripOp {
     int KL, lo, r0;
     __device__ zf a(int m, int k) const { return Y[(size_t)(r0 + m) * KL + k]; }
     __device__ zf b(int k, int n) const { return G[(size_t)k * KL + lo + n]; }
-    __device__ void out(int m, int n, df32 re, df32 im, bool first) const {
-        float4* p = reinterpret_cast<float4*>(P + (size_t)(r0 + m) * KL + lo + n);
+    static constexpr bool kColA = false;
+    using Old = float4;
+    __device__ float4 load(int m, int n, bool first) const {
+        return first ? make_float4(0.f, 0.f, 0.f, 0.f)
+                     : *reinterpret_cast<const float4*>(P + (size_t)(r0 + m) * KL + lo + n);
+    }
+    __device__ void store(int m, int n, float4 x, df32 re, df32 im, bool first) const {
         if (!first) {
-            const float4 x = *p;
             re = df_add(df32{x.x, x.y}, re);
             im = df_add(df32{x.z, x.w}, im);
         }
-        *p = make_float4(re.hi, re.lo, im.hi, im.lo);
+        *reinterpret_cast<float4*>(P + (size_t)(r0 + m) * KL + lo + n) = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
 };
 

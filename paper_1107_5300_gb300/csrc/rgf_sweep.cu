@@ -40,38 +40,15 @@
 
 namespace rgf {
 
-// Shared memory of the sweep itself (panels, buffers, masks) for a largest
-// column size Kmax; with tc the panel width leaves room for the tensor-core
-// area, which follows at the next 1024-byte boundary.
-__host__ __device__ size_t sweep_base_bytes(int Kmax, bool tc) {
-    const int bm = gj_panel_width(Kmax, tc);
-    size_t b = 0;
-    b += 4 * align16((size_t)Kmax * bm * 16);   // 2 panels, multipliers, pivot rows
-    b += 2 * align16((size_t)bm * 16);          // rowbuf, pivot reciprocals
-    b += align16((size_t)Kmax * 16);            // colbuf
-    b += align16(2 * 8 * 64 * 16);              // gemm tiles
-    b += align16(16);                           // inv
-    b += align16((size_t)Kmax * 8);             // eps
-    b += align16(NWARP * 8);                    // red
-    b += align16(16);                           // clmax
-    b += align16((size_t)Kmax * 4) * 2;         // perm, idx
-    b += align16((size_t)(2 * bm + 1) * 4);     // displaced rows of a panel
-    b += align16(16);                           // ctl
-    b += align16(32);                           // pivot keys
-    b += align16((size_t)Kmax) * 3;             // kc, kp, kn
-    return b;
-}
-__host__ __device__ inline size_t tc_offset(int Kmax) { return (sweep_base_bytes(Kmax, true) + 1023) & ~(size_t)1023; }
-
 size_t sweep_smem_bytes(int Kmax, bool tc) {
-    return tc ? tc_offset(Kmax) + tc::smem_bytes() : sweep_base_bytes(Kmax, false);
+    return sweep_total_bytes(Kmax, gj_panel_width(Kmax, tc), tc);
 }
 
 // Sets up the tensor-core area behind the sweep's shared memory (TMEM
 // allocation, mbarrier; every thread) and points the sweep's contractions at it.
 template <class R>
 __device__ void tc_attach(unsigned char* smem_raw, int Kmax, SweepSmem<R>& s, tc::State& st) {
-    st.ar = tc::Area{(int)tc_offset(Kmax)};
+    st.ar = tc::Area{(int)tc_area_offset(Kmax, gj_panel_width(Kmax, true))};
     st.phase = tc::setup(st.ar);
     s.gj.tcs = &st;
     s.tcs = &st;

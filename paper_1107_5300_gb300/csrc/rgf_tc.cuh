@@ -51,10 +51,11 @@ constexpr int MAXC = 48;             // complex output columns per pass
 constexpr int ACOLS = 2 * MAXC;      // TMEM columns per accumulator (5 x 96 <= 512)
 constexpr int KCH = 8;               // complex inner entries per chunk (16 real-block k)
 constexpr int KGRP = 128;            // complex inner entries per exact accumulation group
+constexpr int NCA = 2;               // chunks of A' whose digit tiles stay resident across passes
 
 // Byte offsets inside the tensor-core area of shared memory.
-constexpr int OFF_A = 0;                          // [S][TILE] bf16 digit tiles of A'
-constexpr int OFF_B = OFF_A + S * TILE * 2;       // [S][TILE] bf16 digit tiles of B'
+constexpr int OFF_A = 0;                          // [NCA][S][TILE] bf16 digit tiles of A'
+constexpr int OFF_B = OFF_A + NCA * S * TILE * 2; // [S][TILE] bf16 digit tiles of B'
 constexpr int OFF_RSC = OFF_B + S * TILE * 2;     // [128] row slicing scales 2^(7-e)
 constexpr int OFF_RFAC = OFF_RSC + 128 * 4;       // [128] row output factors 2^(e-7)
 constexpr int OFF_CSC = OFF_RFAC + 128 * 4;       // [MAXC] column slicing scales
@@ -238,22 +239,22 @@ __device__ __forceinline__ float dweight(int i) { return __int_as_float((127 - 8
 // Max with NaN propagation (non-negative arguments).
 __device__ __forceinline__ float nmax(float a, float b) { return (isnan(b) || b > a) ? b : a; }
 
-// Slicing scale and output factor for a row / column maximum mx.
+// Slicing scale 2^(7-e) and output factor 2^(e-7) for a row / column maximum
+// mx, with e the least integer such that mx < 2^e (from the exponent field:
+// mx in [2^(E-127), 2^(E-126)) for a normal binary32 with biased exponent E).
 __device__ __forceinline__ void scales(float mx, float& sc, float& fac) {
+    const unsigned E = (__float_as_uint(mx) >> 23) & 0xFFu;
     if (!(mx <= 3.0e38f)) {          // NaN or Inf: poison the outputs of this row / column
         sc = 1.0f;
         fac = __int_as_float(0x7fc00000);
-        return;
-    }
-    int e = 0;
-    frexpf(mx, &e);                  // mx < 2^e (e = 0 for mx = 0)
-    if (e < -100) {                  // below any value this path meets: treat as zero
+    } else if (E < 27u) {            // below 2^-100 (zeros, subnormals): treat as zero
         sc = 0.0f;
         fac = 0.0f;
-        return;
+    } else {
+        const int e = (int)E - 126;
+        sc = __int_as_float((134 - e) << 23);
+        fac = __int_as_float((120 + e) << 23);
     }
-    sc = ldexpf(1.0f, 7 - e);
-    fac = ldexpf(1.0f, e - 7);
 }
 
 // The accumulators of one (row, column) -> double-float value, scaled.  The
@@ -274,11 +275,15 @@ __device__ __forceinline__ df32 combine(float a0, float a1, float a2, float a3, 
 
 // C op= A B, A: M x Kc (M <= 128), B: Kc x N, complex double-float, through the
 // accessor object `op` (passed by value):
-//   zf  op.a(m, k), op.b(k, n)                   operand entries
-//   void op.out(m, n, df32 re, df32 im, bool first)
-//                                                (A B)[m][n] over one group of up
-//                                                to 128 inner entries; first =
-//                                                the first group.
+//   zf op.a(m, k), op.b(k, n)                 operand entries
+//   Op::kColA                                 true when a(m, k) is contiguous in m
+//   Op::Old op.load(m, n, first)              the target of (m, n) before the
+//                                             update (issued before the last MMA
+//                                             wait, so its latency overlaps it)
+//   void op.store(m, n, old, re, im, first)   writes the target from old and
+//                                             (A B)[m][n] = re + i im over one group
+//                                             of up to 128 inner entries; first =
+//                                             the first group
 // Called by every thread of the block (NT = 512); ends with a barrier.
 // Returns the next mbarrier phase.
 template <class Op>
@@ -291,21 +296,36 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
     float* csc = ar.csc();
     float* cfac = ar.cfac();
     unsigned* cmax = ar.cmax();
-    __nv_bfloat16* ta = ar.a();
+    __nv_bfloat16* ta0 = ar.a();
     __nv_bfloat16* tb = ar.b();
+    const int q4 = warp & 3, mrow = 32 * q4 + lane, cgrp = warp >> 2;   // drain mapping
     for (int g0 = 0; g0 < Kc; g0 += KGRP) {
         const int kg = min(KGRP, Kc - g0);
+        const int nch = (kg + KCH - 1) / KCH;
+        const bool cacheA = nch <= NCA;
         // row scales over this group
-        for (int m = warp; m < 128; m += NWARP) {
-            float mx = 0.0f;
-            if (m < M)
-                for (int k = lane; k < kg; k += 32) {
-                    const zf v = op.a(m, g0 + k);
-                    mx = nmax(mx, nmax(fabsf(v.re.hi), fabsf(v.im.hi)));
-                }
+        if constexpr (Op::kColA) {
+            if (tid < 128) {
+                float mx = 0.0f;
+                if (tid < M)
+                    for (int k = 0; k < kg; ++k) {
+                        const zf v = op.a(tid, g0 + k);
+                        mx = nmax(mx, nmax(fabsf(v.re.hi), fabsf(v.im.hi)));
+                    }
+                scales(mx, rsc[tid], rfac[tid]);
+            }
+        } else {
+            for (int m = warp; m < 128; m += NWARP) {
+                float mx = 0.0f;
+                if (m < M)
+                    for (int k = lane; k < kg; k += 32) {
+                        const zf v = op.a(m, g0 + k);
+                        mx = nmax(mx, nmax(fabsf(v.re.hi), fabsf(v.im.hi)));
+                    }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane == 0) scales(mx, rsc[m], rfac[m]);
+                for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (lane == 0) scales(mx, rsc[m], rfac[m]);
+            }
         }
         for (int n0 = 0; n0 < N; n0 += MAXC) {
             const int nc = min(MAXC, N - n0);
@@ -326,28 +346,35 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
             __syncthreads();
             if (tid < MAXC) scales(__uint_as_float(cmax[tid]), csc[tid], cfac[tid]);
             __syncthreads();
+            typename Op::Old old[4];
             uint32_t init = 0u;
-            for (int k0 = 0; k0 < kg; k0 += KCH) {
-                // A': 128 rows x 8 complex entries, two per thread
+            for (int ch = 0; ch < nch; ++ch) {
+                const int k0 = ch * KCH;
+                __nv_bfloat16* ta = ta0 + (cacheA ? ch : 0) * (S * TILE);
+                if (!cacheA || n0 == 0) {
+                    // A': 128 rows x 8 complex entries, two per thread
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int e = tid + h * NT, m = e >> 3, k = e & 7;
-                    float dr[S], di[S];
-                    if (m < M && k0 + k < kg) {
-                        const zf v = op.a(m, g0 + k0 + k);
-                        const float sc = rsc[m];
-                        digits(v.re.hi, v.re.lo, sc, dr);
-                        digits(v.im.hi, v.im.lo, sc, di);
-                    } else {
+                    for (int h = 0; h < 2; ++h) {
+                        const int e = tid + h * NT;
+                        const int m = Op::kColA ? (e & 127) : (e >> 3);
+                        const int k = Op::kColA ? (e >> 7) : (e & 7);
+                        float dr[S], di[S];
+                        if (m < M && k0 + k < kg) {
+                            const zf v = op.a(m, g0 + k0 + k);
+                            const float sc = rsc[m];
+                            digits(v.re.hi, v.re.lo, sc, dr);
+                            digits(v.im.hi, v.im.lo, sc, di);
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < S; ++i) { dr[i] = 0.0f; di[i] = 0.0f; }
-                    }
-                    const int o = tile_off(m, 2 * k);
+                            for (int i = 0; i < S; ++i) { dr[i] = 0.0f; di[i] = 0.0f; }
+                        }
+                        const int o = tile_off(m, 2 * k);
 #pragma unroll
-                    for (int i = 0; i < S; ++i) {
-                        const float w = dweight(i);
-                        *reinterpret_cast<__nv_bfloat162*>(ta + i * TILE + o) =
-                            __floats2bfloat162_rn(dr[i] * w, di[i] * w);
+                        for (int i = 0; i < S; ++i) {
+                            const float w = dweight(i);
+                            *reinterpret_cast<__nv_bfloat162*>(ta + i * TILE + o) =
+                                __floats2bfloat162_rn(dr[i] * w, di[i] * w);
+                        }
                     }
                 }
                 // B': 8 complex entries x ncp columns, one per thread
@@ -391,33 +418,53 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
                         }
                     commit(ar.bar());
                 }
+                if (ch == nch - 1 && mrow < M) {
+                    // targets of this thread's first drain block, loaded under
+                    // the last MMAs
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int c = 4 * cgrp + j;
+                        if (c < nc) old[j] = op.load(mrow, n0 + c, g0 == 0);
+                    }
+                }
                 phase = wait_mma(ar, phase);   // tiles may be rewritten; accumulators final
                 init = (1u << NACC) - 1u;
             }
-            // drain: warp w reads lanes 32 (w & 3) .. +31 (rows) and every
-            // fourth 8-column block (4 complex columns) starting at block w >> 2
+            // drain: warp w reads lanes 32 (w & 3) .. +31 (rows) and the 8-column
+            // blocks (4 complex columns) w >> 2, + 4, + 8; each block's targets
+            // are loaded before its TMEM reads
             {
-                const int q = warp & 3, m = 32 * q + lane;
-                const float rf = rfac[m];
-                for (int cb = warp >> 2; cb < NR / 8; cb += 4) {
-                    float a0[8], a1[8], a2[8], a3[8], a4[8];
-                    const uint32_t ad = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(8 * cb);
-                    ld8(ad, a0);
-                    ld8(ad + ACOLS, a1);
-                    ld8(ad + 2 * ACOLS, a2);
-                    ld8(ad + 3 * ACOLS, a3);
-                    ld8(ad + 4 * ACOLS, a4);
-                    ld_wait();
-                    if (m < M) {
+                const float rf = rfac[mrow];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int c = 4 * cb + j;
-                            if (c < nc) {
-                                const float f = rf * cfac[c];
-                                const df32 re = combine(a0[2 * j], a1[2 * j], a2[2 * j], a3[2 * j], a4[2 * j], f);
-                                const df32 im = combine(a0[2 * j + 1], a1[2 * j + 1], a2[2 * j + 1],
-                                                        a3[2 * j + 1], a4[2 * j + 1], f);
-                                op.out(m, n0 + c, re, im, g0 == 0);
+                for (int b = 0; b < 3; ++b) {
+                    const int cb = cgrp + 4 * b;
+                    if (cb < NR / 8) {
+                        if (b > 0 && mrow < M) {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int c = 4 * cb + j;
+                                if (c < nc) old[j] = op.load(mrow, n0 + c, g0 == 0);
+                            }
+                        }
+                        float a0[8], a1[8], a2[8], a3[8], a4[8];
+                        const uint32_t ad = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(8 * cb);
+                        ld8(ad, a0);
+                        ld8(ad + ACOLS, a1);
+                        ld8(ad + 2 * ACOLS, a2);
+                        ld8(ad + 3 * ACOLS, a3);
+                        ld8(ad + 4 * ACOLS, a4);
+                        ld_wait();
+                        if (mrow < M) {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int c = 4 * cb + j;
+                                if (c < nc) {
+                                    const float f = rf * cfac[c];
+                                    const df32 re = combine(a0[2 * j], a1[2 * j], a2[2 * j], a3[2 * j], a4[2 * j], f);
+                                    const df32 im = combine(a0[2 * j + 1], a1[2 * j + 1], a2[2 * j + 1],
+                                                            a3[2 * j + 1], a4[2 * j + 1], f);
+                                    op.store(mrow, n0 + c, old[j], re, im, g0 == 0);
+                                }
                             }
                         }
                     }

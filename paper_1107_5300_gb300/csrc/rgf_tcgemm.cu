@@ -32,10 +32,14 @@ struct Z64Op {
         const zd v = B[(size_t)k * ldb + n];
         return from_z<df32>(v.re, v.im);
     }
-    __device__ void out(int m, int n, df32 re, df32 im, bool first) const {
-        zd* p = C + (size_t)(m0 + m) * ldc + n;
+    static constexpr bool kColA = false;
+    using Old = zd;
+    __device__ zd load(int m, int n, bool first) const {
+        return first ? zd{0.0, 0.0} : C[(size_t)(m0 + m) * ldc + n];
+    }
+    __device__ void store(int m, int n, zd old, df32 re, df32 im, bool first) const {
         const zd x = {(double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo};
-        *p = first ? x : cadd(*p, x);
+        C[(size_t)(m0 + m) * ldc + n] = first ? x : cadd(old, x);
     }
 };
 
