@@ -169,6 +169,9 @@ __device__ void cta_gemm(int m, int n, int kd, const cx<R>* __restrict__ A, int 
 //       W[j0+jj][l] = x_jj - sum_{jj' > jj} c_jj'[j0+jj] x_jj'
 //     every other row (one rank-b update)
 //       W[i][l] -= sum_jj c_jj[i] x_jj
+//   (the second line for the pivot rows is the same update, started from x_jj
+//   with the pivot rows' earlier multipliers set to zero, so one product
+//   serves every row)
 //   -- the arithmetic of the unblocked algorithm in a different association,
 //   reading and writing each element once per block instead of once per pivot.
 //   The substitution runs over all (pivot row, column) pairs of the block at
@@ -222,7 +225,7 @@ struct GJSmem {
 // The rank-b update of cta_gj_invert as a tensor-core product over one tile
 // of up to 128 rows: W[i][l] -= sum_jj c_jj[i] x_jj[l] for the block's own
 // columns l outside the panel (column c of the product -> l = own_col(c)) and
-// every row i outside the panel.  The multipliers and pivot rows are read from
+// every row i; a pivot row j0 + r starts from x_r instead of W.  The multipliers and pivot rows are read from
 // shared memory (byte offsets into the dynamic shared memory); W is
 // column-major, so the 32 rows a warp drains are contiguous.
 struct GJUpdateOp {
@@ -239,14 +242,16 @@ struct GJUpdateOp {
     }
     static constexpr bool kColA = true;
     using Old = float4;
+    // the current value: W for other rows, x_r (shared memory) for the pivot rows
     __device__ float4 load(int m, int n, bool) const {
-        return *reinterpret_cast<const float4*>(A + (size_t)col(n) * lda + r0 + m);
+        const int i = r0 + m;
+        if (i >= j0 && i < j0 + bb)
+            return reinterpret_cast<const float4*>(rgf_dyn_smem + xr_off)[(i - j0) * K + col(n)];
+        return *reinterpret_cast<const float4*>(A + (size_t)col(n) * lda + i);
     }
     __device__ void store(int m, int n, float4 x, df32 re, df32 im, bool) const {
-        const int i = r0 + m;
-        if (i >= j0 && i < j0 + bb) return;
         const df32 r = df_sub(df32{x.x, x.y}, re), q = df_sub(df32{x.z, x.w}, im);
-        *reinterpret_cast<float4*>(A + (size_t)col(n) * lda + i) = make_float4(r.hi, r.lo, q.hi, q.lo);
+        *reinterpret_cast<float4*>(A + (size_t)col(n) * lda + r0 + m) = make_float4(r.hi, r.lo, q.hi, q.lo);
     }
 };
 
@@ -416,12 +421,14 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                 }
                 __syncthreads();
             }
-            // the later steps' eliminations of the pivot rows, into W
-            for (int e = tid; e < bb * nown; e += NT) {
-                const int r = e % bb, c = e / bb, l = own_col(c);
-                cx<R> y = Xr[r * K + l];
-                for (int q = r + 1; q < bb; ++q) y = cmac(y, Cm[q * K + j0 + r], Xr[q * K + l], true);
-                A[(size_t)l * lda + j0 + r] = y;
+            // The later steps' eliminations of the pivot rows,
+            //   W[j0+r][l] = x_r - sum_{q > r} c_q[j0+r] x_q,
+            // have the form of the rank-b update below; with the pivot rows'
+            // multipliers of the earlier steps (q <= r) set to zero the update
+            // produces them from x_r.
+            for (int e = tid; e < bb * bb; e += NT) {
+                const int r = e / bb, q = e % bb;
+                if (q < r) Cm[q * K + j0 + r] = czero<R>();
             }
         }
         __syncthreads();
@@ -430,9 +437,9 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
             for (int t = 0; t < s.pm[0]; ++t) s.idx[s.pm[1 + t]] = s.pm[1 + t];
         }
         Pn = Pa;                         // the reduced panel
-        // ... then one rank-bb update of every other row: on the tensor cores
-        // (double-float operands, exact digit slicing) or on the FP32 / FP64
-        // pipes.
+        // ... then one rank-bb update of every row (the pivot rows from x_r):
+        // on the tensor cores (double-float operands, exact digit slicing) or
+        // on the FP32 / FP64 pipes.
         bool tc_done = false;
         if constexpr (std::is_same<R, df32>::value) {
             if (s.tcs && nown > 0) {
@@ -450,23 +457,19 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
             const bool ok_i1 = i0 + 1 < K, ok_c1 = c0 + 1 < nown;
             const int l0 = own_col(c0);
             const int l1 = ok_c1 ? own_col(c0 + 1) : l0;
-            const bool r0 = i0 >= j0 && i0 < j0 + bb;
-            const bool r1 = !ok_i1 || ((i0 + 1) >= j0 && (i0 + 1) < j0 + bb);
-            if (r0 && r1) continue;
-            cx<R>* c0p = A + (size_t)l0 * lda;
-            cx<R>* c1p = A + (size_t)l1 * lda;
-            cx<R> a00 = czero<R>(), a01 = czero<R>(), a10 = czero<R>(), a11 = czero<R>();
-            if (!r0) {
-                a00 = c0p[i0];
-                if (ok_c1) a01 = c1p[i0];
-            }
-            if (!r1) {
-                a10 = c0p[i0 + 1];
-                if (ok_c1) a11 = c1p[i0 + 1];
+            // the current value: W for other rows, x_r for the pivot rows
+            auto cur = [&](int i, int l) {
+                return (i >= j0 && i < j0 + bb) ? Xr[(i - j0) * K + l] : A[(size_t)l * lda + i];
+            };
+            cx<R> a00 = cur(i0, l0), a01 = czero<R>(), a10 = czero<R>(), a11 = czero<R>();
+            if (ok_c1) a01 = cur(i0, l1);
+            if (ok_i1) {
+                a10 = cur(i0 + 1, l0);
+                if (ok_c1) a11 = cur(i0 + 1, l1);
             }
             for (int jj = 0; jj < bb; ++jj) {
-                const cx<R> p0 = r0 ? czero<R>() : Cm[jj * K + i0];
-                const cx<R> p1 = r1 ? czero<R>() : Cm[jj * K + i0 + 1];
+                const cx<R> p0 = Cm[jj * K + i0];
+                const cx<R> p1 = ok_i1 ? Cm[jj * K + i0 + 1] : czero<R>();
                 const cx<R> m0 = Xr[jj * K + l0];
                 const cx<R> m1 = ok_c1 ? Xr[jj * K + l1] : czero<R>();
                 a00 = cmac(a00, p0, m0, true);
@@ -474,11 +477,11 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                 a10 = cmac(a10, p1, m0, true);
                 a11 = cmac(a11, p1, m1, true);
             }
-            if (!r0) {
-                c0p[i0] = a00;
-                if (ok_c1) c1p[i0] = a01;
-            }
-            if (!r1) {
+            cx<R>* c0p = A + (size_t)l0 * lda;
+            cx<R>* c1p = A + (size_t)l1 * lda;
+            c0p[i0] = a00;
+            if (ok_c1) c1p[i0] = a01;
+            if (ok_i1) {
                 c0p[i0 + 1] = a10;
                 if (ok_c1) c1p[i0 + 1] = a11;
             }
