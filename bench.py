@@ -11,8 +11,10 @@ and the trace.  The unit is one unit-cell slice step of one chain
 work and are not counted.
 
 Arms:
-  default           mixed precision (double-float) path, device-resident inputs;
+  default           mixed precision path with the dense contractions on the
+                    tcgen05 tensor cores (RGF_MIXED_TC), device-resident inputs;
                     also the FP64 path once on the same ribbon for |dT|.
+  --precision mixed the double-float path on the FP32 pipes alone (RGF_MIXED).
   --impl reference  the CPU oracle on a bounded sample of the same workload.
 Under torchrun each rank runs its own disorder realisation (seed + rank): the
 chains shard with no collective on the data path ("weak" scaling).
@@ -46,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "tc", "fp64"])
+    ap.add_argument("--precision", default="tc", choices=["tc", "mixed", "fp64"])
     ap.add_argument("--workload", default="agnr245_L4000_anderson")
     ap.add_argument("--cells", type=int, default=0, help="override L (profiling runs)")
     ap.add_argument("--energies", type=int, default=0, help="use only the first n energies")

@@ -203,6 +203,14 @@ __device__ __forceinline__ unsigned long long pivot_key(cx<R> v, int i) {
     return ((unsigned long long)__float_as_uint(m) << 32) | (0xFFFFFFFFu - (unsigned)i);
 }
 
+// Division by a divisor fixed for a loop: floor(n / d) = umulhi(n, ceil(2^32/d)),
+// exact for n, d < 2^16 (the error n/2^32 stays below 1/d).
+struct FastDiv {
+    uint32_t d, m;
+    __device__ explicit FastDiv(int dv) : d((uint32_t)dv), m(dv > 1 ? (uint32_t)((0x100000000ull + dv - 1) / dv) : 0u) {}
+    __device__ int div(int n) const { return d == 1u ? n : (int)__umulhi((uint32_t)n, m); }
+};
+
 template <class R>
 struct GJSmem {
     cx<R>* rowbuf;   // [bmax]   scaled pivot row of the panel
@@ -286,49 +294,46 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         __syncthreads();
         for (int jj = 0; jj < bb; ++jj) {
             const int j = j0 + jj;
-            if (warp == 0) {
-                // lane 0 takes the pivot row from the key the previous pass
-                // left, checks the pivot and forms its reciprocal; lanes < bb
-                // then scale one entry of the pivot row each
-                cx<R> invR = czero<R>();
-                int bi = 0;
-                if (lane == 0) {
-                    const unsigned long long kj = s.key[j % 3];
-                    bi = (int)(0xFFFFFFFFu - (unsigned)(kj & 0xFFFFFFFFull));
-                    cx<R> pv = Pa[bi * bm + jj];
-                    int bad = 0;
-                    const float df = cabs2f(pv);
-                    if (!cfinite(pv)) {
-                        bad = 2;
-                    } else if (!(df >= 1e-30f && df <= 1e30f && df >= 2.0f * tiny2f)) {
-                        const double d = cabs2(pv);       // borderline: decide in binary64
-                        if (!isfinite(d)) bad = 2;
-                        else if (!(d > 0.0)) bad = 1;
-                        else if (d < tiny2) bad = 1;
-                    }
-                    if (bad) pv = from_z<R>(1.0, 0.0);
-                    invR = crecip(pv);
+            // Every warp takes the pivot row from the key the previous pass
+            // left and forms the reciprocal (lane 0, then broadcast), so no
+            // barrier separates the pivot choice from the elimination; warp 0
+            // records the pivot, the flags and the reciprocal.
+            cx<R> invR = czero<R>();
+            int p = 0;
+            if (lane == 0) {
+                const unsigned long long kj = s.key[j % 3];
+                p = (int)(0xFFFFFFFFu - (unsigned)(kj & 0xFFFFFFFFull));
+                cx<R> pv = Pa[p * bm + jj];
+                int bad = 0;
+                const float df = cabs2f(pv);
+                if (!cfinite(pv)) {
+                    bad = 2;
+                } else if (!(df >= 1e-30f && df <= 1e30f && df >= 2.0f * tiny2f)) {
+                    const double d = cabs2(pv);       // borderline: decide in binary64
+                    if (!isfinite(d)) bad = 2;
+                    else if (!(d > 0.0)) bad = 1;
+                    else if (d < tiny2) bad = 1;
+                }
+                if (bad) pv = from_z<R>(1.0, 0.0);
+                invR = crecip(pv);
+                if (warp == 0) {
                     s.ctl[1] |= bad;
-                    s.ctl[0] = bi;
-                    s.perm[j] = bi;
+                    s.perm[j] = p;
                     s.pinv[jj] = invR;
                     s.key[(j + 2) % 3] = 0ull;   // read one pass ago, filled next pass
                 }
-                invR = shfl0(invR);
-                bi = __shfl_sync(0xffffffffu, bi, 0);
-                if (lane < bb) s.rowbuf[lane] = (lane == jj) ? invR : cmul(Pa[bi * bm + lane], invR);
             }
-            __syncthreads();
+            invR = shfl0(invR);
+            p = __shfl_sync(0xffffffffu, p, 0);
             // One pass: row swap j <-> p folded in as an index remap, pivot row
-            // scaled (rowbuf), column jj eliminated from every other row (old ->
-            // new), and the candidates for the next pivot ranked on the fly.
+            // scaled, column jj eliminated from every other row (old -> new),
+            // and the candidates for the next pivot ranked on the fly.
             // Threads: 16 columns x (NT / 16) rows, four rows per round (loads
             // first, then the arithmetic).
-            const int p = s.ctl[0];
             const int l = tid & 15;
             kmax = 0ull;
             if (l < bb) {
-                const cx<R> r = s.rowbuf[l];
+                const cx<R> r = (l == jj) ? invR : cmul(Pa[p * bm + l], invR);
                 constexpr int RS = NT / 16;
                 for (int i0 = tid >> 4; i0 < K; i0 += 4 * RS) {
                     cx<R> mv[4], av[4];
@@ -393,8 +398,9 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         {
             // pivot rows after the swaps into Xr (x_0 scaled); tasks (r, c) with
             // r fastest so that a warp reads contiguous rows of one column
+            const FastDiv dbb(bb), down(max(nown, 1));
             for (int e = tid; e < bb * nown; e += NT) {
-                const int r = e % bb, c = e / bb, l = own_col(c);
+                const int c = dbb.div(e), r = e - c * bb, l = own_col(c);
                 cx<R> v = A[(size_t)l * lda + s.idx[j0 + r]];
                 if (r == 0) v = cmul(v, s.pinv[0]);
                 Xr[r * K + l] = v;
@@ -403,8 +409,9 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
             // rows outside the panel that took a panel row's content (the
             // sources are panel rows, unchanged until the stores below)
             const int npm = s.pm[0];
+            const FastDiv dpm(max(npm, 1));
             for (int e = tid; e < npm * nown; e += NT) {
-                const int t = e % npm, c = e / npm;
+                const int c = dpm.div(e), t = e - c * npm;
                 cx<R>* colp = A + (size_t)own_col(c) * lda;
                 colp[s.pm[1 + t]] = colp[s.pm[1 + bm + t]];
             }
@@ -414,7 +421,7 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
             for (int q = 0; q + 1 < bb; ++q) {
                 const int nr = bb - 1 - q;
                 for (int e = tid; e < nr * nown; e += NT) {
-                    const int r = q + 1 + e / nown, c = e % nown, l = own_col(c);
+                    const int rr = down.div(e), c = e - rr * nown, r = q + 1 + rr, l = own_col(c);
                     cx<R> a = cmac(Xr[r * K + l], Cm[q * K + j0 + r], Xr[q * K + l], true);
                     if (r == q + 1) a = cmul(a, s.pinv[r]);
                     Xr[r * K + l] = a;
