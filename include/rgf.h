@@ -174,7 +174,7 @@ rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, i
  * calls), here by exact bfloat16 digit slicing of double-float operands
  * (Ozaki scheme: 7 signed base-256 digits per real value, per-row and
  * per-column power-of-two scales), binary32 tensor-core accumulation that is
- * exact for the three leading digit levels, and double-float recombination.
+ * exact for the five leading digit levels, and double-float recombination.
  * The binary64 inputs are first rounded to double-float (48-bit significand).
  * Accuracy per entry: a few units of 2^-48 times k max_j |A_mj| max_j |B_jn|.
  *   A: device [m][lda], lda >= k;  B: device [k][ldb], ldb >= n;

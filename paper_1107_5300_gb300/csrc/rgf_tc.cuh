@@ -10,18 +10,21 @@
 // every digit exact in bfloat16.  The tile of digit i holds d_i 2^(-8 i).
 // A product of digit tiles i (of A) and j (of B) carries the weight
 // 2^(-8 (i + j)); the tensor core accumulates it in binary32:
-//     level l = i + j = 0 .. 3    one TMEM accumulator each.  Every term of a
+//     level l = i + j = 0 .. 4    one TMEM accumulator each.  Every term of a
 //                                 level is an integer multiple of 2^(-8 l)
 //                                 below 2^14, and a level sums at most
-//                                 4 x 256 x 2^14 = 2^24 of them: exact;
-//     levels 4 .. S-1             one shared accumulator.  The tensor core's
+//                                 5 x 192 of them (groups of up to 96 complex
+//                                 inner entries): below 2^24, exact;
+//     levels 5 .. S-1             one shared accumulator.  The tensor core's
 //                                 binary32 additions drop low-order bits at
 //                                 every MMA (measured: sharing it with level 3
-//                                 cost 2^-44 of the scale); at 2^-32 of the
-//                                 scale these levels lose less than 2^-50;
+//                                 cost 2^-44 of the scale, with level 4 about
+//                                 2^-48 over the 288 MMAs of a 123-deep
+//                                 product); at 2^-40 of the scale these
+//                                 levels lose less than 2^-55;
 //     levels >= S                 dropped (below 2^-(8S-1) of the scale).
-// The five accumulators are combined in double-float (error-free sums) and
-// scaled back by 2^(e_row - 7) 2^(e_col - 7).  With S = 7 digits (55 bits)
+// The six accumulators are summed in double-float and scaled back by
+// 2^(e_row - 7) 2^(e_col - 7).  With S = 7 digits (55 bits)
 // the product is accurate to a few units of 2^-48 of (row max x column max x
 // inner dimension), the accuracy of the double-float arithmetic it replaces.
 //
@@ -34,7 +37,7 @@
 // threads that slice them (K-major, no swizzle: 8-row x 16-byte core
 // matrices, 128 B apart along K and 256 B apart along M/N); one elected
 // thread issues the MMAs and commits them to an mbarrier; the accumulators
-// live in TMEM (5 x 96 columns) and are read back with tcgen05.ld.
+// live in TMEM (6 x 80 columns) and are read back with tcgen05.ld.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -46,11 +49,11 @@ namespace tc {
 
 constexpr int S = 7;                 // digits per real value
 constexpr int TILE = 128 * 16;       // elements of one operand tile (128 rows x 16 k)
-constexpr int NACC = 5;              // TMEM accumulators: levels 0..3 exact, 4.. shared
-constexpr int MAXC = 48;             // complex output columns per pass
-constexpr int ACOLS = 2 * MAXC;      // TMEM columns per accumulator (5 x 96 <= 512)
+constexpr int NACC = 6;              // TMEM accumulators: levels 0..4 exact, 5.. shared
+constexpr int MAXC = 40;             // complex output columns per pass
+constexpr int ACOLS = 2 * MAXC;      // TMEM columns per accumulator (6 x 80 <= 512)
 constexpr int KCH = 8;               // complex inner entries per chunk (16 real-block k)
-constexpr int KGRP = 128;            // complex inner entries per exact accumulation group
+constexpr int KGRP = 96;             // complex inner entries per exact accumulation group
 constexpr int NCA = 2;               // chunks of A' whose digit tiles stay resident across passes
 
 // Byte offsets inside the tensor-core area of shared memory.
@@ -257,20 +260,12 @@ __device__ __forceinline__ void scales(float mx, float& sc, float& fac) {
     }
 }
 
-// The accumulators of one (row, column) -> double-float value, scaled.  The
-// exact levels are summed error-free (their rounding errors are multiples of
-// 2^-24 small enough to add exactly into t); the shared one is added last.
-__device__ __forceinline__ df32 combine(float a0, float a1, float a2, float a3, float a4, float f) {
-    float s, t, s2, e2, s3, e3;
-    two_sum(a0, a1, s, t);
-    two_sum(s, a2, s2, e2);
-    two_sum(s2, a3, s3, e3);
-    t = __fadd_rn(__fadd_rn(__fadd_rn(t, e2), e3), a4);
-    df32 r;
-    fast_two_sum(s3, t, r.hi, r.lo);
-    r.hi = __fmul_rn(r.hi, f);
-    r.lo = __fmul_rn(r.lo, f);
-    return r;
+// Adds a binary32 value to a double-float accumulator (error-free sum of the
+// high parts, renormalised).
+__device__ __forceinline__ void acc_add(float& hi, float& lo, float a) {
+    float s, e;
+    two_sum(hi, a, s, e);
+    fast_two_sum(s, __fadd_rn(lo, e), hi, lo);
 }
 
 // C op= A B, A: M x Kc (M <= 128), B: Kc x N, complex double-float, through the
@@ -282,7 +277,7 @@ __device__ __forceinline__ df32 combine(float a0, float a1, float a2, float a3, 
 //                                             wait, so its latency overlaps it)
 //   void op.store(m, n, old, re, im, first)   writes the target from old and
 //                                             (A B)[m][n] = re + i im over one group
-//                                             of up to 128 inner entries; first =
+//                                             of up to 96 inner entries; first =
 //                                             the first group
 // Called by every thread of the block (NT = 512); ends with a barrier.
 // Returns the next mbarrier phase.
@@ -432,7 +427,8 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
             }
             // drain: warp w reads lanes 32 (w & 3) .. +31 (rows) and the 8-column
             // blocks (4 complex columns) w >> 2, + 4, + 8; each block's targets
-            // are loaded before its TMEM reads
+            // are loaded before its TMEM reads; the six levels are summed in
+            // double-float, three accumulators at a time
             {
                 const float rf = rfac[mrow];
 #pragma unroll
@@ -446,23 +442,44 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
                                 if (c < nc) old[j] = op.load(mrow, n0 + c, g0 == 0);
                             }
                         }
-                        float a0[8], a1[8], a2[8], a3[8], a4[8];
                         const uint32_t ad = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(8 * cb);
-                        ld8(ad, a0);
-                        ld8(ad + ACOLS, a1);
-                        ld8(ad + 2 * ACOLS, a2);
-                        ld8(ad + 3 * ACOLS, a3);
-                        ld8(ad + 4 * ACOLS, a4);
-                        ld_wait();
+                        float hi[8], lo[8];
+                        {
+                            float a0[8], a1[8], a2[8];
+                            ld8(ad, a0);
+                            ld8(ad + ACOLS, a1);
+                            ld8(ad + 2 * ACOLS, a2);
+                            ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                two_sum(a0[j], a1[j], hi[j], lo[j]);   // exact
+                                acc_add(hi[j], lo[j], a2[j]);
+                            }
+                        }
+                        {
+                            float a3[8], a4[8], a5[8];
+                            ld8(ad + 3 * ACOLS, a3);
+                            ld8(ad + 4 * ACOLS, a4);
+                            ld8(ad + 5 * ACOLS, a5);
+                            ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                acc_add(hi[j], lo[j], a3[j]);
+                                acc_add(hi[j], lo[j], a4[j]);
+                                lo[j] = __fadd_rn(lo[j], a5[j]);
+                            }
+                        }
                         if (mrow < M) {
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 const int c = 4 * cb + j;
                                 if (c < nc) {
                                     const float f = rf * cfac[c];
-                                    const df32 re = combine(a0[2 * j], a1[2 * j], a2[2 * j], a3[2 * j], a4[2 * j], f);
-                                    const df32 im = combine(a0[2 * j + 1], a1[2 * j + 1], a2[2 * j + 1],
-                                                            a3[2 * j + 1], a4[2 * j + 1], f);
+                                    df32 re, im;
+                                    fast_two_sum(hi[2 * j], lo[2 * j], re.hi, re.lo);
+                                    fast_two_sum(hi[2 * j + 1], lo[2 * j + 1], im.hi, im.lo);
+                                    re.hi = __fmul_rn(re.hi, f); re.lo = __fmul_rn(re.lo, f);
+                                    im.hi = __fmul_rn(im.hi, f); im.lo = __fmul_rn(im.lo, f);
                                     op.store(mrow, n0 + c, old[j], re, im, g0 == 0);
                                 }
                             }

@@ -15,7 +15,7 @@ void set_last_error(const std::string& msg);
 namespace {
 
 // Accessors of the binary64 operands (rounded to double-float on load) and
-// of the output (the sum of the groups of 128 inner entries).
+// of the output (the sum of the groups of 96 inner entries).
 struct Z64Op {
     const zd* A;
     int lda;

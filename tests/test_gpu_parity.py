@@ -187,3 +187,43 @@ def test_invalid_arguments_are_rejected(rgflib):
         rgflib.conductance([rib], np.array([0.1]), precision=7)
     with pytest.raises(rgflib.RGFError):
         rgflib.conductance([rib], np.array([0.1]), eta_lead=0.0)
+
+
+@pytest.fixture(scope="module")
+def wide_case():
+    # N = 501 (KL = 251 orbitals per column): two 128-row tiles, two exact
+    # accumulation groups in the strip product, a narrower Gauss-Jordan panel
+    N, L = 501, 2
+    eps = workloads.anderson_onsite(N, L, 0.1, 501)
+    rem = workloads.edge_removed(N, L, 0.02, 502)
+    Es = np.array([-0.21, 0.13])
+    refs = [_oracle_T(N, L, e, 1e-8, 1e-8, eps, rem) for e in Es]
+    return N, L, eps, rem, Es, refs
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_wide_columns_vs_oracle(rgflib, wide_case, prec):
+    N, L, eps, rem, Es, refs = wide_case
+    T, st = _run(rgflib, N, L, Es, eps, rem, prec)
+    assert (st == 0).all()
+    tol = 1e-9 if prec == 0 else 1e-7
+    for e, t, ref in zip(Es, T, refs):
+        assert abs(t - ref) < tol * max(1.0, abs(ref)), (e, t, ref)
+
+
+def test_config5_width_precisions_agree(rgflib):
+    # N = 1001 (KL = 501, the 2002-orbital ribbon): four row tiles and four
+    # accumulation groups; the three precisions agree and respect 0 <= T <= n_ch
+    N, L = 1001, 3
+    eps = workloads.anderson_onsite(N, L, 0.1, 5)
+    rem = workloads.edge_removed(N, L, 0.02, 55)
+    Es = np.array([-0.27, 0.08])
+    out = {}
+    for prec in (0, 1, 2):
+        T, st = _run(rgflib, N, L, Es, eps, rem, prec)
+        assert (st == 0).all()
+        out[prec] = T
+    for e, t in zip(Es, out[0]):
+        assert -1e-9 <= t <= bands.channels_closed_form(N, e) + 1e-9
+    assert np.max(np.abs(out[1] - out[0])) < 1e-7
+    assert np.max(np.abs(out[2] - out[0])) < 1e-7

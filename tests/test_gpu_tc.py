@@ -72,9 +72,10 @@ def test_real_dominated_operands(rgflib):
 
 
 def test_leading_levels_accumulate_exactly(rgflib):
-    # every entry close to its row / column maximum with one sign: the four
-    # exact digit levels sum up to 4 x 2^22 = 2^24, the limit of exact binary32
-    # accumulation; any rounding there would show at ~2^-24 relative
+    # every entry close to its row / column maximum with one sign: the exact
+    # digit levels sum up to 5 x 192 x 2^14 < 2^24 terms' worth, near the limit
+    # of exact binary32 accumulation; any rounding there would show at ~2^-24
+    # relative
     rng = np.random.default_rng(9)
     A = (1.0 - 1e-3 * rng.random((128, 128))) * (1 + 1j)
     B = (1.0 - 1e-3 * rng.random((128, 128))) * (1 + 1j)
