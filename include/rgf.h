@@ -65,10 +65,10 @@ typedef enum {
     RGF_MIXED = 1,       /* slice recursion in double-float (pairs of binary32 on the
                             FP32 pipes, ~48-bit significand); leads and trace binary64 */
     RGF_MIXED_TC = 2     /* as RGF_MIXED, with the dense contractions of every slice
-                            step (the rank-b updates of the slice inverse and the
-                            corner-strip product of Eq. 5) on the tcgen05 tensor cores
-                            by exact bfloat16 digit slicing (see rgf_zgemm_tc); forward
-                            sweep only (rgf_conductance, rgf_conductance_dev) */
+                            step (the rank-b updates of the slice inverse, the
+                            corner-strip product of Eq. 5, the adjoint's products) on
+                            the tcgen05 tensor cores by exact bfloat16 digit slicing
+                            (see rgf_zgemm_tc) */
 } rgf_precision;
 
 /* One ribbon instance (the paper's input step: geometry, defects, disorder). */

@@ -186,9 +186,6 @@ rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchai
     if (!rib || !E_dev || !T_dev) return fail(RGF_EINVAL, "NULL argument");
     if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
         return fail(RGF_EINVAL, "unknown precision");
-    if (precision == RGF_MIXED_TC && dT_dev)
-        return fail(RGF_EINVAL, "RGF_MIXED_TC is a forward-sweep precision; use RGF_MIXED or RGF_FP64 "
-                                "for rgf_conductance_grad");
     if (!(eta_device >= 0.0) || !(eta_lead > 0.0) || !std::isfinite(eta_device) ||
         !std::isfinite(eta_lead))
         return fail(RGF_EINVAL, "eta_device must be >= 0 and eta_lead > 0 (finite)");

@@ -248,8 +248,8 @@ struct GJUpdateOp {
     __device__ zf b(int k, int n) const {
         return reinterpret_cast<const zf*>(rgf_dyn_smem + xr_off)[k * K + col(n)];
     }
-    static constexpr bool kColA = true;
     using Old = float4;
+    __device__ bool colA() const { return true; }
     // the current value: W for other rows, x_r (shared memory) for the pivot rows
     __device__ float4 load(int m, int n, bool) const {
         const int i = r0 + m;

@@ -18,6 +18,9 @@
 // 4 * stride columns (stride in unit cells, ~sqrt(L) by default); the reverse
 // pass recomputes each segment's g_k, P_k from its checkpoint, then walks it
 // backwards.  The workspace holds Q = -A_bar (so dT/d eps_i = 2 Re Q_ii).
+// With TC (precision RGF_MIXED_TC) the forward and recomputed column steps
+// and the dense products of the reverse pass run on the tcgen05 tensor cores
+// (rgf_tc.cuh); the block holds the SM's TMEM for the whole launch.
 #include "rgf_steps.cuh"
 
 namespace rgf {
@@ -32,15 +35,15 @@ __device__ void copy_blk(cx<R>* D, const cx<R>* S, size_t n) {
 
 }  // namespace
 
-template <class R>
+template <class R, bool TC>
 __global__ void __launch_bounds__(NT, 1)
 grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
             int Kmax, double eta_d, const zd* __restrict__ leadout,
             const int* __restrict__ lead_status, const LeadDev* __restrict__ leads,
             cx<R>* __restrict__ ws, const int* __restrict__ seg_cols, double* __restrict__ Tout,
             double* __restrict__ dT, int32_t* __restrict__ status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SweepSmem<R> s = carve<R>(smem_raw, Kmax);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    SweepSmem<R> s = carve<R>(smem_raw, Kmax, TC);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ci = order[blockIdx.x];
     const ChainDev ch = chains[ci];
@@ -64,6 +67,8 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     double* grad = dT + ch.grad_off;
     const auto t = Hop<R>::t(c);
     const auto t2 = Hop<R>::t2(c);
+    tc::State tst;
+    if constexpr (TC) tc_attach<R>(Kmax, s, tst);
 
     // Forward pass with checkpoints.
     int flag = 0;
@@ -78,13 +83,19 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
         __syncthreads();
         flag |= fwd_column<R>(c, k, G, G, P, P, X, Y, s);
     }
+    if constexpr (TC) {
+        if (*(volatile int*)tst.ar.err()) flag |= 4;
+    }
     const double T = trace_T<R>(c, P, X, T1, gbar, s);
     const int st = chain_status(c, flag, T);
     if (threadIdx.x == 0) {
         Tout[ci] = (st == ST_OK) ? T : NAN;
         if (status) status[ci] = st;
     }
-    if (st != ST_OK) return;
+    if (st != ST_OK) {
+        if constexpr (TC) tc::teardown(tst.ar);
+        return;
+    }
 
     // P_bar = Gamma_L conj(P) Gamma_R  (KL x KR)
     for (size_t e = threadIdx.x; e < B; e += NT) {
@@ -93,8 +104,8 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
         if ((int)(e % KL) < KR) Y[e] = cconj(P[e]);
     }
     __syncthreads();
-    cta_gemm<R, false, false>(KL, KR, KL, GL, KL, Y, KL, T1, KL, GEMM_SET, s.gemm);
-    cta_gemm<R, false, false>(KL, KR, KR, T1, KL, GR, KR, Pb[0], KL, GEMM_SET, s.gemm);
+    dense_product<R, false>(KL, KR, KL, GL, KL, Y, KL, T1, KL, s);
+    dense_product<R, false>(KL, KR, KR, T1, KL, GR, KR, Pb[0], KL, s);
     int pb = 0, qb = 0;
 
     for (int j = nseg - 1; j >= 0; --j) {
@@ -124,7 +135,7 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
             const cx<R>* Qn = Qb[qb];      // -A_bar_{k+1}
             // g_bar_k
             if (k > 0)
-                cta_gemm<R, true, false>(Kp, K, KL, Pm, KL, Pbar, KL, T1, KL, GEMM_SET, s.gemm);
+                dense_product<R, true>(Kp, K, KL, Pm, KL, Pbar, KL, T1, KL, s);
             const int ctn = (k + 1) & 3;
             for (int i = warp; i < K; i += NWARP) {
                 int a0 = -1, a1 = -1, n0 = -1, n1 = -1;
@@ -159,15 +170,15 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
             }
             __syncthreads();
             // Q_k = g_k g_bar_k g_k  (= -A_bar_k)
-            cta_gemm<R, false, false>(K, K, K, gbar, KL, gk, KL, T1, KL, GEMM_SET, s.gemm);
+            dense_product<R, false>(K, K, K, gbar, KL, gk, KL, T1, KL, s);
             cx<R>* Qk = Qb[qb ^ 1];
-            cta_gemm<R, false, false>(K, K, K, gk, KL, T1, KL, Qk, KL, GEMM_SET, s.gemm);
+            dense_product<R, false>(K, K, K, gk, KL, T1, KL, Qk, KL, s);
             const int n = k >> 2;
             for (int i = threadIdx.x; i < K; i += NT)
                 if (s.kc[i]) grad[(size_t)n * c.M + 4 * i + ct] = 2.0 * to_z(Qk[(size_t)i * KL + i]).re;
             // P_bar_{k-1} = P_bar_k g_k W_k^T
             if (k > 0) {
-                cta_gemm<R, false, false>(KL, K, K, Pbar, KL, gk, KL, T1, KL, GEMM_SET, s.gemm);
+                dense_product<R, false>(KL, K, K, Pbar, KL, gk, KL, T1, KL, s);
                 cx<R>* Pn = Pb[pb ^ 1];
                 for (int r = warp; r < KL; r += NWARP)
                     for (int a = lane; a < Kp; a += 32) {
@@ -187,6 +198,10 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
             qb ^= 1;
         }
     }
+    if constexpr (TC) {
+        if (*(volatile int*)tst.ar.err() && threadIdx.x == 0 && status) status[ci] = ST_ETIMEOUT;
+        tc::teardown(tst.ar);
+    }
 }
 
 size_t grad_ws_elems(int N, int L, int seg_cols) {
@@ -201,22 +216,30 @@ cudaError_t launch_grad(int precision, const ChainDev* chains, const int* order,
                         const LeadDev* leads, void* ws, const int* seg_cols, double* T, double* dT,
                         int32_t* status, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    size_t smem = sweep_smem_bytes(Kmax);
+    const bool tc = precision == 2;
+    const size_t smem = sweep_smem_bytes(Kmax, tc);
     cudaError_t e;
     if (precision == 0) {
-        e = cudaFuncSetAttribute(grad_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = cudaFuncSetAttribute(grad_kernel<double, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        grad_kernel<double><<<nchains, NT, smem, st>>>(chains, order, nchains, Kmax, eta_device,
-                                                      (const zd*)leadout, lead_status, leads,
-                                                      (zd*)ws, seg_cols, T, dT, status);
+        grad_kernel<double, false><<<nchains, NT, smem, st>>>(
+            chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status, leads,
+            (zd*)ws, seg_cols, T, dT, status);
+    } else if (tc) {
+        e = cudaFuncSetAttribute(grad_kernel<df32, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        grad_kernel<df32, true><<<nchains, NT, smem, st>>>(
+            chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status, leads,
+            (zf*)ws, seg_cols, T, dT, status);
     } else {
-        e = cudaFuncSetAttribute(grad_kernel<df32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = cudaFuncSetAttribute(grad_kernel<df32, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        grad_kernel<df32><<<nchains, NT, smem, st>>>(chains, order, nchains, Kmax, eta_device,
-                                                    (const zd*)leadout, lead_status, leads,
-                                                    (zf*)ws, seg_cols, T, dT, status);
+        grad_kernel<df32, false><<<nchains, NT, smem, st>>>(
+            chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status, leads,
+            (zf*)ws, seg_cols, T, dT, status);
     }
     return cudaGetLastError();
 }

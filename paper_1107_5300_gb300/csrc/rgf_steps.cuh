@@ -94,6 +94,77 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax, bool tc = false) {
     return s;
 }
 
+// Sets up the tensor-core area behind the sweep's shared memory (TMEM
+// allocation, mbarrier; every thread) and points the contractions at it.
+template <class R>
+__device__ void tc_attach(int Kmax, SweepSmem<R>& s, tc::State& st) {
+    st.ar = tc::Area{(int)tc_area_offset(Kmax, gj_panel_width(Kmax, true))};
+    st.phase = tc::setup(st.ar);
+    s.gj.tcs = &st;
+    s.tcs = &st;
+}
+
+// C (M x N) = op(A) (M x Kd) B (Kd x N), op(A) = A or A^T (ta; no
+// conjugation), as a tensor-core product over one tile of up to 128 rows of C.
+// C must not overlap A or B.
+struct DenseOp {
+    const zf* A;
+    int lda;
+    const zf* B;
+    int ldb;
+    zf* C;
+    int ldc, r0;
+    bool ta;
+    using Old = float4;
+    __device__ bool colA() const { return ta; }
+    __device__ zf a(int m, int k) const {
+        return ta ? A[(size_t)k * lda + r0 + m] : A[(size_t)(r0 + m) * lda + k];
+    }
+    __device__ zf b(int k, int n) const { return B[(size_t)k * ldb + n]; }
+    __device__ float4 load(int m, int n, bool first) const {
+        return first ? make_float4(0.f, 0.f, 0.f, 0.f)
+                     : *reinterpret_cast<const float4*>(C + (size_t)(r0 + m) * ldc + n);
+    }
+    __device__ void store(int m, int n, float4 x, df32 re, df32 im, bool first) const {
+        if (!first) {
+            re = df_add(df32{x.x, x.y}, re);
+            im = df_add(df32{x.z, x.w}, im);
+        }
+        *reinterpret_cast<float4*>(C + (size_t)(r0 + m) * ldc + n) = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+};
+
+// C = op(A) B on the tensor cores over row tiles of 128; one out-of-line copy
+// for the adjoint's dense products (arguments by value; the sweep's strip
+// product is inlined).  Returns the next mbarrier phase.
+static __device__ __noinline__ uint32_t tc_dense(int m, int n, int kd, const zf* A, int lda,
+                                                 const zf* B, int ldb, zf* C, int ldc, bool ta,
+                                                 tc::Area ar, uint32_t phase) {
+    for (int r0 = 0; r0 < m; r0 += 128) {
+        const DenseOp op{A, lda, B, ldb, C, ldc, r0, ta};
+        phase = tc::zgemm(op, min(128, m - r0), n, kd, ar, phase);
+    }
+    return phase;
+}
+
+// C = op(A) B on the tensor cores when the block holds them (double-float
+// operands), else on the FP32 / FP64 pipes.  Every thread; ends with a barrier.
+template <class R, bool TA>
+__device__ void dense_product(int m, int n, int kd, const cx<R>* A, int lda, const cx<R>* B, int ldb,
+                              cx<R>* C, int ldc, SweepSmem<R>& s) {
+    if constexpr (std::is_same<R, df32>::value) {
+        if (s.tcs) {
+            if (m <= 0 || n <= 0 || kd <= 0) {
+                __syncthreads();
+                return;
+            }
+            s.tcs->phase = tc_dense(m, n, kd, A, lda, B, ldb, C, ldc, TA, s.tcs->ar, s.tcs->phase);
+            return;
+        }
+    }
+    cta_gemm<R, TA, false>(m, n, kd, A, lda, B, ldb, C, ldc, GEMM_SET, s.gemm);
+}
+
 // Everything a block needs to know about its chain.
 struct ChainCtx {
     const double* eps;
@@ -171,30 +242,6 @@ __device__ inline void load_col(const ChainCtx& c, int k, uint8_t* km, double* e
 
 template <class R>
 __device__ __forceinline__ cx<R> ld_z(const zd* p) { return from_z<R>(p->re, p->im); }
-
-// The strip product Pout = Y Gk (columns lo.. of Gk and Pout) as a
-// tensor-core product over one tile of up to 128 rows of Y.
-struct StripOp {
-    const zf* Y;
-    const zf* G;
-    zf* P;
-    int KL, lo, r0;
-    __device__ zf a(int m, int k) const { return Y[(size_t)(r0 + m) * KL + k]; }
-    __device__ zf b(int k, int n) const { return G[(size_t)k * KL + lo + n]; }
-    static constexpr bool kColA = false;
-    using Old = float4;
-    __device__ float4 load(int m, int n, bool first) const {
-        return first ? make_float4(0.f, 0.f, 0.f, 0.f)
-                     : *reinterpret_cast<const float4*>(P + (size_t)(r0 + m) * KL + lo + n);
-    }
-    __device__ void store(int m, int n, float4 x, df32 re, df32 im, bool first) const {
-        if (!first) {
-            re = df_add(df32{x.x, x.y}, re);
-            im = df_add(df32{x.z, x.w}, im);
-        }
-        *reinterpret_cast<float4*>(P + (size_t)(r0 + m) * KL + lo + n) = make_float4(re.hi, re.lo, im.hi, im.lo);
-    }
-};
 
 // The two halves of one forward column step k (row-major, leading dimension KL):
 //   inv_column:   X = A_k (K x K), Gout = A_k^-1 (Gauss-Jordan; Gout may alias
@@ -287,7 +334,7 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
     if constexpr (std::is_same<R, df32>::value) {
         if (s.tcs) {
             for (int r0 = 0; r0 < KL; r0 += 128) {
-                const StripOp op{Y, Gk, Pout, KL, lo, r0};
+                const DenseOp op{Y, KL, Gk + lo, KL, Pout + lo, KL, r0, false};
                 s.tcs->phase = tc::zgemm(op, min(128, KL - r0), n, K, s.tcs->ar, s.tcs->phase);
             }
             return;

@@ -44,16 +44,6 @@ size_t sweep_smem_bytes(int Kmax, bool tc) {
     return sweep_total_bytes(Kmax, gj_panel_width(Kmax, tc), tc);
 }
 
-// Sets up the tensor-core area behind the sweep's shared memory (TMEM
-// allocation, mbarrier; every thread) and points the sweep's contractions at it.
-template <class R>
-__device__ void tc_attach(unsigned char* smem_raw, int Kmax, SweepSmem<R>& s, tc::State& st) {
-    st.ar = tc::Area{(int)tc_area_offset(Kmax, gj_panel_width(Kmax, true))};
-    st.phase = tc::setup(st.ar);
-    s.gj.tcs = &st;
-    s.tcs = &st;
-}
-
 template <class R, bool TC>
 __global__ void __launch_bounds__(NT, 1)
 sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
@@ -79,7 +69,7 @@ sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
     cx<R>* P = X + 2 * B;
     cx<R>* Y = X + 3 * B;
     tc::State tst;
-    if constexpr (TC) tc_attach<R>(smem_raw, Kmax, s, tst);
+    if constexpr (TC) tc_attach<R>(Kmax, s, tst);
     int flag = 0;
     for (int k = 0; k < c.ncol; ++k) {
         load_col(c, k, s.kc, s.eps);
@@ -130,7 +120,7 @@ sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ o
     cx<R>* Y = X + 4 * B;
     int* flag_slot = reinterpret_cast<int*>(X + 5 * B);
     tc::State tst;
-    if constexpr (TC) tc_attach<R>(smem_raw, Kmax, s, tst);
+    if constexpr (TC) tc_attach<R>(Kmax, s, tst);
     if (role == 0) {
         int flag = 0;
         for (int k = 0; k < c.ncol; ++k) {

@@ -271,7 +271,7 @@ __device__ __forceinline__ void acc_add(float& hi, float& lo, float a) {
 // C op= A B, A: M x Kc (M <= 128), B: Kc x N, complex double-float, through the
 // accessor object `op` (passed by value):
 //   zf op.a(m, k), op.b(k, n)                 operand entries
-//   Op::kColA                                 true when a(m, k) is contiguous in m
+//   bool op.colA()                            true when a(m, k) is contiguous in m
 //   Op::Old op.load(m, n, first)              the target of (m, n) before the
 //                                             update (issued before the last MMA
 //                                             wait, so its latency overlaps it)
@@ -299,7 +299,8 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
         const int nch = (kg + KCH - 1) / KCH;
         const bool cacheA = nch <= NCA;
         // row scales over this group
-        if constexpr (Op::kColA) {
+        const bool colA = op.colA();
+        if (colA) {
             if (tid < 128) {
                 float mx = 0.0f;
                 if (tid < M)
@@ -351,8 +352,8 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int e = tid + h * NT;
-                        const int m = Op::kColA ? (e & 127) : (e >> 3);
-                        const int k = Op::kColA ? (e >> 7) : (e & 7);
+                        const int m = colA ? (e & 127) : (e >> 3);
+                        const int k = colA ? (e >> 7) : (e & 7);
                         float dr[S], di[S];
                         if (m < M && k0 + k < kg) {
                             const zf v = op.a(m, g0 + k0 + k);

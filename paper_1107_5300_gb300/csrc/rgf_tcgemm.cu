@@ -32,8 +32,8 @@ struct Z64Op {
         const zd v = B[(size_t)k * ldb + n];
         return from_z<df32>(v.re, v.im);
     }
-    static constexpr bool kColA = false;
     using Old = zd;
+    __device__ bool colA() const { return false; }
     __device__ zd load(int m, int n, bool first) const {
         return first ? zd{0.0, 0.0} : C[(size_t)(m0 + m) * ldc + n];
     }

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 T_HOP = -2.7
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-8)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-8), (2, 1e-8)])
 def test_gradient_matches_oracle_closed_form(rgflib, prec, tol):
     N, L = 11, 6
     eps = workloads.anderson_onsite(N, L, 0.3, 11)
@@ -32,7 +32,7 @@ def test_gradient_oracle_n11_l20(rgflib):
     eps = workloads.anderson_onsite(N, L, 0.15, 4)
     rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps)
     Es = np.array([-0.8, -0.2, 0.45])
-    for prec, tol in ((0, 1e-10), (1, 1e-8)):
+    for prec, tol in ((0, 1e-10), (1, 1e-8), (2, 1e-8)):
         T, g, st = rgflib.conductance_grad([rib] * 3, Es, 1e-8, 1e-8, prec)
         for c, E in enumerate(Es):
             ref = ograd.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps, None)
@@ -70,7 +70,7 @@ def test_gradient_against_finite_differences_n101(rgflib):
             ribs.append(rgflib.Ribbon(N, L, T_HOP, onsite=e2))
     Tfd, st = rgflib.conductance(ribs, np.full(len(ribs), E))
     fd = (Tfd[0::2] - Tfd[1::2]) / (2 * d)
-    for prec in (0, 1):
+    for prec in (0, 1, 2):
         T, g, st = rgflib.conductance_grad([rib], np.array([E]), 1e-8, 1e-8, prec, ckpt_stride=23)
         assert st[0] == 0
         gs = np.array([g[0, n, i] for (n, i) in sites])
