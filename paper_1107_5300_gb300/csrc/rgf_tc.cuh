@@ -170,6 +170,15 @@ __device__ __forceinline__ void ld8(uint32_t addr, float* v) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
+// 32 lanes x 4 consecutive columns of TMEM.
+__device__ __forceinline__ void ld4(uint32_t addr, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
 __device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Allocates all 512 TMEM columns (warp 0) and initialises the mbarrier.  Must
@@ -258,14 +267,6 @@ __device__ __forceinline__ void scales(float mx, float& sc, float& fac) {
         sc = __int_as_float((134 - e) << 23);
         fac = __int_as_float((120 + e) << 23);
     }
-}
-
-// Adds a binary32 value to a double-float accumulator (error-free sum of the
-// high parts, renormalised).
-__device__ __forceinline__ void acc_add(float& hi, float& lo, float a) {
-    float s, e;
-    two_sum(hi, a, s, e);
-    fast_two_sum(s, __fadd_rn(lo, e), hi, lo);
 }
 
 // C op= A B, A: M x Kc (M <= 128), B: Kc x N, complex double-float, through the
@@ -428,8 +429,7 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
             }
             // drain: warp w reads lanes 32 (w & 3) .. +31 (rows) and the 8-column
             // blocks (4 complex columns) w >> 2, + 4, + 8; each block's targets
-            // are loaded before its TMEM reads; the six levels are summed in
-            // double-float, three accumulators at a time
+            // are loaded before its TMEM reads
             {
                 const float rf = rfac[mrow];
 #pragma unroll
@@ -444,44 +444,40 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
                             }
                         }
                         const uint32_t ad = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(8 * cb);
-                        float hi[8], lo[8];
-                        {
-                            float a0[8], a1[8], a2[8];
-                            ld8(ad, a0);
-                            ld8(ad + ACOLS, a1);
-                            ld8(ad + 2 * ACOLS, a2);
-                            ld_wait();
+                        // two halves of 4 columns (2 complex columns); levels
+                        // 0 + 1 and 2 + 3 pair up error-free, 4 + 5 in binary32
+                        // (below 2^-32 of the scale), then one double-float sum
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                two_sum(a0[j], a1[j], hi[j], lo[j]);   // exact
-                                acc_add(hi[j], lo[j], a2[j]);
-                            }
-                        }
-                        {
-                            float a3[8], a4[8], a5[8];
-                            ld8(ad + 3 * ACOLS, a3);
-                            ld8(ad + 4 * ACOLS, a4);
-                            ld8(ad + 5 * ACOLS, a5);
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t ah = ad + 4u * h;
+                            float a0[4], a1[4], a2[4], a3[4], a4[4], a5[4];
+                            ld4(ah, a0);
+                            ld4(ah + ACOLS, a1);
+                            ld4(ah + 2 * ACOLS, a2);
+                            ld4(ah + 3 * ACOLS, a3);
+                            ld4(ah + 4 * ACOLS, a4);
+                            ld4(ah + 5 * ACOLS, a5);
                             ld_wait();
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                acc_add(hi[j], lo[j], a3[j]);
-                                acc_add(hi[j], lo[j], a4[j]);
-                                lo[j] = __fadd_rn(lo[j], a5[j]);
-                            }
-                        }
-                        if (mrow < M) {
+                            float hi[4], lo[4];
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
-                                const int c = 4 * cb + j;
-                                if (c < nc) {
-                                    const float f = rf * cfac[c];
-                                    df32 re, im;
-                                    fast_two_sum(hi[2 * j], lo[2 * j], re.hi, re.lo);
-                                    fast_two_sum(hi[2 * j + 1], lo[2 * j + 1], im.hi, im.lo);
-                                    re.hi = __fmul_rn(re.hi, f); re.lo = __fmul_rn(re.lo, f);
-                                    im.hi = __fmul_rn(im.hi, f); im.lo = __fmul_rn(im.lo, f);
-                                    op.store(mrow, n0 + c, old[j], re, im, g0 == 0);
+                                float s01, e01, s23, e23, s, e;
+                                two_sum(a0[j], a1[j], s01, e01);        // exact
+                                two_sum(a2[j], a3[j], s23, e23);        // exact
+                                const float r45 = __fadd_rn(a4[j], a5[j]);
+                                two_sum(s01, s23, s, e);
+                                fast_two_sum(s, __fadd_rn(__fadd_rn(e01, e), __fadd_rn(e23, r45)), hi[j], lo[j]);
+                            }
+                            if (mrow < M) {
+#pragma unroll
+                                for (int jj = 0; jj < 2; ++jj) {
+                                    const int j = 2 * h + jj, c = 4 * cb + j;
+                                    if (c < nc) {
+                                        const float f = rf * cfac[c];
+                                        const df32 re{__fmul_rn(hi[2 * jj], f), __fmul_rn(lo[2 * jj], f)};
+                                        const df32 im{__fmul_rn(hi[2 * jj + 1], f), __fmul_rn(lo[2 * jj + 1], f)};
+                                        op.store(mrow, n0 + c, old[j], re, im, g0 == 0);
+                                    }
                                 }
                             }
                         }
