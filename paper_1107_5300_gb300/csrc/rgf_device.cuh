@@ -213,8 +213,6 @@ struct FastDiv {
 
 template <class R>
 struct GJSmem {
-    cx<R>* rowbuf;   // [bmax]   scaled pivot row of the panel
-    cx<R>* colbuf;   // [Kmax]   pivot column of the panel
     cx<R>* panel;    // [Kmax][bmax]  working panel
     cx<R>* panel2;   // [Kmax][bmax]  second panel buffer
     cx<R>* mult;     // [bmax][Kmax]  multipliers c_jj[i] at mult[jj*K + i]
@@ -223,9 +221,8 @@ struct GJSmem {
     int* perm;       // [Kmax]
     int* idx;        // [Kmax]   row labels during the sweep, column order at the end
     int* pm;         // [2 bmax + 1]  rows displaced by a panel's swaps: count, rows, sources
-    int* ctl;        // [4]: pivot row, flag
+    int* ctl;        // [4]: [1] = the pivot flags
     unsigned long long* key;   // [3]  pivot keys, one per pass, rotating
-    zd* inv;         // [1]
     int bmax;        // panel width
     tc::State* tcs;  // tensor-core state for the rank-b update, or nullptr
 };

@@ -32,10 +32,8 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline size_t sweep_base_bytes(int Kmax, int bm, bool tc) {
     size_t b = 0;
     b += 4 * align16((size_t)Kmax * bm * 16);   // 2 panels, multipliers, pivot rows
-    b += 2 * align16((size_t)bm * 16);          // rowbuf, pivot reciprocals
-    b += align16((size_t)Kmax * 16);            // colbuf
+    b += align16((size_t)bm * 16);              // pivot reciprocals
     if (!tc) b += align16(2 * 8 * 64 * 16);     // gemm tiles
-    b += align16(16);                           // inv
     b += align16((size_t)Kmax * 8);             // eps
     b += align16(NWARP * 8);                    // red
     b += align16(16);                           // clmax
@@ -75,11 +73,8 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax, bool tc = false) {
     s.gj.panel2 = (cx<R>*)take((size_t)Kmax * bm * 16);
     s.gj.mult = (cx<R>*)take((size_t)Kmax * bm * 16);
     s.gj.xrow = (cx<R>*)take((size_t)Kmax * bm * 16);
-    s.gj.rowbuf = (cx<R>*)take((size_t)bm * 16);
     s.gj.pinv = (cx<R>*)take((size_t)bm * 16);
-    s.gj.colbuf = (cx<R>*)take((size_t)Kmax * 16);
     s.gemm = tc ? (cx<R>*)(base + tc_area_offset(Kmax, bm)) : (cx<R>*)take(2 * 8 * 64 * 16);
-    s.gj.inv = (zd*)take(16);
     s.eps = (double*)take((size_t)Kmax * 8);
     s.red = (double*)take(NWARP * 8);
     s.clmax = (double*)take(16);
