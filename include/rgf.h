@@ -189,6 +189,20 @@ rgf_status rgf_zgemm_tc(int m, int n, int k, const double* A, int lda, const dou
                         double* C, int ldc, void* stream);
 
 /*
+ * Self-test of the bounded tensor-core completion wait (no counterpart in the
+ * paper).  Runs one 64 x 64 x 64 rgf_zgemm_tc product on the legacy default
+ * stream with the MMA completion never committed to the mbarrier the kernel
+ * waits on and a wait limit of about half a millisecond of device clock, so
+ * that the wait runs out.  The kernel then sets its error flag, commits the
+ * MMAs still in flight to a second mbarrier, waits for them (bounded), frees
+ * its tensor memory and returns; the CUDA context stays usable.  Allocates and
+ * frees its own 192 KiB device buffer.
+ * Returns RGF_ETIMEOUT when the timeout path works; RGF_OK would mean that the
+ * wait did not run out; RGF_ECUDA on a CUDA error.
+ */
+rgf_status rgf_zgemm_tc_selftest_timeout(void);
+
+/*
  * Allocation-free variant of rgf_conductance_dev (no counterpart in the paper).
  *
  * For callers that may not allocate device memory: e.g. a host application

@@ -65,10 +65,16 @@ constexpr int OFF_CSC = OFF_RFAC + 128 * 4;       // [MAXC] column slicing scale
 constexpr int OFF_CFAC = OFF_CSC + MAXC * 4;      // [MAXC] column output factors
 constexpr int OFF_CMAX = OFF_CFAC + MAXC * 4;     // [MAXC] column maxima (binary32 bits)
 constexpr int OFF_BAR = OFF_CMAX + MAXC * 4;      // MMA completion mbarrier (8 bytes)
-constexpr int OFF_TSLOT = OFF_BAR + 8;            // TMEM base address (tcgen05.alloc)
+constexpr int OFF_BAR2 = OFF_BAR + 8;             // drain mbarrier after a timeout (8 bytes)
+constexpr int OFF_LIMIT = OFF_BAR2 + 8;           // completion-wait limit, device clock cycles
+constexpr int OFF_TSLOT = OFF_LIMIT + 8;          // TMEM base address (tcgen05.alloc)
 constexpr int OFF_ERR = OFF_TSLOT + 4;            // sticky: an MMA wait gave up
-constexpr int BYTES = (OFF_ERR + 4 + 15) / 16 * 16;
-static_assert(OFF_BAR % 8 == 0 && BYTES % 16 == 0, "tensor-core area layout");
+constexpr int OFF_SKIP = OFF_ERR + 4;             // self-test: completion commits left out
+constexpr int BYTES = (OFF_SKIP + 4 + 15) / 16 * 16;
+static_assert(OFF_BAR % 8 == 0 && OFF_LIMIT % 8 == 0 && BYTES % 16 == 0, "tensor-core area layout");
+
+// Default limit of a completion wait: about a second of device clock.
+constexpr long long kWaitLimit = 2000000000ll;
 
 __host__ __device__ constexpr size_t smem_bytes() { return (size_t)BYTES; }
 
@@ -101,6 +107,9 @@ struct Area {
     __device__ float* cfac() const { return reinterpret_cast<float*>(base() + OFF_CFAC); }
     __device__ unsigned* cmax() const { return reinterpret_cast<unsigned*>(base() + OFF_CMAX); }
     __device__ unsigned long long* bar() const { return reinterpret_cast<unsigned long long*>(base() + OFF_BAR); }
+    __device__ unsigned long long* bar2() const { return reinterpret_cast<unsigned long long*>(base() + OFF_BAR2); }
+    __device__ long long* limit() const { return reinterpret_cast<long long*>(base() + OFF_LIMIT); }
+    __device__ int* skip() const { return reinterpret_cast<int*>(base() + OFF_SKIP); }
     __device__ uint32_t* tslot() const { return reinterpret_cast<uint32_t*>(base() + OFF_TSLOT); }
     __device__ int* err() const { return reinterpret_cast<int*>(base() + OFF_ERR); }
 };
@@ -181,10 +190,12 @@ __device__ __forceinline__ void ld4(uint32_t addr, float* v) {
 }
 __device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Allocates all 512 TMEM columns (warp 0) and initialises the mbarrier.  Must
+// Allocates all 512 TMEM columns (warp 0) and initialises the mbarriers, the
+// completion-wait limit and the self-test switch (skip != 0: the completion of
+// the MMAs is never committed, so the first wait runs into its limit).  Must
 // be called by every thread of the block (it ends with a barrier); the block
 // must be the only one on its SM that uses TMEM.  Returns the initial phase.
-__device__ inline uint32_t setup(Area ar) {
+__device__ inline uint32_t setup(Area ar, long long limit = kWaitLimit, int skip = 0) {
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
                      :: "r"(su32(ar.tslot())) : "memory");
@@ -192,8 +203,11 @@ __device__ inline uint32_t setup(Area ar) {
     }
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(ar.bar())) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(ar.bar2())) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *ar.err() = 0;
+        *ar.limit() = limit;
+        *ar.skip() = skip;
     }
     fence_before();
     __syncthreads();
@@ -201,25 +215,39 @@ __device__ inline uint32_t setup(Area ar) {
     return 0u;
 }
 
-// Releases TMEM.  Every thread; no MMA may be in flight.
+// Releases TMEM.  Every thread.  If a completion wait gave up, MMAs may still
+// be in flight: the issuing thread commits them to the second mbarrier and the
+// block waits for it (bounded by the default limit) before the release.
 __device__ inline void teardown(Area ar) {
     fence_before();
     __syncthreads();
+    if (*(volatile int*)ar.err()) {
+        if (threadIdx.x == 0)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(su32(ar.bar2())) : "memory");
+        const long long t0 = clock64();
+        while (!try_wait(ar.bar2(), 0u) && clock64() - t0 <= kWaitLimit) {
+        }
+        fence_after();
+        fence_before();
+        __syncthreads();
+    }
     if ((threadIdx.x >> 5) == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(*ar.tslot()) : "memory");
 }
 
-// Waits (every thread) for the MMAs committed last; gives up after about a
-// second of device clock and sets the sticky error flag, after which later
-// waits return at once.  Returns the next phase.
+// Waits (every thread) for the MMAs committed last; gives up after the
+// block's limit (about a second of device clock by default) and sets the
+// sticky error flag, after which later waits return at once.  Returns the next
+// phase.
 __device__ inline uint32_t wait_mma(Area ar, uint32_t phase) {
     if (!*(volatile int*)ar.err()) {
         bool done = try_wait(ar.bar(), phase);
         if (!done) {
-            const long long t0 = clock64();
+            const long long t0 = clock64(), lim = *(volatile long long*)ar.limit();
             while (!done) {
                 done = try_wait(ar.bar(), phase);
-                if (!done && clock64() - t0 > 2000000000ll) break;
+                if (!done && clock64() - t0 > lim) break;
             }
             if (!done) *(volatile int*)ar.err() = 1;
         }
@@ -413,7 +441,7 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
                                 id, (init >> acc) & 1u);
                             init |= 1u << acc;
                         }
-                    commit(ar.bar());
+                    if (!*ar.skip()) commit(ar.bar());
                 }
                 if (ch == nch - 1 && mrow < M) {
                     // targets of this thread's first drain block, loaded under

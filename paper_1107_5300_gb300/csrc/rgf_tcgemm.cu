@@ -49,9 +49,10 @@ constexpr size_t kSmem = tc::smem_bytes() > 120 * 1024 ? tc::smem_bytes() : 120 
 
 __global__ void __launch_bounds__(NT, 1)
 zgemm_tc_kernel(int m, int n, int k, const zd* __restrict__ A, int lda, const zd* __restrict__ B,
-                int ldb, zd* __restrict__ C, int ldc, int* __restrict__ err) {
+                int ldb, zd* __restrict__ C, int ldc, int* __restrict__ err, long long wait_limit,
+                int skip_commit) {
     const tc::Area ar{0};
-    uint32_t phase = tc::setup(ar);
+    uint32_t phase = tc::setup(ar, wait_limit, skip_commit);
     const Z64Op op{A, lda, B, ldb, C, ldc, (int)blockIdx.x * 128};
     phase = tc::zgemm(op, min(128, m - op.m0), n, k, ar, phase);
     if (threadIdx.x == 0 && *(volatile int*)ar.err()) atomicExch(err, 1);
@@ -61,36 +62,24 @@ zgemm_tc_kernel(int m, int n, int k, const zd* __restrict__ A, int lda, const zd
 }  // namespace
 }  // namespace rgf
 
-extern "C" rgf_status rgf_zgemm_tc(int m, int n, int k, const double* A, int lda, const double* B,
-                                   int ldb, double* C, int ldc, void* stream) {
-    using namespace rgf;
-    if (m < 0 || n < 0 || k < 0 || lda < (k > 0 ? k : 1) || ldb < (n > 0 ? n : 1) ||
-        ldc < (n > 0 ? n : 1) || (m > 0 && n > 0 && (!C || (k > 0 && (!A || !B))))) {
-        set_last_error("rgf_zgemm_tc: bad sizes or NULL pointer");
-        return RGF_EINVAL;
-    }
-    if (m == 0 || n == 0) return RGF_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e;
-    if (k == 0) {
-        e = cudaMemset2DAsync(C, (size_t)ldc * 16, 0, (size_t)n * 16, (size_t)m, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            set_last_error(std::string("rgf_zgemm_tc: ") + cudaGetErrorString(e));
-            return RGF_ECUDA;
-        }
-        return RGF_OK;
-    }
+namespace rgf {
+namespace {
+
+// One product on `st`, waited for; the kernel's completion-wait limit and the
+// self-test switch are passed through.
+rgf_status zgemm_tc_run(int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                        double* C, int ldc, cudaStream_t st, long long wait_limit, int skip_commit) {
     int* derr = nullptr;
     int herr = 0;
-    e = cudaMallocAsync(&derr, sizeof(int), st);
+    cudaError_t e = cudaMallocAsync(&derr, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(zgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmem);
     if (e == cudaSuccess) {
         zgemm_tc_kernel<<<(m + 127) / 128, NT, kSmem, st>>>(m, n, k, (const zd*)A, lda,
-                                                            (const zd*)B, ldb, (zd*)C, ldc, derr);
+                                                            (const zd*)B, ldb, (zd*)C, ldc, derr,
+                                                            wait_limit, skip_commit);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -108,4 +97,47 @@ extern "C" rgf_status rgf_zgemm_tc(int m, int n, int k, const double* A, int lda
         return RGF_ETIMEOUT;
     }
     return RGF_OK;
+}
+
+}  // namespace
+}  // namespace rgf
+
+extern "C" rgf_status rgf_zgemm_tc(int m, int n, int k, const double* A, int lda, const double* B,
+                                   int ldb, double* C, int ldc, void* stream) {
+    using namespace rgf;
+    if (m < 0 || n < 0 || k < 0 || lda < (k > 0 ? k : 1) || ldb < (n > 0 ? n : 1) ||
+        ldc < (n > 0 ? n : 1) || (m > 0 && n > 0 && (!C || (k > 0 && (!A || !B))))) {
+        set_last_error("rgf_zgemm_tc: bad sizes or NULL pointer");
+        return RGF_EINVAL;
+    }
+    if (m == 0 || n == 0) return RGF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (k == 0) {
+        cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc * 16, 0, (size_t)n * 16, (size_t)m, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("rgf_zgemm_tc: ") + cudaGetErrorString(e));
+            return RGF_ECUDA;
+        }
+        return RGF_OK;
+    }
+    return zgemm_tc_run(m, n, k, A, lda, B, ldb, C, ldc, st, tc::kWaitLimit, 0);
+}
+
+extern "C" rgf_status rgf_zgemm_tc_selftest_timeout(void) {
+    using namespace rgf;
+    const int n = 64;
+    double* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 3 * (size_t)n * n * 16);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("rgf_zgemm_tc_selftest_timeout: ") + cudaGetErrorString(e));
+        return RGF_ECUDA;
+    }
+    e = cudaMemset(buf, 0, 3 * (size_t)n * n * 16);
+    rgf_status s = RGF_ECUDA;
+    if (e == cudaSuccess)
+        s = zgemm_tc_run(n, n, n, buf, n, buf + 2 * n * n, n, buf + 4 * n * n, n, 0,
+                         1000000ll /* about 0.5 ms of device clock */, 1);
+    cudaFree(buf);
+    return s;
 }

@@ -26,8 +26,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENON
 # Symbols declared in include/rgf.h (checked by the CPU tests).
 EXPORTS = ["rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "rgf_free_ribbon",
            "rgf_lead_selfenergy", "rgf_conductance", "rgf_conductance_dev",
-           "rgf_conductance_grad", "rgf_conductance_noalloc", "rgf_zgemm_tc", "rgf_profile_enable",
-           "rgf_profile_read", "rgf_status_str",
+           "rgf_conductance_grad", "rgf_conductance_noalloc", "rgf_zgemm_tc",
+           "rgf_zgemm_tc_selftest_timeout", "rgf_profile_enable", "rgf_profile_read", "rgf_status_str",
            "rgf_last_error", "rgf_version"]
 
 
@@ -62,6 +62,8 @@ lib.rgf_conductance_noalloc.restype = C.c_int
 lib.rgf_zgemm_tc.argtypes = [C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int,
                              _vp]
 lib.rgf_zgemm_tc.restype = C.c_int
+lib.rgf_zgemm_tc_selftest_timeout.argtypes = []
+lib.rgf_zgemm_tc_selftest_timeout.restype = C.c_int
 lib.rgf_profile_enable.argtypes = [C.c_int]
 lib.rgf_profile_enable.restype = C.c_int
 lib.rgf_profile_read.argtypes = [_dp, _dp]
@@ -242,6 +244,12 @@ def conductance_noalloc(N, L, t, onsite_ptr, removed_ptr, E_ptr, n, T_ptr, statu
     if check:
         _check(st)
     return st
+
+
+def zgemm_tc_selftest_timeout():
+    """Runs the tensor-core product with its completion wait forced to run out;
+    returns the status (RGF_ETIMEOUT when the timeout path works)."""
+    return lib.rgf_zgemm_tc_selftest_timeout()
 
 
 def zgemm_tc(A_ptr, B_ptr, C_ptr, m, n, k, lda=None, ldb=None, ldc=None, stream=0, check=True):

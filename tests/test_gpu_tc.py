@@ -114,3 +114,15 @@ def test_empty_and_invalid_sizes(rgflib):
     assert np.array_equal(C, np.zeros((4, 3)))
     st = rgflib.zgemm_tc(0, 0, 0, 3, 3, 5, lda=4, check=False)
     assert st == rgflib.RGF_EINVAL
+
+
+def test_completion_wait_timeout_is_reported(rgflib):
+    # the MMAs' completion is never committed to the barrier the kernel waits
+    # on: the bounded wait runs out, the kernel reports it and drains its MMAs
+    # before freeing tensor memory; the context stays usable afterwards
+    assert rgflib.zgemm_tc_selftest_timeout() == rgflib.RGF_ETIMEOUT
+    rng = np.random.default_rng(13)
+    A, B = _rand(rng, 64, 64), _rand(rng, 64, 64)
+    C, st = _run(rgflib, A, B)
+    assert st == rgflib.RGF_OK
+    _check_close(C, A, B)
