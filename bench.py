@@ -38,6 +38,19 @@ sys.path.insert(0, str(ROOT))
 
 import workloads  # noqa: E402
 
+
+def kernel_sources_digest(csrc: Path | None = None) -> str:
+    """SHA-256 over the CUDA sources of the library (file names and bytes, in
+    name order): the DRAM counters of a capture hold only for the sources they
+    were taken on."""
+    import hashlib
+    csrc = csrc or ROOT / "paper_1107_5300_gb300" / "csrc"
+    h = hashlib.sha256()
+    for p in sorted({*csrc.glob("*.cu"), *csrc.glob("*.cuh"), *csrc.glob("*.h")}):
+        h.update(p.name.encode() + b"\0" + p.read_bytes())
+    return h.hexdigest()
+
+
 METRIC = "RGF slice-inversions/s (M=490, batched energies)"
 UNIT = "slice-steps/s"
 
@@ -461,14 +474,19 @@ def main():
         bound = "alu"
     achieved = fl / sweep_s / 1e12
     traffic_file = ROOT / "profiles" / "traffic.json"
-    traffic = None
+    traffic, traffic_note = None, "no DRAM counters recorded for this kernel and workload"
     if traffic_file.exists():
         try:
-            traffic = json.loads(traffic_file.read_text()).get(f"sweep_{args.precision}_{args.workload}")
+            rec = json.loads(traffic_file.read_text())
+            traffic = rec.get(f"sweep_{args.precision}_{args.workload}")
+            if traffic is not None and rec.get("_sources_sha256") != kernel_sources_digest():
+                traffic = None
+                traffic_note = "DRAM counters were taken on other kernel sources; not reported"
         except Exception:
             traffic = None
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
+            **({} if traffic is not None else {"traffic_note": traffic_note}),
             "kernel": {0: "sweep_kernel<double>", 1: "sweep_kernel<df32>", 2: "sweep_kernel<df32,tc>"}[prec],
             "peak_source": f"derived from unit counts and sm_max_mhz={smax:.0f} ({peaks_src})",
             "ms_sweep": statistics.mean(ms_sweep), "ms_lead": statistics.mean(ms_lead)}
