@@ -330,8 +330,8 @@ def run_grad(args):
         rel = np.abs(g - g64).max(axis=(1, 2)) / np.where(scale > 0, scale, 1.0)
         far = both & (np.abs(Es) >= 0.1)
         near = both & (np.abs(Es) < 0.1)
-        # near E = 0 the adjoint is condition-limited in every precision (binary64
-        # included, checked against binary64 central differences): reported apart
+        # near E = 0 the reverse sweep over column slices amplifies rounding at
+        # isolated sites (binary64 included): reported apart
         parity = {"max_rel_dgrad_vs_fp64_absE_ge_0.1": float(rel[far].max()) if far.any() else None,
                   "median_rel_dgrad_vs_fp64": float(np.median(rel[both])) if both.any() else None,
                   "max_rel_dgrad_vs_fp64_absE_lt_0.1": float(rel[near].max()) if near.any() else None,

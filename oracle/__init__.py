@@ -19,8 +19,10 @@ nanoribbons using GPU", Comput. Phys. Commun. 183 (2012) 543):
   (Eq. 1) and the Landauer trace (Eq. 2), by dense inversion.
 * ``rgf``      -- the recursion over unit-cell slices (Eqs. 4-5) and the
   trace (Eq. 2).
-* ``gradient`` -- dT/d eps_i: the closed form from the dense G, and the
-  reverse (adjoint) sweep of the recursion.
+* ``gradient`` -- dT/d eps_i: the closed form from the dense G, the closed
+  form with its blocks assembled slice by slice from left- and
+  right-connected sweeps (accurate near E = 0), and the reverse (adjoint)
+  sweep of the recursion.
 * ``bands``    -- channel counts: closed-form armchair band edges and a
   brute-force band structure.
 * ``mp``       -- the same recursion in arbitrary precision (mpmath) for the

@@ -18,6 +18,23 @@ X_bar = dT/dX (holomorphic part, dT = 2 Re Tr[X_bar^T dX]) and g_j symmetric,
         dT/d eps_{j,i} = -2 Re (A_bar_j)_ii
         P_bar_{j-1} = P_bar_j g_j V_{j-1,j}^T
 
+``two_sided`` evaluates the closed form slice by slice without the dense G:
+the blocks it needs follow from the Dyson equation (Eq. 3) with the bond
+between slices j-1 and j (or j and j+1) cut,
+
+    G_jj = (A_j - V_{j-1,j}^T gl_{j-1} V_{j-1,j} - V_{j,j+1} gr_{j+1} V_{j,j+1}^T)^-1
+    G_{1j} = Pl_{j-1} V_{j-1,j} G_jj,        G_{jL} = G_jj V_{j,j+1} Qr_{j+1}
+
+with gl, Pl = G_{1j} of the part left of the cut (the forward recursion of
+Eqs. 4-5) and gr, Qr = G_{jL} of the part right of it (the same recursion run
+from the right lead), A_j = z - H_jj (minus Sigma_L, Sigma_R on the end
+slices).  It forms the blocks of the whole system's G directly instead of
+propagating the cotangents through the half systems' Green's functions.
+Near the poles of the half systems (E close to 0, where the ends of a cut
+carry nearly bound states) the reverse sweep loses accuracy at isolated
+sites (rounding amplified by the large g_j), while this form stays at the
+dense closed form (tests/test_oracle.py).
+
 Removed atoms get derivative 0.
 """
 from __future__ import annotations
@@ -25,7 +42,8 @@ from __future__ import annotations
 import numpy as np
 
 from .dense import green_dense
-from .leads import broadening
+from .lattice import device_slices
+from .leads import broadening, self_energies
 from .rgf import forward
 
 
@@ -66,3 +84,45 @@ def adjoint(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=N
             Pbar = Pbar @ g[j] @ V[j - 1].T
         Abar_next = Abar
     return f["T"], out
+
+
+def two_sided(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
+    """Returns (T, dT/d eps [L, 2N]) from the closed form with the blocks of G
+    assembled by the Dyson relations above (left- and right-connected sweeps)."""
+    Hd, V, keep = device_slices(N, L, t, eps, removed)
+    if sig is None:
+        sig = self_energies(N, E, eta_lead, t)
+    sigL = sig[0][np.ix_(keep[0], keep[0])]
+    sigR = sig[1][np.ix_(keep[-1], keep[-1])]
+    z = E + 1j * eta_device
+    A = [z * np.eye(len(keep[j])) - Hd[j] for j in range(L)]
+    A[0] = A[0] - sigL
+    A[L - 1] = A[L - 1] - sigR
+    # left-connected: gl[j] = G_jj and Pl[j] = G_1j of slices 1..j
+    gl, Pl = [], []
+    for j in range(L):
+        Aj = A[j] if j == 0 else A[j] - V[j - 1].T @ gl[j - 1] @ V[j - 1]
+        gl.append(np.linalg.inv(Aj))
+        Pl.append(gl[j] if j == 0 else Pl[j - 1] @ V[j - 1] @ gl[j])
+    # right-connected: gr[j] = G_jj and Qr[j] = G_jL of slices j..L
+    gr, Qr = [None] * L, [None] * L
+    for j in range(L - 1, -1, -1):
+        Aj = A[j] if j == L - 1 else A[j] - V[j] @ gr[j + 1] @ V[j].T
+        gr[j] = np.linalg.inv(Aj)
+        Qr[j] = gr[j] if j == L - 1 else gr[j] @ V[j] @ Qr[j + 1]
+    G1L = Pl[L - 1]
+    gL, gR = broadening(sigL), broadening(sigR)
+    T = float(np.real(np.trace(gL @ G1L @ gR @ G1L.conj().T)))
+    mid = gR @ G1L.conj().T @ gL          # K_L x K_1
+    out = np.zeros((L, 2 * N))
+    for j in range(L):
+        Aj = A[j].copy()
+        if j > 0:
+            Aj -= V[j - 1].T @ gl[j - 1] @ V[j - 1]
+        if j < L - 1:
+            Aj -= V[j] @ gr[j + 1] @ V[j].T
+        Gjj = np.linalg.inv(Aj)
+        G1j = Gjj if j == 0 else Pl[j - 1] @ V[j - 1] @ Gjj
+        GjL = Gjj if j == L - 1 else Gjj @ V[j] @ Qr[j + 1]
+        out[j, keep[j]] = 2.0 * np.real(np.einsum("ia,ab,bi->i", GjL, mid, G1j))
+    return T, out

@@ -229,10 +229,11 @@ struct GJSmem {
 
 // The rank-b update of cta_gj_invert as a tensor-core product over one tile
 // of up to 128 rows: W[i][l] -= sum_jj c_jj[i] x_jj[l] for the block's own
-// columns l outside the panel (column c of the product -> l = own_col(c)) and
-// every row i; a pivot row j0 + r starts from x_r instead of W.  The multipliers and pivot rows are read from
-// shared memory (byte offsets into the dynamic shared memory); W is
-// column-major, so the 32 rows a warp drains are contiguous.
+// columns l outside the panel (column c of the product -> l = col(c)) and
+// every row i; a pivot row j0 + r starts from x_r instead of W.  The
+// multipliers and pivot rows are read from shared memory (byte offsets into
+// the dynamic shared memory); W is column-major, so the 32 rows a warp drains
+// are contiguous.
 struct GJUpdateOp {
     int cm_off;      // multipliers [bm][K]
     int xr_off;      // substituted pivot rows [bm][K]
@@ -387,7 +388,7 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
         }
         __syncthreads();
         // This block's columns outside the panel: the swaps, then the pivot
-        // rows by substitution, one column per 16-lane half-warp ...
+        // rows by block-wide substitution ...
         const int ps = max(j0, clo), pe = min(j0 + bb, chi);
         const int pskip = max(0, pe - ps);
         const int nown = (chi - clo) - pskip;            // own columns outside the panel

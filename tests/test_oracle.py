@@ -148,6 +148,33 @@ def test_gradient_adjoint_closed_form_and_finite_differences():
         assert abs(fd - gcf[n, i]) < 1e-8 + 1e-5 * abs(gcf[n, i])
 
 
+@pytest.mark.parametrize("E,eta_d", [(0.31, 1e-8), (-0.9, 1e-8), (0.004, 1e-8), (0.52, 0.0)])
+def test_gradient_two_sided_matches_closed_form(E, eta_d):
+    # The Dyson-assembled blocks (Eq. 3 with one bond cut) against the dense G
+    # of Eq. 1, with removed atoms (ragged slices).
+    N, L = 11, 6
+    eps = workloads.anderson_onsite(N, L, 0.3, 11)
+    rem = workloads.edge_removed(N, L, 0.3, 12)
+    T, g = gradient.two_sided(N, L, E, eta_d, 1e-8, T_HOP, eps, rem)
+    gcf = gradient.closed_form(N, L, E, eta_d, 1e-8, T_HOP, eps, rem)
+    assert np.abs(g - gcf).max() < 1e-12 * max(1.0, np.abs(gcf).max())
+    assert np.all(g[rem.astype(bool)] == 0.0)
+    assert abs(T - dense.transmission_dense(N, L, E, eta_d, 1e-8, T_HOP, eps, rem)) < 1e-12
+
+
+def test_gradient_two_sided_near_half_system_poles():
+    # Near E = 0 the ends of the half systems left and right of a cut carry
+    # nearly bound states; the two-sided form stays at the dense closed form
+    # (here within 1e-8 of the gradient's scale; the reverse sweep of the same
+    # recursion is off by about 2.5e-5 of it on this ribbon)
+    N, L = 20, 40
+    eps = workloads.anderson_onsite(N, L, 0.15, 7)
+    E = float(np.linspace(-0.12, 0.12, 12)[2])
+    _, g = gradient.two_sided(N, L, E, 1e-8, 1e-8, T_HOP, eps)
+    gcf = gradient.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps)
+    assert np.abs(g - gcf).max() < 1e-8 * np.abs(gcf).max()
+
+
 def test_gradient_sums_to_uniform_shift_derivative():
     # The derivative along a uniform shift of every device on-site energy is the
     # sum of the gradient.
