@@ -294,7 +294,8 @@ def run_grad(args):
     """dT/d eps for every on-site energy (rgf_conductance_grad, host buffers): the
     N = 101, L = 500 ribbon, Anderson +-0.15 eV, 128 energies in [-0.8, 0.8] eV,
     checkpoints every 23 cells.  One step = one call over all energies; the unit
-    is one unit-cell step of one chain (forward, recompute and reverse)."""
+    is one unit-cell step of one chain (right-to-left sweep, segment recompute
+    and left-to-right sweep of the two-sided gradient)."""
     import torch
     from paper_1107_5300_gb300 import rgf
     rank, world, local = dist_env()
@@ -330,8 +331,8 @@ def run_grad(args):
         rel = np.abs(g - g64).max(axis=(1, 2)) / np.where(scale > 0, scale, 1.0)
         far = both & (np.abs(Es) >= 0.1)
         near = both & (np.abs(Es) < 0.1)
-        # near E = 0 the reverse sweep over column slices amplifies rounding at
-        # isolated sites (binary64 included): reported apart
+        # energies near the charge-neutrality point (where the half systems'
+        # poles make the gradient ill-conditioned) reported apart
         parity = {"max_rel_dgrad_vs_fp64_absE_ge_0.1": float(rel[far].max()) if far.any() else None,
                   "median_rel_dgrad_vs_fp64": float(np.median(rel[both])) if both.any() else None,
                   "max_rel_dgrad_vs_fp64_absE_lt_0.1": float(rel[near].max()) if near.any() else None,

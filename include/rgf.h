@@ -156,9 +156,14 @@ rgf_status rgf_conductance_dev(const rgf_ribbon* const* rib, const double* E_dev
 
 /*
  * Conductance and its gradient dT/d eps for every on-site energy of the
- * scattering region (adjoint, reverse sweep over the recursion of Eqs. 4-5;
- * the slice Green's functions are checkpointed every ckpt_stride unit cells
- * and recomputed between checkpoints).  ckpt_stride <= 0 picks ~sqrt(L).
+ * scattering region: dT/d eps_i = 2 Re (G_iL Gamma_R G_1L^dagger Gamma_L G_1i)
+ * (from Eqs. 1-2), with the blocks of G assembled slice by slice through the
+ * Dyson equation (Eq. 3) from the recursion of Eqs. 4-5 run from both leads.
+ * The right-connected Green's functions are checkpointed every ckpt_stride
+ * unit cells and recomputed between checkpoints; ckpt_stride <= 0 picks
+ * ~sqrt(L).  Device workspace per chain: (14 + 2 ceil(4L / (4 s)) +
+ * 2 (4 s + 1)) ceil(N/2)^2 complex values (s the stride), 16 bytes each.
+ * T is the value rgf_conductance returns for the same chain, bit for bit.
  *   dT_deps: host [nchains][L*2N] binary64 (row-major per chain, orbital
  *            order of rgf_ribbon_desc); 0 on removed atoms.
  * Other arguments and errors as rgf_conductance.

@@ -1,8 +1,8 @@
 """``torch.autograd.Function`` over the conductance entry points.
 
 Forward: T(E_c) for every energy of one ribbon whose on-site energies are the
-input tensor (rgf_conductance).  Backward: the adjoint sweep
-(rgf_conductance_grad) gives dT_c/d eps for every site; the vector-Jacobian
+input tensor (rgf_conductance).  Backward: rgf_conductance_grad (the
+two-sided gradient sweep) gives dT_c/d eps for every site; the vector-Jacobian
 product sums them with the incoming weights.  All numerics run in librgf.so.
 """
 from __future__ import annotations

@@ -1,5 +1,9 @@
-"""Adjoint gradient dT/d eps (rgf_conductance_grad) against the oracle and
-against finite differences of the GPU conductance."""
+"""Gradient dT/d eps (rgf_conductance_grad) against the oracle (dense closed
+form, and golden values of its two-sided form on the N = 101, L = 500 ribbon)
+and against finite differences of the GPU conductance."""
+import json
+from pathlib import Path
+
 import numpy as np
 import pytest
 
@@ -8,6 +12,7 @@ from oracle import gradient as ograd
 
 pytestmark = pytest.mark.gpu
 T_HOP = -2.7
+GOLDEN = Path(__file__).resolve().parent / "golden"
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-8), (2, 1e-8)])
@@ -76,6 +81,41 @@ def test_gradient_against_finite_differences_n101(rgflib):
         gs = np.array([g[0, n, i] for (n, i) in sites])
         err = np.abs(gs - fd)
         assert np.all(err < 1e-5 + 1e-4 * np.abs(fd)), (prec, err.max())
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-7), (1, 1e-5), (2, 1e-5)])
+def test_gradient_next_to_a_half_system_pole(rgflib, prec, tol):
+    # N = 20, L = 40 (Anderson +-0.15 eV, seed 7) at E = -0.0764 eV, next to a
+    # pole of the half systems: a reverse sweep over the column slices is off
+    # by about 4e-4 of the gradient's scale here even in complex128.
+    N, L = 20, 40
+    eps = workloads.anderson_onsite(N, L, 0.15, 7)
+    E = float(np.linspace(-0.12, 0.12, 12)[2])
+    rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps)
+    T, g, st = rgflib.conductance_grad([rib], np.array([E]), 1e-8, 1e-8, prec, ckpt_stride=3)
+    assert st[0] == 0
+    ref = ograd.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps, None)
+    err = np.abs(g[0] - ref).max() / np.abs(ref).max()
+    assert err < tol, (prec, err)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 2e-4), (2, 2e-4)])
+def test_gradient_near_zero_energy_matches_golden(rgflib, prec, tol):
+    # The N = 101, L = 500 ribbon at three energies with |E| < 0.07 eV: the
+    # largest entries, seeded random sites and sites where a reverse sweep
+    # over column slices was off by 10 to 400 times the gradient's scale,
+    # against oracle.gradient.two_sided (tests/golden/make_grad_golden.py).
+    gold = json.loads((GOLDEN / "grad_two_sided.json").read_text())
+    eps = workloads.anderson_onsite(gold["N"], gold["L"], gold["W"], gold["seed"])
+    rib = rgflib.Ribbon(gold["N"], gold["L"], gold["t"], onsite=eps)
+    Es = np.array([cs["E"] for cs in gold["cases"]])
+    T, g, st = rgflib.conductance_grad([rib] * len(Es), Es, gold["eta_device"], gold["eta_lead"],
+                                       prec, ckpt_stride=23)
+    assert (st == 0).all()
+    for c, cs in enumerate(gold["cases"]):
+        assert abs(T[c] - cs["T"]) < 1e-7
+        for n, i, v in cs["sites"]:
+            assert abs(g[c, n, i] - v) < tol * cs["scale"], (prec, cs["E"], n, i, g[c, n, i], v)
 
 
 def test_autograd_function(rgflib):
