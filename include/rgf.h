@@ -66,7 +66,7 @@ typedef enum {
                             FP32 pipes, ~48-bit significand); leads and trace binary64 */
     RGF_MIXED_TC = 2     /* as RGF_MIXED, with the dense contractions of every slice
                             step (the rank-b updates of the slice inverse, the
-                            corner-strip product of Eq. 5, the adjoint's products) on
+                            corner-strip product of Eq. 5, the gradient's products) on
                             the tcgen05 tensor cores by exact bfloat16 digit slicing
                             (see rgf_zgemm_tc) */
 } rgf_precision;

@@ -110,7 +110,7 @@ struct Plan {
     int Kmax = 1;
 };
 
-// grad: size the adjoint workspace with checkpoints every ckpt_stride cells
+// grad: size the gradient workspace with checkpoints every ckpt_stride cells
 // (<= 0: ceil(sqrt(L))).
 rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl, bool grad = false,
                      int ckpt_stride = 0) {
@@ -175,7 +175,7 @@ __global__ void fill_energy(rgf::ChainDev* chains, rgf::LeadDev* leads, const do
 }
 
 // Runs the whole path on `st`: lead decimation, then the forward sweep (or,
-// with dT_dev, the checkpointed adjoint sweep).  E_dev, T_dev, status_dev,
+// with dT_dev, the checkpointed two-sided gradient sweep).  E_dev, T_dev, status_dev,
 // dT_dev: device.
 rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
                     double eta_device, double eta_lead, int precision, cudaStream_t st,
@@ -232,7 +232,7 @@ rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchai
         RGF_CUDA(rgf::launch_grad(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
                                   dlout.p, (int*)dlst.p, dleads, dws.p, dseg, T_dev, dT_dev,
                                   status_dev, st),
-                 "adjoint sweep launch");
+                 "gradient sweep launch");
     } else {
         RGF_CUDA(rgf::launch_sweep(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
                                    dlout.p, (int*)dlst.p, dleads, dws.p, T_dev, status_dev, st),

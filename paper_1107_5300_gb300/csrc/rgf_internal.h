@@ -32,7 +32,7 @@ struct ChainDev {
     double t, E;
     int lead;               // index of its lead problem
     size_t ws_off;          // offset (16-byte elements) of its sweep workspace
-    size_t grad_off;        // offset (doubles) of its dT/d eps block (adjoint only)
+    size_t grad_off;        // offset (doubles) of its dT/d eps block (gradient only)
 };
 
 // Number of 16-byte elements of the decimation workspace of one lead problem.
@@ -67,7 +67,7 @@ cudaError_t launch_sweep(int precision, const ChainDev* chains, const int* order
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st);
 
-// Adjoint sweep: workspace (16-byte elements) of one chain with segments of
+// Gradient sweep: workspace (16-byte elements) of one chain with segments of
 // seg_cols columns, and the launcher (seg_cols: [nchains] on the device; dT:
 // zero-initialised doubles, chain c's block at chains[c].grad_off).
 size_t grad_ws_elems(int N, int L, int seg_cols);

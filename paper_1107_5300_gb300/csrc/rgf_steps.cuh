@@ -1,5 +1,5 @@
 // rgf_steps.cuh -- one column step of the forward RGF recursion (Eqs. 4-5) and
-// the helpers shared by the forward sweep (rgf_sweep.cu) and the adjoint sweep
+// the helpers shared by the forward sweep (rgf_sweep.cu) and the gradient sweep
 // (rgf_grad.cu).  See rgf_sweep.cu for the column slicing.
 #pragma once
 
@@ -16,7 +16,7 @@ struct SweepSmem {
     cx<R>* gemm;
     uint8_t* kc;     // keep mask of the current column
     uint8_t* kp;     // keep mask of the previous column
-    uint8_t* kn;     // keep mask of the next column (adjoint)
+    uint8_t* kn;     // keep mask of the next column (gradient)
     double* eps;
     double* red;
     double* clmax;   // this block's partial max |A|^2, read by the team
@@ -130,7 +130,7 @@ struct DenseOp {
 };
 
 // C = op(A) B on the tensor cores over row tiles of 128; one out-of-line copy
-// for the adjoint's dense products (arguments by value; the sweep's strip
+// for the gradient's dense products (arguments by value; the sweep's strip
 // product is inlined).  Returns the next mbarrier phase.
 static __device__ __noinline__ uint32_t tc_dense(int m, int n, int kd, const zf* A, int lda,
                                                  const zf* B, int ldb, zf* C, int ldc, bool ta,
@@ -336,16 +336,6 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
         }
     }
     cta_gemm<R, false, false>(KL, n, K, Y, KL, Gk + lo, KL, Pout + lo, KL, GEMM_SET, s.gemm);
-}
-
-// One whole forward column step on one block (used by the adjoint).
-template <class R>
-__device__ int fwd_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout,
-                          const cx<R>* Pprev, cx<R>* Pout, cx<R>* X, cx<R>* Y,
-                          SweepSmem<R>& s) {
-    const int flag = inv_column<R>(c, k, Gprev, Gout, X, s);
-    strip_column<R>(c, k, Gout, Pprev, Pout, Y, s);
-    return flag;
 }
 
 // Tr[Gamma_L P Gamma_R P^dagger] in binary64.  P: KL x KR (ld KL) in the working
