@@ -23,8 +23,10 @@ nanoribbons using GPU", Comput. Phys. Commun. 183 (2012) 543):
   form with its blocks assembled slice by slice from left- and
   right-connected sweeps (accurate near E = 0), and the reverse (adjoint)
   sweep of the recursion.
+* ``ldos``     -- the local density of states -Im G_ii / pi from the
+  Dyson-assembled diagonal blocks of G.
 * ``bands``    -- channel counts: closed-form armchair band edges and a
-  brute-force band structure.
+  brute-force band structure; the Bloch-state LDOS of the infinite ribbon.
 * ``mp``       -- the same recursion in arbitrary precision (mpmath) for the
   ill-conditioned E = 0 point on small ribbons.
 """

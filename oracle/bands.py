@@ -11,6 +11,11 @@ states at E.  Two independent counts:
 * ``channels_band_structure``: diagonalise H(k) = H00 + H01 e^{ik} + H01^T e^{-ik}
   of the unit cell on a k grid and count, for every band, the sign changes of
   E_b(k) - E with positive slope.
+
+``bloch_ldos`` is the local density of states of the infinite pristine ribbon
+per orbital of a cell, from its Bloch states: every crossing k* of a band with
+E contributes |psi_b(k*)_i|^2 / (2 pi |dE_b/dk|), the slope taken from the
+Hellmann-Feynman form psi^dagger dH/dk psi.
 """
 from __future__ import annotations
 
@@ -46,3 +51,35 @@ def channels_band_structure(N: int, E: float, nk: int = 2001, t: float = -2.7, b
     d_next = np.roll(d, -1, axis=0)
     up = (d < 0) & (d_next >= 0)
     return int(np.sum(up))
+
+
+def _hk(H00, H01, k):
+    return H00 + H01 * np.exp(1j * k) + H01.T * np.exp(-1j * k)
+
+
+def bloch_ldos(N: int, E: float, nk: int = 4001, t: float = -2.7) -> np.ndarray:
+    """LDOS [2N] (states per eV per orbital) of the infinite pristine ribbon."""
+    H00, H01 = blocks(N, t)
+    ks, bands = band_structure(N, nk, t)
+    ks = np.append(ks, np.pi)
+    bands = np.vstack([bands, bands[:1]])
+    rho = np.zeros(2 * N)
+    for b in range(2 * N):
+        d = bands[:, b] - E
+        for i in np.nonzero(np.sign(d[:-1]) * np.sign(d[1:]) < 0)[0]:
+            lo, hi = ks[i], ks[i + 1]
+            flo = d[i]
+            for _ in range(60):
+                mid = 0.5 * (lo + hi)
+                fm = np.linalg.eigvalsh(_hk(H00, H01, mid))[b] - E
+                if np.sign(fm) == np.sign(flo):
+                    lo, flo = mid, fm
+                else:
+                    hi = mid
+            k = 0.5 * (lo + hi)
+            w, U = np.linalg.eigh(_hk(H00, H01, k))
+            psi = U[:, b]
+            dH = 1j * H01 * np.exp(1j * k) - 1j * H01.T * np.exp(-1j * k)
+            v = float(np.real(psi.conj() @ dH @ psi))
+            rho += np.abs(psi) ** 2 / (2.0 * np.pi * abs(v))
+    return rho

@@ -86,9 +86,13 @@ def adjoint(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=N
     return f["T"], out
 
 
-def two_sided(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
-    """Returns (T, dT/d eps [L, 2N]) from the closed form with the blocks of G
-    assembled by the Dyson relations above (left- and right-connected sweeps)."""
+def half_sweeps(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
+    """The left- and right-connected recursions (Eqs. 4-5 from either lead).
+
+    Returns a dict with the slice matrices A_j (z - H_jj, minus Sigma_L and
+    Sigma_R on the end slices), the couplings V, the kept-atom lists, gl / Pl
+    (G_jj and G_1j of slices 1..j), gr / Qr (G_jj and G_jL of slices j..L) and
+    the lead self-energies restricted to the kept atoms."""
     Hd, V, keep = device_slices(N, L, t, eps, removed)
     if sig is None:
         sig = self_energies(N, E, eta_lead, t)
@@ -98,30 +102,43 @@ def two_sided(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig
     A = [z * np.eye(len(keep[j])) - Hd[j] for j in range(L)]
     A[0] = A[0] - sigL
     A[L - 1] = A[L - 1] - sigR
-    # left-connected: gl[j] = G_jj and Pl[j] = G_1j of slices 1..j
     gl, Pl = [], []
     for j in range(L):
         Aj = A[j] if j == 0 else A[j] - V[j - 1].T @ gl[j - 1] @ V[j - 1]
         gl.append(np.linalg.inv(Aj))
         Pl.append(gl[j] if j == 0 else Pl[j - 1] @ V[j - 1] @ gl[j])
-    # right-connected: gr[j] = G_jj and Qr[j] = G_jL of slices j..L
     gr, Qr = [None] * L, [None] * L
     for j in range(L - 1, -1, -1):
         Aj = A[j] if j == L - 1 else A[j] - V[j] @ gr[j + 1] @ V[j].T
         gr[j] = np.linalg.inv(Aj)
         Qr[j] = gr[j] if j == L - 1 else gr[j] @ V[j] @ Qr[j + 1]
+    return dict(A=A, V=V, keep=keep, gl=gl, Pl=Pl, gr=gr, Qr=Qr, sigL=sigL, sigR=sigR)
+
+
+def diagonal_block(h, j):
+    """G_jj of the whole system: (A_j - V^T gl_{j-1} V - V gr_{j+1} V^T)^-1."""
+    A, V, gl, gr = h["A"], h["V"], h["gl"], h["gr"]
+    L = len(A)
+    Aj = A[j].copy()
+    if j > 0:
+        Aj -= V[j - 1].T @ gl[j - 1] @ V[j - 1]
+    if j < L - 1:
+        Aj -= V[j] @ gr[j + 1] @ V[j].T
+    return np.linalg.inv(Aj)
+
+
+def two_sided(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
+    """Returns (T, dT/d eps [L, 2N]) from the closed form with the blocks of G
+    assembled by the Dyson relations above (left- and right-connected sweeps)."""
+    h = half_sweeps(N, L, E, eta_device, eta_lead, t, eps, removed, sig)
+    V, keep, Pl, Qr = h["V"], h["keep"], h["Pl"], h["Qr"]
     G1L = Pl[L - 1]
-    gL, gR = broadening(sigL), broadening(sigR)
+    gL, gR = broadening(h["sigL"]), broadening(h["sigR"])
     T = float(np.real(np.trace(gL @ G1L @ gR @ G1L.conj().T)))
     mid = gR @ G1L.conj().T @ gL          # K_L x K_1
     out = np.zeros((L, 2 * N))
     for j in range(L):
-        Aj = A[j].copy()
-        if j > 0:
-            Aj -= V[j - 1].T @ gl[j - 1] @ V[j - 1]
-        if j < L - 1:
-            Aj -= V[j] @ gr[j + 1] @ V[j].T
-        Gjj = np.linalg.inv(Aj)
+        Gjj = diagonal_block(h, j)
         G1j = Gjj if j == 0 else Pl[j - 1] @ V[j - 1] @ Gjj
         GjL = Gjj if j == L - 1 else Gjj @ V[j] @ Qr[j + 1]
         out[j, keep[j]] = 2.0 * np.real(np.einsum("ia,ab,bi->i", GjL, mid, G1j))

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import workloads
-from oracle import bands, dense, gradient, lattice, leads, mp, rgf
+from oracle import bands, dense, gradient, lattice, ldos, leads, mp, rgf
 
 T_HOP = -2.7
 GOLDEN = Path(__file__).resolve().parent / "golden"
@@ -173,6 +173,32 @@ def test_gradient_two_sided_near_half_system_poles():
     _, g = gradient.two_sided(N, L, E, 1e-8, 1e-8, T_HOP, eps)
     gcf = gradient.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps)
     assert np.abs(g - gcf).max() < 1e-8 * np.abs(gcf).max()
+
+
+@pytest.mark.parametrize("E", [0.31, -0.9])
+def test_ldos_matches_dense_diagonal(E):
+    # -Im G_ii / pi from the Dyson-assembled diagonal blocks against the dense
+    # G of Eq. 1 (disorder, removed atoms)
+    N, L = 11, 6
+    eps = workloads.anderson_onsite(N, L, 0.3, 11)
+    rem = workloads.edge_removed(N, L, 0.3, 12)
+    r = ldos.ldos(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+    G, off, keep, _, _ = dense.green_dense(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+    ref = np.zeros((L, 2 * N))
+    for n in range(L):
+        ref[n, keep[n]] = -np.imag(np.diag(G)[off[n]:off[n + 1]]) / np.pi
+    assert np.abs(r - ref).max() < 1e-12 * np.abs(ref).max()
+    assert np.all(r[rem.astype(bool)] == 0.0) and np.all(r >= 0.0)
+
+
+@pytest.mark.parametrize("N,E", [(5, 0.9), (7, -1.3), (6, 2.2)])
+def test_ldos_of_pristine_ribbon_is_the_bloch_ldos(N, E):
+    # A pristine device between pristine leads (eta_device = 0) is a piece of
+    # the infinite ribbon: every cell has the LDOS of its Bloch states at E,
+    # computed from the band structure (band crossings, Hellmann-Feynman slopes)
+    b = bands.bloch_ldos(N, E)
+    r = ldos.ldos(N, 5, E, 0.0, 1e-8, T_HOP)
+    assert np.abs(r - b[None, :]).max() < 1e-6 * b.max()
 
 
 def test_gradient_sums_to_uniform_shift_derivative():
