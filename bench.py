@@ -94,6 +94,16 @@ def flops_per_cell(N: int) -> float:
     return f
 
 
+def cell_slicing_flops_per_step(N: int) -> float:
+    """Algorithmic real flops of one slice step when the slice is the whole unit
+    cell (M = 2N orbitals): an LU of the M x M slice matrix (8/3 M^3), the solve
+    for the floor(N/2) columns the next step needs (8 M^2 floor(N/2)) and the
+    corner-strip product (8 ceil(N/2)^2 floor(N/2)).  Reported beside the
+    column recursion's own count (flops_per_cell), which is lower."""
+    M, KL, KR = 2 * N, (N + 1) // 2, N // 2
+    return 8.0 / 3.0 * M ** 3 + 8.0 * M * M * KR + 8.0 * KL * KL * KR
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -485,8 +495,12 @@ def main():
                 traffic_note = "DRAM counters were taken on other kernel sources; not reported"
         except Exception:
             traffic = None
+    fl_cell_slicing = cell_slicing_flops_per_step(N) * float(ok.sum()) * L
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
+            "flops_per_step": flops_per_cell(N),
+            "cell_slicing_flops_per_step": cell_slicing_flops_per_step(N),
+            "achieved_at_cell_slicing_count": fl_cell_slicing / sweep_s / 1e12,
             **({} if traffic is not None else {"traffic_note": traffic_note}),
             "kernel": {0: "sweep_kernel<double>", 1: "sweep_kernel<df32>", 2: "sweep_kernel<df32,tc>"}[prec],
             "peak_source": f"derived from unit counts and sm_max_mhz={smax:.0f} ({peaks_src})",

@@ -53,3 +53,12 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--cpu-cells", "2"],
                    env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_flop_counts_per_slice_step():
+    # N = 245 (M = 490): the column recursion's count and the unit-cell count
+    # (LU + boundary solve + strip), 5.63e8
+    assert abs(bench.flops_per_cell(245) - 1.18e8) < 0.01e8
+    assert abs(bench.cell_slicing_flops_per_step(245) - 5.628e8) < 0.001e8
+    # N = 101 (M = 202): 3.9e7 by the unit-cell count
+    assert abs(bench.cell_slicing_flops_per_step(101) - 3.9e7) < 0.1e7
