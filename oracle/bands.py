@@ -25,6 +25,8 @@ from .lattice import blocks
 
 
 def channels_closed_form(N: int, E: float, t: float = -2.7) -> int:
+    """Right-moving channels at E from the closed-form armchair band edges (the
+    step-like conductance of an ideal ribbon, discussion of Fig. 3)."""
     p = np.arange(1, N + 1)
     c = np.cos(p * np.pi / (N + 1))
     lo = abs(t) * np.abs(1.0 + 2.0 * c)
@@ -33,7 +35,8 @@ def channels_closed_form(N: int, E: float, t: float = -2.7) -> int:
 
 
 def band_structure(N: int, nk: int = 2001, t: float = -2.7):
-    """Bands E_b(k), k in [-pi, pi) (nk points), shape [nk, 2N] sorted per k."""
+    """Bands E_b(k), k in [-pi, pi) (nk points), shape [nk, 2N] sorted per k
+    (the band structure behind the conductance steps discussed with Fig. 3)."""
     H00, H01 = blocks(N, t)
     ks = np.linspace(-np.pi, np.pi, nk, endpoint=False)
     out = np.empty((nk, 2 * N))
@@ -54,6 +57,7 @@ def channels_band_structure(N: int, E: float, nk: int = 2001, t: float = -2.7, b
 
 
 def _hk(H00, H01, k):
+    """Bloch Hamiltonian H(k) of the unit cell."""
     return H00 + H01 * np.exp(1j * k) + H01.T * np.exp(-1j * k)
 
 

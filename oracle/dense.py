@@ -15,7 +15,7 @@ from .leads import self_energies, broadening
 
 
 def green_dense(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
-    """Dense retarded G of the scattering region. Returns (G, off, keep, sigL, sigR)."""
+    """Dense retarded G of the scattering region. Returns (G, off, keep, sigL, sigR). (Eq. 1.)"""
     H, off, keep = full_hamiltonian(N, L, t, eps, removed)
     if sig is None:
         sig = self_energies(N, E, eta_lead, t)
@@ -30,6 +30,7 @@ def green_dense(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, s
 
 
 def transmission_dense(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
+    """T of Eq. 2 from the dense G of Eq. 1."""
     G, off, keep, sigL, sigR = green_dense(N, L, E, eta_device, eta_lead, t, eps, removed, sig)
     G1L = G[off[0]:off[1], off[L - 1]:off[L]]
     gL, gR = broadening(sigL), broadening(sigR)

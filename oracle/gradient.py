@@ -48,6 +48,7 @@ from .rgf import forward
 
 
 def closed_form(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None):
+    """dT/d eps_i = 2 Re[G_iL Gamma_R G_1L^dagger Gamma_L G_1i] with the dense G (from Eqs. 1-2)."""
     G, off, keep, sigL, sigR = green_dense(N, L, E, eta_device, eta_lead, t, eps, removed)
     gL, gR = broadening(sigL), broadening(sigR)
     first = slice(off[0], off[1])
@@ -63,7 +64,7 @@ def closed_form(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None):
 
 
 def adjoint(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
-    """Returns (T, dT/d eps [L, 2N])."""
+    """Returns (T, dT/d eps [L, 2N]). Reverse sweep of the recursion of Eqs. 4-5 (from Eqs. 1-2)."""
     f = forward(N, L, E, eta_device, eta_lead, t, eps, removed, sig, keep_history=True)
     g, Ps, V, keep = f["g"], f["Ps"], f["V"], f["keep"]
     gL, gR = broadening(f["sigL"]), broadening(f["sigR"])
@@ -116,7 +117,7 @@ def half_sweeps(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, s
 
 
 def diagonal_block(h, j):
-    """G_jj of the whole system: (A_j - V^T gl_{j-1} V - V gr_{j+1} V^T)^-1."""
+    """G_jj of the whole system: (A_j - V^T gl_{j-1} V - V gr_{j+1} V^T)^-1. (Dyson, Eq. 3.)"""
     A, V, gl, gr = h["A"], h["V"], h["gl"], h["gr"]
     L = len(A)
     Aj = A[j].copy()
@@ -129,7 +130,8 @@ def diagonal_block(h, j):
 
 def two_sided(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
     """Returns (T, dT/d eps [L, 2N]) from the closed form with the blocks of G
-    assembled by the Dyson relations above (left- and right-connected sweeps)."""
+    assembled by the Dyson relations above (left- and right-connected sweeps).
+    (Eqs. 1-3.)"""
     h = half_sweeps(N, L, E, eta_device, eta_lead, t, eps, removed, sig)
     V, keep, Pl, Qr = h["V"], h["keep"], h["Pl"], h["Qr"]
     G1L = Pl[L - 1]

@@ -19,7 +19,8 @@ import numpy as np
 
 
 def cell_coordinates(N: int, a: float = 1.0) -> np.ndarray:
-    """(2N, 2) array of (x, y) positions of one unit cell, orbital order 2j + k."""
+    """(2N, 2) array of (x, y) positions of one unit cell, orbital order 2j + k
+    (the geometry of Fig. 1(a))."""
     xy = np.zeros((2 * N, 2))
     h = np.sqrt(3.0) / 2.0 * a
     for j in range(N):
@@ -30,6 +31,7 @@ def cell_coordinates(N: int, a: float = 1.0) -> np.ndarray:
 
 
 def _bonds(xa: np.ndarray, xb: np.ndarray, a: float) -> np.ndarray:
+    """Adjacency of atoms xa[i], xb[j] at the C-C distance a (nearest neighbours)."""
     d = np.linalg.norm(xa[:, None, :] - xb[None, :, :], axis=-1)
     return np.abs(d - a) < 1e-6 * a
 
@@ -37,7 +39,8 @@ def _bonds(xa: np.ndarray, xb: np.ndarray, a: float) -> np.ndarray:
 def blocks(N: int, t: float = -2.7, a: float = 1.0):
     """Return (H00, H01): intra-cell and cell(n) -> cell(n+1) hopping blocks (2N x 2N, real).
 
-    H_{n,n+1} = H01 and H_{n+1,n} = H01.T.
+    H_{n,n+1} = H01 and H_{n+1,n} = H01.T.  One p orbital per carbon atom and
+    nearest-neighbour hopping (text around Fig. 1(a)).
     """
     xy = cell_coordinates(N, a)
     nxt = xy + np.array([3.0 * a, 0.0])
@@ -52,7 +55,8 @@ def device_slices(N, L, t, eps, removed):
     eps: [L, 2N] on-site energies (or None), removed: [L, 2N] uint8 (or None).
     Returns (Hd, V, keep): Hd[n] is the on-site block of slice n over its kept
     orbitals, V[n] = H_{n,n+1} between kept orbitals of slices n and n+1
-    (n = 0..L-2), keep[n] the kept orbital indices.
+    (n = 0..L-2), keep[n] the kept orbital indices.  (The scattering region of
+    length L, Fig. 1(a).)
     """
     H00, H01 = blocks(N, t)
     M = 2 * N
@@ -67,7 +71,7 @@ def device_slices(N, L, t, eps, removed):
 
 
 def full_hamiltonian(N, L, t, eps, removed):
-    """Dense Hamiltonian of the L-slice scattering region (kept orbitals only)."""
+    """Dense Hamiltonian of the L-slice scattering region (kept orbitals only). (The H of Eq. 1.)"""
     Hd, V, keep = device_slices(N, L, t, eps, removed)
     sizes = [len(k) for k in keep]
     off = np.concatenate([[0], np.cumsum(sizes)])

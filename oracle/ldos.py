@@ -20,7 +20,8 @@ from .gradient import diagonal_block, half_sweeps
 
 
 def ldos(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
-    """rho_i(E) in states per eV per orbital, [L, 2N]."""
+    """rho_i(E) in states per eV per orbital, [L, 2N]. (From Eq. 1; Dyson-assembled diagonal
+    blocks, Eq. 3.)"""
     h = half_sweeps(N, L, E, eta_device, eta_lead, t, eps, removed, sig)
     out = np.zeros((L, 2 * N))
     for j in range(L):

@@ -33,7 +33,8 @@ class NoConvergence(RuntimeError):
 
 
 def surface_green(H00, alpha0, beta0, z, tol=1e-14, max_iter=200):
-    """Sancho-Rubio surface Green's function. Returns (g_s, iterations)."""
+    """Sancho-Rubio surface Green's function. Returns (g_s, iterations). (The lead self-energies
+    entering at the first and last slice, text after Eqs. 4-5.)"""
     M = H00.shape[0]
     I = np.eye(M)
     eps_s = H00.astype(np.complex128).copy()
@@ -61,7 +62,8 @@ def fixed_point_residual(g_s, H00, alpha0, beta0, z):
 
 
 def self_energies(N, E, eta, t=-2.7, tol=1e-14, max_iter=200, return_iters=False):
-    """Full-cell (2N x 2N) Sigma_L and Sigma_R of pristine semi-infinite leads."""
+    """Full-cell (2N x 2N) Sigma_L and Sigma_R of pristine semi-infinite leads. (Text after Eqs.
+    4-5.)"""
     H00, H01 = blocks(N, t)
     z = E + 1j * eta
     gR, itR = surface_green(H00, H01, H01.T, z, tol, max_iter)
@@ -74,5 +76,5 @@ def self_energies(N, E, eta, t=-2.7, tol=1e-14, max_iter=200, return_iters=False
 
 
 def broadening(sigma):
-    """Gamma = i (Sigma - Sigma^dagger)."""
+    """Gamma = i (Sigma - Sigma^dagger). (Eq. 2.)"""
     return 1j * (sigma - sigma.conj().T)

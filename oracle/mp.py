@@ -18,14 +18,17 @@ from .lattice import blocks, device_slices
 
 
 def _m(a):
+    """mpmath matrix from a numpy array."""
     return mpm.matrix(np.asarray(a).tolist())
 
 
 def _absmax(m):
+    """Largest entry magnitude of an mpmath matrix."""
     return max(abs(m[i, j]) for i in range(m.rows) for j in range(m.cols))
 
 
 def _surface(H00, a0, b0, z, tol):
+    """Sancho-Rubio decimation in dps digits (text after Eqs. 4-5)."""
     M = H00.rows
     I = mpm.eye(M)
     eps_s, eps, al, be = H00.copy(), H00.copy(), a0.copy(), b0.copy()
@@ -58,6 +61,7 @@ def self_energies(N, E, eta, t=-2.7, dps=40):
 
 
 def transmission(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, dps=40):
+    """T of Eq. 2 by the recursion of Eqs. 4-5 in dps digits."""
     with mpm.workdps(dps):
         tol = mpm.mpf(10) ** (-(dps - 5))
         H00n, H01n = blocks(N, t)

@@ -23,6 +23,7 @@ from .leads import self_energies, broadening
 
 
 def _sigmas(N, E, eta_lead, t, keep, sig):
+    """Lead self-energies restricted to the kept atoms of the end slices (text after Eqs. 4-5)."""
     if sig is None:
         sig = self_energies(N, E, eta_lead, t)
     sigL_full, sigR_full = sig
@@ -31,7 +32,8 @@ def _sigmas(N, E, eta_lead, t, keep, sig):
 
 def forward(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None,
             keep_history=False):
-    """Left-to-right sweep. Returns dict with T, P (= G_1L), and optionally g[], P[] history."""
+    """Left-to-right sweep. Returns dict with T, P (= G_1L), and optionally g[], P[] history. (Eqs.
+    4-5, then Eq. 2.)"""
     Hd, V, keep = device_slices(N, L, t, eps, removed)
     sigL, sigR = _sigmas(N, E, eta_lead, t, keep, sig)
     z = E + 1j * eta_device
@@ -60,12 +62,14 @@ def forward(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=N
 
 
 def transmission(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None, sig=None):
+    """T of Eq. 2 by the forward recursion of Eqs. 4-5."""
     return forward(N, L, E, eta_device, eta_lead, t, eps, removed, sig)["T"]
 
 
 def transmission_right_to_left(N, L, E, eta_device, eta_lead, t=-2.7, eps=None, removed=None,
                                sig=None):
-    """The mirror sweep (from the right lead to the left): T_RL = Tr[Gamma_R G_L1 Gamma_L G_L1^dagger]."""
+    """The mirror sweep (from the right lead to the left): T_RL = Tr[Gamma_R G_L1 Gamma_L
+    G_L1^dagger]."""
     Hd, V, keep = device_slices(N, L, t, eps, removed)
     sigL, sigR = _sigmas(N, E, eta_lead, t, keep, sig)
     z = E + 1j * eta_device
