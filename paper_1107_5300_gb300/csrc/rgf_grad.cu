@@ -41,9 +41,10 @@ __device__ void copy_blk(cx<R>* D, const cx<R>* S, size_t n) {
 
 // X = (z - eps_k) I - [left] SigmaL_k - [right] SigmaR_k for column k, identity
 // rows and columns at removed atoms.  SigmaL_k: Sigma_L at k = 0, else
-// t^2 W_k^T glp W_k; SigmaR_k: Sigma_R at the last column, else
-// t^2 W_{k+1} grn W_{k+1}^T.  Needs s.kc, s.eps of column k, s.kp of k-1 and
-// s.kn of k+1.  Returns max |X_il|^2 over the block (ends with a barrier).
+// W_k^T glp W_k; SigmaR_k: Sigma_R at the last column, else
+// W_{k+1} grn W_{k+1}^T (W = t times the bond pattern between two columns,
+// applied as a stencil).  Needs s.kc, s.eps of column k, s.kp of k-1 and s.kn
+// of k+1.  Returns max |X_il|^2 over the block (ends with a barrier).
 template <class R>
 __device__ double build_A(const ChainCtx& c, int k, bool left, const cx<R>* glp, bool right,
                           const cx<R>* grn, cx<R>* X, SweepSmem<R>& s) {
