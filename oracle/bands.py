@@ -26,12 +26,15 @@ from .lattice import blocks
 
 def channels_closed_form(N: int, E: float, t: float = -2.7) -> int:
     """Right-moving channels at E from the closed-form armchair band edges (the
-    step-like conductance of an ideal ribbon, discussion of Fig. 3)."""
+    step-like conductance of an ideal ribbon, discussion of Fig. 3).  A lower
+    edge within 1e-12 |t| of |E| counts: the metallic mode of N = 3q + 2 has its
+    edge at exactly 0, a linear band crossing that carries one channel at E = 0
+    (rounding of the cosine puts the computed edge a few 1e-16 eV off 0)."""
     p = np.arange(1, N + 1)
     c = np.cos(p * np.pi / (N + 1))
     lo = abs(t) * np.abs(1.0 + 2.0 * c)
     hi = abs(t) * (1.0 + 2.0 * np.abs(c))
-    return int(np.sum((lo < abs(E)) & (abs(E) < hi)))
+    return int(np.sum((lo <= abs(E) + 1e-12 * abs(t)) & (abs(E) < hi)))
 
 
 def band_structure(N: int, nk: int = 2001, t: float = -2.7):

@@ -40,12 +40,14 @@ def test_band_edges_closed_form_vs_band_structure():
 
 
 def test_metallic_armchair_has_one_channel_at_low_energy():
-    # N = 3q + 2 armchair ribbons are metallic; N = 11 has one channel on [-1, 1] eV.
+    # N = 3q + 2 armchair ribbons are metallic; N = 11 has one channel on [-1, 1] eV,
+    # E = 0 included (the linear crossing of the metallic mode; the 40-digit
+    # T(0) of tests/golden/mp_transmission.json is 0.99999985); N = 3q + 1 has a gap.
     for E in np.linspace(-1, 1, 21):
-        if E == 0:
-            continue
         assert bands.channels_closed_form(11, E) == 1
+    assert bands.channels_closed_form(245, 0.0) == 1
     assert bands.channels_closed_form(245, 0.5) == 17
+    assert bands.channels_closed_form(7, 0.0) == 0 and bands.channels_closed_form(7, 0.3) == 0
 
 
 def _chain_surface(E, eta, t=T_HOP):
@@ -233,3 +235,122 @@ def test_mp_recursion_matches_complex128_when_well_conditioned():
     a = mp.transmission(N, L, E, 1e-8, 1e-8, T_HOP, eps, dps=30)
     b = rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, eps)
     assert abs(a - b) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Lead self-energies in the transverse-mode basis (oracle.modes) and the
+# recursion with the end slices in that basis (oracle.rgf.transmission_modes).
+# ---------------------------------------------------------------------------
+from oracle import modes  # noqa: E402
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 11, 12, 24])
+def test_mode_self_energies_equal_full_cell_decimation(N):
+    # The closed form (root of the mode chain's surface Dyson equation) is the
+    # value the full-cell Sancho-Rubio iteration converges to (text after
+    # Eqs. 4-5: the self-energies enter at the first and the last slice).
+    for E in (-1.3, -0.2, 0.003, 0.4, 1.7, 3.1):
+        a = modes.self_energies(N, E, 1e-8, T_HOP)
+        b = leads.self_energies(N, E, 1e-8, T_HOP)
+        for x, y in zip(a, b):
+            assert np.abs(x - y).max() < 1e-10 * max(1.0, np.abs(y).max()), (N, E)
+
+
+def test_mode_surface_green_function_special_cases():
+    # tau = t: the mode chain is the monatomic chain (textbook closed form);
+    # every root is the retarded one (Im g < 0) and a fixed point of the
+    # surface Dyson equation.
+    for E in (-3.0, -0.7, 0.0, 0.4, 5.5):
+        g = modes.surface_green(E + 1e-8j, T_HOP, T_HOP)
+        assert abs(g - _chain_surface(E, 1e-8)) < 1e-12 * abs(g)
+    for N in (5, 11, 24):
+        for E in (0.0, 1e-3, 0.4, 2.0):
+            assert modes.dyson_residual(N, E, 1e-8, T_HOP) < 1e-13
+            assert np.all(modes.mode_self_energies(N, E, 1e-8, T_HOP).imag <= 0.0)
+
+
+def test_mode_vectors_diagonalise_the_decimated_self_energy():
+    N, E = 12, 0.37
+    UL, UR = modes.mode_vectors(N)
+    assert np.abs(UL.T @ UL - np.eye(UL.shape[0])).max() < 1e-13
+    assert np.abs(UR.T @ UR - np.eye(UR.shape[0])).max() < 1e-13
+    sL, sR = leads.self_energies(N, E, 1e-8, T_HOP)
+    iL, iR = modes.left_orbitals(N), modes.right_orbitals(N)
+    w = modes.mode_self_energies(N, E, 1e-8, T_HOP)
+    dL = UL.T @ sL[np.ix_(iL, iL)] @ UL
+    dR = UR.T @ sR[np.ix_(iR, iR)] @ UR
+    assert np.abs(dL - np.diag(w)).max() < 1e-10 * np.abs(w).max()
+    assert np.abs(dR - np.diag(w[:UR.shape[0]])).max() < 1e-10 * np.abs(w).max()
+
+
+def test_mode_self_energies_at_charge_neutrality_vs_40_digits():
+    # At E = 0 the surface-state modes give |Sigma| ~ 1e9 eV; the closed form
+    # keeps full relative accuracy against 40-digit decimation (oracle.mp).
+    for N in (5, 6):
+        sL, sR = mp.self_energies(N, 0.0, 1e-8, T_HOP, dps=40)
+        a = modes.self_energies(N, 0.0, 1e-8, T_HOP)
+        assert np.abs(a[0] - sL).max() < 1e-13 * np.abs(sL).max()
+        assert np.abs(a[1] - sR).max() < 1e-13 * np.abs(sR).max()
+
+
+def test_mp_self_energies_match_decimation_when_well_conditioned():
+    sL, sR = mp.self_energies(5, 0.37, 1e-8, T_HOP, dps=30)
+    a, b = leads.self_energies(5, 0.37, 1e-8, T_HOP)
+    assert np.abs(sL - a).max() < 1e-12 * np.abs(a).max()
+    assert np.abs(sR - b).max() < 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("N,L,p", [(5, 1, 0.0), (11, 3, 0.0), (12, 7, 0.0), (23, 5, 0.3), (2, 3, 0.0)])
+def test_transmission_modes_equals_recursion_and_dense(N, L, p):
+    # An orthogonal change of basis on the lead-attached atoms of the end slices
+    # changes neither G_1L's trace (Eq. 2) nor the recursion (Eqs. 4-5).
+    eps = workloads.anderson_onsite(N, L, 0.25, 100 + N)
+    rem = None
+    if p > 0:
+        rem = workloads.edge_removed(N, L, p, 7)
+        rem[0, modes.left_orbitals(N)] = 0
+        rem[-1, modes.right_orbitals(N)] = 0
+    for E in (-1.1, -0.3, 0.02, 0.45):
+        a = rgf.transmission_modes(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        b = rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        c = dense.transmission_dense(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+        assert abs(a - b) < 1e-11 and abs(a - c) < 1e-11, (N, L, E, a, b, c)
+
+
+def test_transmission_modes_at_charge_neutrality_vs_40_digits():
+    # E = 0 exactly (eta = 1e-8 eV): with the end slices in the mode basis the
+    # complex128 recursion meets the 40-digit values to 1e-9 on the disordered
+    # ribbon (measured 3.1e-10; the site-basis recursion is off by 7.5e-5) and to
+    # 2e-7 on the pristine one, whose every partial system carries a surface
+    # state at E = 0 (measured 5.2e-8; site basis: 1.6e-3).
+    g = json.loads((GOLDEN / "mp_transmission.json").read_text())
+    for name, tol in (("agnr5_L8_anderson_E0", 1e-9), ("agnr11_L10_pristine_E0", 2e-7),
+                      ("agnr5_L8_anderson_E1e-3", 1e-12), ("agnr11_L10_pristine_E1e-4", 1e-12)):
+        v = g[name]
+        eps = workloads.anderson_onsite(v["N"], v["L"], v["W"], v["seed"]) if v["W"] > 0 else None
+        T = rgf.transmission_modes(v["N"], v["L"], v["E"], v["eta_device"], v["eta_lead"], T_HOP, eps)
+        assert abs(T - v["T"]) < tol, (name, T - v["T"])
+
+
+def test_removed_atom_is_the_infinite_onsite_limit():
+    # Dropping an atom (its orbital removed from its slice) is the limit of an
+    # infinite on-site energy on it: T and the gradient at the other sites
+    # approach the dropped values as 1/eps.
+    N, L, E = 11, 4, 0.31
+    eps = workloads.anderson_onsite(N, L, 0.2, 8)
+    rem = np.zeros((L, 2 * N), dtype=np.uint8)
+    sites = [(1, 0), (2, 2 * N - 1), (3, 1)]
+    for n, o in sites:
+        rem[n, o] = 1
+    T_drop = rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+    g_drop = gradient.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps, rem)
+    devs = []
+    for big in (1e6, 1e7):
+        e2 = eps.copy()
+        for n, o in sites:
+            e2[n, o] = big
+        T_big = rgf.transmission(N, L, E, 1e-8, 1e-8, T_HOP, e2, None)
+        g_big = gradient.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, e2, None)
+        devs.append(abs(T_big - T_drop))
+        assert np.abs(g_big - g_drop).max() < 100.0 / big * max(1.0, np.abs(g_drop).max())
+    assert devs[1] < 1e-5 and devs[1] < 0.2 * devs[0] + 1e-12
