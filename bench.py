@@ -16,8 +16,15 @@ Arms:
                     also the FP64 path once on the same ribbon for |dT|.
   --precision mixed the double-float path on the FP32 pipes alone (RGF_MIXED).
   --impl reference  the CPU oracle on a bounded sample of the same workload.
-Under torchrun each rank runs its own disorder realisation (seed + rank): the
-chains shard with no collective on the data path ("weak" scaling).
+Under torchrun the job holds one disorder realisation per rank (seed + rank)
+at every energy, and its chain list is sharded over the ranks by the
+library's longest-processing-time partition (paper_1107_5300_gb300.shard): no
+collective on the data path, one gather of T to rank 0 after the timed
+region ("weak" scaling: the work per GPU is fixed as ranks are added).
+
+Other workloads: --workload batched_uneven_chains (2048 uneven chains;
+--cells caps L), agnr101_L500_grad (dT/d eps), agnr1001_L2000 (the 123 nm
+ribbon, N = 1001; --cells and --energies take a bounded sample).
 """
 from __future__ import annotations
 
@@ -157,18 +164,6 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload_arrays(args, rank):
-    w = workloads.WORKLOADS[args.workload]
-    N, L = w["N"], (args.cells or w["L"])
-    seed = w["seed"] + rank
-    eps = workloads.anderson_onsite(N, L, w["W"], seed)
-    rem = workloads.edge_removed(N, L, w["edge_p"], w["edge_seed"] + rank) if w["edge_p"] > 0 else None
-    Es = w["energies"]()
-    if args.energies:
-        Es = Es[: args.energies]
-    return w, N, L, eps, rem, Es, seed
-
-
 def cpu_oracle_sample(N, L_s, E, W, seed, rem_p=0.0, edge_seed=0):
     """Times the CPU oracle (as it stands) on one energy x L_s cells."""
     from oracle import rgf as orgf
@@ -177,6 +172,20 @@ def cpu_oracle_sample(N, L_s, E, W, seed, rem_p=0.0, edge_seed=0):
     t0 = time.perf_counter()
     orgf.transmission(N, L_s, E, 1e-8, 1e-8, -2.7, eps, rem)
     return time.perf_counter() - t0
+
+
+def cpu_baseline(N, cells, W, seed):
+    """The oracle as it stands on 1 energy x `cells` cells of the workload, with
+    all BLAS threads and with one."""
+    from threadpoolctl import threadpool_limits
+    dt = cpu_oracle_sample(N, cells, 0.3, W, seed)
+    with threadpool_limits(limits=1):
+        dt1 = cpu_oracle_sample(N, cells, 0.3, W, seed)
+    sample = f"1 energy (E=0.3 eV) x {cells} cells of N={N}, whole path (decimation + recursion + trace)"
+    return {"value": cells / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": sample,
+            "single_thread": {"value": cells / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": sample}}
 
 
 def blas_threads():
@@ -262,7 +271,7 @@ def run_uneven(args):
                 e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-            ms_sweep.append(rgf.profile_read()[1])
+            ms_sweep.append(rgf.profile_read_phases()[2])
     rgf.profile_enable(False)
     status = Sd.cpu().numpy()
     T = Td.cpu().numpy()
@@ -276,11 +285,14 @@ def run_uneven(args):
         parity = {"max_abs_dT_vs_fp64": float(np.abs(T - T64)[both].max()) if both.any() else None,
                   "chains_compared": int(both.sum()), "status_mismatch": int((status != s64).sum()),
                   "tolerance": 1e-6}
-    fl = sum(flops_per_cell(int(N)) * float(L) for N, L, o in zip(Ns, cells, ok) if o)
+    fl = sum(cell_slicing_flops_per_step(int(N)) * float(L) for N, L, o in zip(Ns, cells, ok) if o)
     achieved = fl / (statistics.mean(ms_sweep) / 1e3) / 1e12
     peaks, src = measured_peaks()
-    smax = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = 152 * 128 * smax * 1e6 * 8.0 / 54.0 / 1e12 if prec != rgf.RGF_FP64 else 1.25
+    if prec != rgf.RGF_FP64:
+        bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        peak_src = f"bf16_tflops_sustained of MEASURED_PEAKS.json ({src})"
+    else:
+        bound, peak, peak_src = "alu", 1.25, "nominal GB300 FP64 rate (no measured figure)"
     clocks = sampler.summary()
     out = {"metric": "RGF slice-inversions/s (uneven batch, M in [102, 802])", "value": units * args.steps / t,
            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -291,10 +303,12 @@ def run_uneven(args):
                       "precision": args.precision, "l2": "flushed (256 MB write) between steps"},
            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                       "reasons": clocks["reasons"]},
-           "gpu_launches": 3 * args.steps,
-           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "gpu_launches": 5 * args.steps,
+           "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": None,
-                        "peak_source": f"derived from unit counts and sm_max_mhz={smax:.0f} ({src})"},
+                        "kernel": "half_kernel (the half sweeps alone)",
+                        "flops_note": "F_alg(M = 2N) per unit-cell slice step of each chain",
+                        "peak_source": peak_src},
            "parity": parity,
            "status_counts": {rgf.STATUS_NAMES[s]: int((status == s).sum()) for s in set(status.tolist())}}
     print(json.dumps(out), flush=True)
@@ -383,14 +397,30 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1107_5300_gb300 import rgf
+    from paper_1107_5300_gb300 import rgf, shard
 
     prec = {"mixed": rgf.RGF_MIXED, "tc": rgf.RGF_MIXED_TC, "fp64": rgf.RGF_FP64}[args.precision]
-    w, N, L, eps, rem, Es, seed = workload_arrays(args, rank)
+    w = workloads.WORKLOADS[args.workload]
+    N, L = w["N"], (args.cells or w["L"])
+    Es_all = w["energies"]()
+    if args.energies:
+        Es_all = Es_all[: args.energies]
+    # The job: one disorder realisation (seed + r) per rank, every energy of the
+    # grid; the chain list is sharded over the ranks longest-processing-time
+    # first (shard.lpt_partition), so each rank evaluates its share with no
+    # exchange on the data path and one gather brings T to rank 0.
+    job = [dict(N=N, L=L, seed=w["seed"] + r, E=float(e), idx=(r, i))
+           for r in range(world) for i, e in enumerate(Es_all)]
+    mine = [job[i] for i in shard.lpt_partition([shard.chain_cost(N, L)] * len(job), world)[rank]]
+    seeds = sorted({c["seed"] for c in mine})
+    arrays = {sd: (workloads.anderson_onsite(N, L, w["W"], sd),
+                   workloads.edge_removed(N, L, w["edge_p"], w["edge_seed"] + sd - w["seed"])
+                   if w["edge_p"] > 0 else None) for sd in seeds}
+    ribbons = {sd: rgf.Ribbon(N, L, -2.7, onsite=arrays[sd][0], removed=arrays[sd][1]) for sd in seeds}
+    ribs = [ribbons[c["seed"]] for c in mine]
+    Es = np.array([c["E"] for c in mine])
     n = Es.size
     stream = torch.cuda.Stream()
-    rib = rgf.Ribbon(N, L, -2.7, onsite=eps, removed=rem)
-    ribs = [rib] * n
     Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
     Td = torch.empty(n, dtype=torch.float64, device="cuda")
     Sd = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -409,7 +439,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     peaks, peaks_src = measured_peaks()
-    ms_steps, ms_sweep, ms_lead = [], [], []
+    ms_steps, phases = [], []
     sampler = ClockSampler(local)
     with sampler:
         for _ in range(args.steps):
@@ -422,9 +452,7 @@ def main():
                 e1.record(stream)
             e1.synchronize()
             ms_steps.append(e0.elapsed_time(e1))
-            a, b = rgf.profile_read()
-            ms_lead.append(a)
-            ms_sweep.append(b)
+            phases.append(rgf.profile_read_phases())
     torch.cuda.synchronize()
     rgf.profile_enable(False)
     if dist:
@@ -439,11 +467,14 @@ def main():
         tmax = tt.clone(); dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
         usum = tt.clone(); dist.all_reduce(usum[1:], op=dist.ReduceOp.SUM)
         t_job, units = float(tmax[0]), float(usum[1])
+        gathered = [None] * world if rank == 0 else None
+        dist.gather_object(([c["idx"] for c in mine], T, status), gathered, dst=0)
     else:
         t_job, units = t_local, units_local
+        gathered = [([c["idx"] for c in mine], T, status)]
     value = units * args.steps / t_job
 
-    # Parity of this arm against the FP64 GPU path on the same ribbon (untimed).
+    # Parity of this arm against the FP64 GPU path on the same chains (untimed).
     parity = None
     if not args.no_check and prec != rgf.RGF_FP64:
         T64, s64 = rgf.conductance(ribs, Es, 1e-8, 1e-8, rgf.RGF_FP64, check=False)
@@ -452,6 +483,8 @@ def main():
         low = both & (np.abs(Es) <= 5e-3)
         parity = {"max_abs_dT_vs_fp64": float(d[both].max()) if both.any() else None,
                   "max_abs_dT_low_energy": float(d[low].max()) if low.any() else None,
+                  "abs_dT_at_E0": (float(d[both & (Es == 0.0)].max())
+                                   if (both & (Es == 0.0)).any() else None),
                   "chains_compared": int(both.sum()),
                   "status_mismatch": int((status != s64).sum()),
                   "tolerance": 1e-6}
@@ -460,73 +493,101 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e_steps = min(args.steps, 2)
+        h2d = d2h = 0
+        okn = 0
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            r2 = rgf.Ribbon(N, L, -2.7, onsite=eps, removed=rem)
-            Th, sh = rgf.conductance([r2] * n, Es, 1e-8, 1e-8, prec, check=False)
-            r2.close()
+            rs = {sd: rgf.Ribbon(N, L, -2.7, onsite=arrays[sd][0], removed=arrays[sd][1])
+                  for sd in seeds}
+            Th, sh = rgf.conductance([rs[c["seed"]] for c in mine], Es, 1e-8, 1e-8, prec, check=False)
+            for r in rs.values():
+                r.close()
+            okn += int((sh == 0).sum())
         te = time.perf_counter() - t0
-        h2d = eps.nbytes + (rem.nbytes if rem is not None else 0) + Es.nbytes
+        for sd in seeds:
+            h2d += arrays[sd][0].nbytes + (arrays[sd][1].nbytes if arrays[sd][1] is not None else 0)
+        h2d += Es.nbytes
         d2h = Th.nbytes + sh.nbytes
-        e2e = {"value": float((sh == 0).sum()) * L * e2e_steps / te * (world if dist else 1),
-               "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        if dist:
+            tt = torch.tensor([te, okn * L], dtype=torch.float64, device="cuda")
+            tm = tt.clone(); dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+            us = tt.clone(); dist.all_reduce(us[1:], op=dist.ReduceOp.SUM)
+            te, e2e_units = float(tm[0]), float(us[1])
+        else:
+            e2e_units = okn * L
+        e2e = {"value": e2e_units / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
 
-    # Roofline of the dominant kernel (the slice sweep).
-    fl = flops_per_cell(N) * float(ok.sum()) * L
-    sweep_s = statistics.mean(ms_sweep) / 1e3
+    # Roofline of the dominant kernel (the half sweeps): algorithmic flops of
+    # the slice steps it processes (the unit-cell count F_alg(M)) over its
+    # CUDA-event duration, against the measured sustained bf16 tensor peak.
+    ph = np.array(phases)                       # [steps, 4]: lead, prep, half, merge
+    half_s = float(ph[:, 2].mean()) / 1e3
+    steps_ok = float(ok.sum()) * L
+    F_alg = cell_slicing_flops_per_step(N)
+    achieved = F_alg * steps_ok / half_s / 1e12
     smax = float(peaks.get("sm_max_mhz", 2070.0))
-    if prec in (rgf.RGF_MIXED, rgf.RGF_MIXED_TC):
-        # double-float arithmetic on the FP32 pipes: 54 FP32 instructions per
-        # complex multiply-add (8 algorithmic flops); 152 SMs x 128 lanes.
-        peak = 152 * 128 * smax * 1e6 * 8.0 / 54.0 / 1e12
-        bound = "alu"
+    alu_peak = 152 * 128 * smax * 1e6 * 8.0 / 54.0 / 1e12
+    if prec == rgf.RGF_FP64:
+        bound, peak, peak_src = "alu", 1.25, "nominal GB300 FP64 rate (no measured figure)"
     else:
-        peak = 1.25    # FP64 pipe, nominal TFLOP/s
-        bound = "alu"
-    achieved = fl / sweep_s / 1e12
+        bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        peak_src = f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peaks_src})"
     traffic_file = ROOT / "profiles" / "traffic.json"
     traffic, traffic_note = None, "no DRAM counters recorded for this kernel and workload"
     if traffic_file.exists():
         try:
             rec = json.loads(traffic_file.read_text())
-            traffic = rec.get(f"sweep_{args.precision}_{args.workload}")
+            traffic = rec.get(f"half_{args.precision}_{args.workload}")
+            if traffic is not None:
+                traffic = float(traffic) * (L / float(rec.get("_cells", L)))
             if traffic is not None and rec.get("_sources_sha256") != kernel_sources_digest():
                 traffic = None
                 traffic_note = "DRAM counters were taken on other kernel sources; not reported"
         except Exception:
             traffic = None
-    fl_cell_slicing = cell_slicing_flops_per_step(N) * float(ok.sum()) * L
+    algo_bytes = float(ok.sum()) * L * 2 * N * 8     # the on-site energies each slice step reads
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "flops_per_step": flops_per_cell(N),
-            "cell_slicing_flops_per_step": cell_slicing_flops_per_step(N),
-            "achieved_at_cell_slicing_count": fl_cell_slicing / sweep_s / 1e12,
             **({} if traffic is not None else {"traffic_note": traffic_note}),
-            "kernel": {0: "sweep_kernel<double>", 1: "sweep_kernel<df32>", 2: "sweep_kernel<df32,tc>"}[prec],
-            "peak_source": f"derived from unit counts and sm_max_mhz={smax:.0f} ({peaks_src})",
-            "ms_sweep": statistics.mean(ms_sweep), "ms_lead": statistics.mean(ms_lead)}
+            "kernel": {0: "half_kernel<double>", 1: "half_kernel<df32>", 2: "half_kernel<df32,tc>"}[prec],
+            "flops_per_step": F_alg,
+            "flops_note": "F_alg(M) = 8/3 M^3 + 8 M^2 floor(N/2) + 8 ceil(N/2)^2 floor(N/2) per unit-cell "
+                          "slice step (M = 2N); achieved = F_alg x slice steps / half-sweep kernel time",
+            "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": algo_bytes,
+            "column_slicing_flops_per_step": flops_per_cell(N),
+            "achieved_at_column_slicing_count": flops_per_cell(N) * steps_ok / half_s / 1e12,
+            "alu_peak_double_float": alu_peak,
+            "frac_of_alu_peak_at_column_slicing_count": flops_per_cell(N) * steps_ok / half_s / 1e12 / alu_peak,
+            "ms_half": float(ph[:, 2].mean()), "ms_lead": float(ph[:, 0].mean()),
+            "ms_prep": float(ph[:, 1].mean()), "ms_merge": float(ph[:, 3].mean())}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        L_s = args.cpu_cells
-        dt = cpu_oracle_sample(N, L_s, 0.3, w["W"], seed)
-        cpu = {"value": L_s / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-               "sample": f"1 energy (E=0.3 eV) x {L_s} cells of N={N}, whole path"}
+        cpu = cpu_baseline(N, args.cpu_cells, w["W"], w["seed"])
 
     clocks = sampler.summary()
     if rank == 0:
+        T_all = np.full(len(job), np.nan)
+        for idx, Tr, _ in gathered:
+            for (r, i), t in zip(idx, Tr):
+                T_all[r * len(Es_all) + i] = t
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if prec == rgf.RGF_FP64 else "f32x2", "data": "synthetic",
-               "config": {"workload": args.workload, "N": N, "M": 2 * N, "L": L, "energies": int(n),
+               "config": {"workload": args.workload, "N": N, "M": 2 * N, "L": L,
+                          "energies": int(len(Es_all)), "chains_per_rank": int(n),
                           "chains_ok": int(ok.sum()), "W_eV": w["W"], "eta_eV": 1e-8,
                           "precision": args.precision, "l2": "flushed (256 MB write) between steps",
-                          "parallelism": f"chains x{world} (one disorder realisation per rank)"},
+                          "parallelism": f"chains sharded over {world} rank(s) (LPT), one disorder "
+                                         "realisation per rank"},
                "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                           "reasons": clocks["reasons"]},
-               "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roof,
+               "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roof,
                "cpu_baseline": cpu, "parity": parity,
+               "T_gathered_finite": int(np.isfinite(T_all).sum()),
                "status_counts": {rgf.STATUS_NAMES[s]: int((status == s).sum()) for s in set(status.tolist())}}
         print(json.dumps(out), flush=True)
     if dist:

@@ -48,10 +48,13 @@ extern "C" {
 
 typedef enum {
     RGF_OK = 0,
-    RGF_EINVAL = 1,      /* bad argument (sizes, NULL pointer, unknown enum)          */
+    RGF_EINVAL = 1,      /* bad argument (sizes, NULL pointer, unknown enum); per chain:
+                            a non-finite energy                                       */
     RGF_ENOMEM = 2,      /* device or host allocation failed                          */
     RGF_ECUDA = 3,       /* a CUDA runtime call failed                                */
-    RGF_ENOCONV = 4,     /* lead decimation hit its iteration cap or went non-finite   */
+    RGF_ENOCONV = 4,     /* lead decimation hit its iteration cap, went non-finite, or
+                            missed the fixed point of the surface Dyson equation by
+                            more than the residual tolerance (rgf_set_lead_controls)  */
     RGF_ESINGULAR = 5,   /* a zero pivot, or a pivot below 64 u max|A| (u the unit
                             roundoff of the working precision), in a slice inverse     */
     RGF_ENONFINITE = 6,  /* NaN or Inf in a slice Green's function or in T            */
@@ -122,7 +125,11 @@ void rgf_free_ribbon(rgf_ribbon* rib);
  *   side 0: Sigma_L = H01^T g_s H01 on the first device cell (left lead);
  *   side 1: Sigma_R = H01 g_s H01^T on the last device cell (right lead);
  * with z = E + i*eta and the decimation stopped when the largest entry of the
- * effective couplings is below 1e-14 eV (cap 200 iterations).
+ * effective couplings is below 1e-14 eV (cap 200 iterations by default).  The
+ * pristine lead separates into transverse modes, and the decimation runs per
+ * mode; each mode's surface Green's function g must then satisfy the surface
+ * Dyson equation g = 1/(z - t^2/(z - tau^2 g)) to a relative residual of 1e-10
+ * (by default; see rgf_set_lead_controls), else the energy fails.
  * sigma: host [nE][2N][2N] complex, interleaved (re, im) binary64, row-major
  *        (caller-owned, 8*nE*(2N)^2 doubles).
  * iters: host [nE] or NULL: iterations used, or -1 where decimation failed.
@@ -136,6 +143,17 @@ rgf_status rgf_lead_selfenergy(int N, double t, const double* E, int nE, double 
  * is ribbon rib[c] at energy E[c] (several chains may share a ribbon).
  * eta_device is the broadening inside the scattering region, eta_lead the one
  * of the lead decimation.
+ *
+ * Method: the recursion of Eqs. 4-5 over the four atom columns of each unit
+ * cell, run as two halves at the same time -- from the left lead up to the
+ * middle of the ribbon and from the right lead down to it -- and joined by one
+ * Dyson step (Eq. 3) across the middle bond; T = Tr[Gamma_L G_1L Gamma_R
+ * G_1L^dagger] (Eq. 2) evaluated in the leads' transverse-mode bases.  The
+ * lead-attached column at each end is formed and inverted in binary64 in the
+ * mode basis of its lead, where the lead self-energy is diagonal, so that the
+ * order-1/eta self-energies of the surface-state modes near E = 0 do not
+ * swamp the order-1 terms (see rgf_lead_selfenergy); the join and the trace
+ * are binary64; `precision` sets the arithmetic of the column recursion.
  *   rib:   host array of nchains ribbon pointers.
  *   E:     host [nchains] energies (eV).
  *   T:     host [nchains] output.
@@ -149,7 +167,8 @@ rgf_status rgf_conductance(const rgf_ribbon* const* rib, const double* E, int nc
 /* Same with device buffers and a caller stream (E_dev, T_dev, status_dev on
  * the device; status_dev may be NULL).  Asynchronous: returns after launch;
  * results are valid once `stream` has passed the call.  Launch-time errors are
- * returned; per-chain failures appear in status_dev. */
+ * returned; per-chain failures appear in status_dev (a non-finite energy as
+ * RGF_EINVAL). */
 rgf_status rgf_conductance_dev(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
                                double eta_device, double eta_lead, int precision,
                                void* stream, double* T_dev, int32_t* status_dev);
@@ -163,7 +182,11 @@ rgf_status rgf_conductance_dev(const rgf_ribbon* const* rib, const double* E_dev
  * unit cells and recomputed between checkpoints; ckpt_stride <= 0 picks
  * ~sqrt(L).  Device workspace per chain: (14 + 2 ceil(4L / (4 s)) +
  * 2 (4 s + 1)) ceil(N/2)^2 complex values (s the stride), 16 bytes each.
- * T is the value rgf_conductance returns for the same chain, bit for bit.
+ * T comes from this sweep's own left-to-right recursion with the lead
+ * self-energies in the site basis; it agrees with rgf_conductance to the
+ * working precision (not bit for bit), except near E = 0, where only
+ * rgf_conductance treats the surface-state modes of the leads in their mode
+ * basis.
  *   dT_deps: host [nchains][L*2N] binary64 (row-major per chain, orbital
  *            order of rgf_ribbon_desc); 0 on removed atoms.
  * Other arguments and errors as rgf_conductance.
@@ -172,6 +195,43 @@ rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, i
                                 double eta_device, double eta_lead, int precision,
                                 int ckpt_stride, double* T, double* dT_deps,
                                 int32_t* chain_status);
+
+/*
+ * Same as rgf_conductance_grad with device buffers and a caller stream
+ * (asynchronous: results are valid once `stream` has passed the call).
+ * E_dev [nchains], T_dev [nchains], status_dev [nchains] (or NULL) on the device.
+ *   weights_dev NULL:  dT_dev [nchains][L*2N] (device), per chain, packed in
+ *                      chain order (chain c at the sum of the sizes before it);
+ *   weights_dev [nchains] (device): dT_dev [L*2N] = sum_c weights[c] dT_c/d eps,
+ *                      the vector-Jacobian product of the chains' T (every
+ *                      ribbon must have the same N and L; summed over chains in
+ *                      order, deterministic).  A failed chain contributes 0.
+ * Launch-time errors are returned; per-chain failures appear in status_dev.
+ */
+rgf_status rgf_conductance_grad_dev(const rgf_ribbon* const* rib, const double* E_dev,
+                                    int nchains, double eta_device, double eta_lead,
+                                    int precision, int ckpt_stride, const double* weights_dev,
+                                    void* stream, double* T_dev, double* dT_dev,
+                                    int32_t* status_dev);
+
+/*
+ * Local density of states rho_i(E) = -Im G_ii(E) / pi (states per eV per
+ * orbital) at every site of the scattering region.  The paper notes that the
+ * Green's function of Eq. 1 gives every quantity of interest, the charge
+ * density among them (text after Eq. 1); rho is that density's integrand over
+ * energy.  The diagonal block G_kk of each column k comes from the Dyson
+ * equation (Eq. 3) with the bonds on both sides of column k cut, joining the
+ * recursion of Eqs. 4-5 run from the left lead with the same recursion run
+ * from the right lead (checkpointed every ckpt_stride unit cells, as in
+ * rgf_conductance_grad, with the same workspace).
+ *   rho: host [nchains][L*2N] binary64 (row-major per chain, orbital order of
+ *        rgf_ribbon_desc); 0 on removed atoms.
+ *   T:   host [nchains], as rgf_conductance_grad returns it.
+ * Other arguments and errors as rgf_conductance_grad.
+ */
+rgf_status rgf_ldos(const rgf_ribbon* const* rib, const double* E, int nchains,
+                    double eta_device, double eta_lead, int precision, int ckpt_stride,
+                    double* T, double* rho, int32_t* chain_status);
 
 /*
  * Complex matrix product C = A B on the tcgen05 tensor cores: the dense
@@ -215,24 +275,32 @@ rgf_status rgf_zgemm_tc_selftest_timeout(void);
  * cudaMalloc, a plugin whose host only hands it pre-allocated buffers, or a
  * loop that must not trigger the implicit device synchronisation of
  * cudaMalloc / cudaFree.  This call performs no cudaMalloc, cudaFree or other
- * allocating call: its scratch (chain descriptors, lead workspace and output,
- * sweep workspace) lives in one fixed 64 MiB device array inside the library,
- * which every GPU that loads the library holds until the process exits.
+ * allocating call and copies nothing from host memory: its scratch (chain and
+ * lead descriptors, lead workspace and output, sweep workspace) lives in one
+ * fixed 64 MiB device array inside the library, which every GPU that loads
+ * the library's device code holds until the process exits.  CUDA loads device
+ * code lazily by default, so the array is created by the first call on each
+ * device (or at context creation when CUDA_MODULE_LOADING=EAGER is set): a
+ * caller that reserves the remaining device memory for itself should make one
+ * call first.
  *
  * One ribbon of N dimer lines and L cells, given as device arrays
  * onsite_dev [L][2N] (binary64) and removed_dev [L][2N] (uint8, or NULL),
  * evaluated at nE energies E_dev [nE] (device).  Outputs on the device:
- * T_dev [nE], status_dev [nE] (int32, or NULL), as rgf_conductance_dev.
- * Asynchronous on `stream`; results are valid once the stream has passed the
- * call.  Returns RGF_EINVAL, with a message naming the limit, when the scratch
- * the call needs exceeds 64 MiB (about 25 energies at N = 245, more at smaller
- * N); split the energies over several calls then.
+ * T_dev [nE], status_dev [nE] (int32, or NULL), as rgf_conductance_dev, in any
+ * precision (RGF_FP64, RGF_MIXED, RGF_MIXED_TC).  Asynchronous on `stream`;
+ * results are valid once the stream has passed the call.  Returns RGF_EINVAL,
+ * with a message naming the limit, when the scratch the call needs exceeds
+ * 64 MiB (21 energies at N = 245, more at smaller N); split the energies over
+ * several calls then.
  *
  * The array is shared by all calls and keeps the last call's contents; two
  * calls whose GPU work overlaps (different streams, or a second call before
  * the first has finished) race on it.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.
+ * first call before any stream capture.  After cudaDeviceReset of a device the
+ * cached address is stale: do not use this entry point on that device again in
+ * the same process.
  */
 rgf_status rgf_conductance_noalloc(int N, int L, double t, const double* onsite_dev,
                                    const uint8_t* removed_dev, const double* E_dev, int nE,
@@ -250,6 +318,23 @@ rgf_status rgf_conductance_noalloc(int N, int L, double t, const double* onsite_
  */
 rgf_status rgf_profile_enable(int on);
 rgf_status rgf_profile_read(double* ms_lead, double* ms_sweep);
+
+/* The phases of the last profiled rgf_conductance* call, in milliseconds:
+ * ms[0] lead decimation, ms[1] end-column preparation, ms[2] half sweeps (the
+ * gradient sweep for rgf_conductance_grad), ms[3] join and trace.
+ * rgf_profile_read's ms_sweep is ms[1] + ms[2] + ms[3].  ms: host [4]. */
+rgf_status rgf_profile_read_phases(double* ms);
+
+/*
+ * Decimation controls (no counterpart in the paper; process-wide, for
+ * diagnostics and host-side fault injection): the iteration cap of every mode
+ * (default 200) and the relative residual tolerance of the surface Dyson
+ * equation (default 1e-10) that rgf_lead_selfenergy and every rgf_conductance*
+ * call apply.  A cap of 1, or a tolerance of 0, makes the energies fail with
+ * RGF_ENOCONV without any device fault.  Errors: RGF_EINVAL (max_iter outside
+ * [1, 100000], residual_tol negative or NaN).
+ */
+rgf_status rgf_set_lead_controls(int max_iter, double residual_tol);
 
 const char* rgf_status_str(int status);
 const char* rgf_last_error(void);

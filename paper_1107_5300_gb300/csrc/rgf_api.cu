@@ -5,9 +5,10 @@
 // lead self-energies -> recursion on the device -> conductance):
 //   1. one lead problem per chain (pristine ribbon of the chain's width at the
 //      chain's energy), decimated on the device (rgf_lead.cu);
-//   2. one thread block per chain runs the column-sliced recursion and the
-//      trace (rgf_sweep.cu); chains are launched longest first so that the
-//      hardware block scheduler balances uneven chains across SMs;
+//   2. the column-sliced recursion as two halves per chain, one from each
+//      lead, joined by one Dyson step, and the trace (rgf_sweep.cu: end-column
+//      preparation, half sweeps, merge); chains are launched longest first so
+//      that the hardware block scheduler balances uneven chains across SMs;
 //   3. T and the per-chain status words return to the host.
 // Only on-site energies / masks (at ribbon build), energies and T cross the
 // host-device boundary.
@@ -36,9 +37,12 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Events around the phases of the last call: [0] lead decimation [1]
+// end-column preparation [2] half sweeps (or the gradient sweep) [3] merge [4].
+constexpr int kProfEvents = 5;
 struct Profile {
     bool on = false, recorded = false;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[kProfEvents] = {};
 };
 Profile g_prof;
 
@@ -163,14 +167,14 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl, bool g
     return RGF_OK;
 }
 
-__global__ void fill_energy(rgf::ChainDev* chains, rgf::LeadDev* leads, const double* E, int n,
-                            int* bad) {
+// Energies into the descriptors.  A non-finite energy reaches the lead
+// kernel, which reports its chain as RGF_EINVAL.
+__global__ void fill_energy(rgf::ChainDev* chains, rgf::LeadDev* leads, const double* E, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         double e = E[i];
         chains[i].E = e;
         leads[i].E = e;
-        if (!isfinite(e)) atomicExch(bad, 1);
     }
 }
 
@@ -180,7 +184,7 @@ __global__ void fill_energy(rgf::ChainDev* chains, rgf::LeadDev* leads, const do
 rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
                     double eta_device, double eta_lead, int precision, cudaStream_t st,
                     double* T_dev, int32_t* status_dev, double* dT_dev = nullptr,
-                    int ckpt_stride = 0) {
+                    int ckpt_stride = 0, int out_mode = rgf::OUT_GRAD) {
     if (nchains < 0) return fail(RGF_EINVAL, "nchains < 0");
     if (nchains == 0) return RGF_OK;
     if (!rib || !E_dev || !T_dev) return fail(RGF_EINVAL, "NULL argument");
@@ -203,7 +207,7 @@ rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchai
     std::memcpy(hdr.data() + nC + nL, pl.order.data(), nO);
     std::memcpy(hdr.data() + nC + nL + nO, pl.seg_cols.data(), nO);
 
-    DevBuf dhdr, dws, dlws, dlout, dlst, dbad;
+    DevBuf dhdr, dws, dlws, dlout, dlst;
     RGF_CUDA(dhdr.alloc(hdr.size(), st), "cudaMallocAsync(descriptors)");
     cudaError_t ae = dws.alloc(pl.ws_elems * 16, st);
     if (ae == cudaErrorMemoryAllocation) return fail(RGF_ENOMEM, "workspace allocation failed");
@@ -211,17 +215,16 @@ rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchai
     RGF_CUDA(dlws.alloc(pl.lead_ws_elems * 16, st), "cudaMallocAsync(lead workspace)");
     RGF_CUDA(dlout.alloc(pl.lead_out_elems * 16, st), "cudaMallocAsync(lead output)");
     RGF_CUDA(dlst.alloc(2 * sizeof(int) * nchains, st), "cudaMallocAsync(lead status)");
-    RGF_CUDA(dbad.alloc(sizeof(int), st), "cudaMallocAsync(flag)");
     RGF_CUDA(cudaMemcpyAsync(dhdr.p, hdr.data(), hdr.size(), cudaMemcpyHostToDevice, st),
              "cudaMemcpyAsync(descriptors)");
-    RGF_CUDA(cudaMemsetAsync(dbad.p, 0, sizeof(int), st), "cudaMemsetAsync");
     if (grad) RGF_CUDA(cudaMemsetAsync(dT_dev, 0, pl.grad_elems * sizeof(double), st), "cudaMemsetAsync");
+    double* dgrad = (out_mode & rgf::OUT_GRAD) ? dT_dev : nullptr;
+    double* drho = (out_mode & rgf::OUT_LDOS) ? dT_dev : nullptr;
     auto* dchains = (rgf::ChainDev*)dhdr.p;
     auto* dleads = (rgf::LeadDev*)((unsigned char*)dhdr.p + nC);
     auto* dorder = (int*)((unsigned char*)dhdr.p + nC + nL);
     auto* dseg = (int*)((unsigned char*)dhdr.p + nC + nL + nO);
-    fill_energy<<<(nchains + 255) / 256, 256, 0, st>>>(dchains, dleads, E_dev, nchains,
-                                                       (int*)dbad.p);
+    fill_energy<<<(nchains + 255) / 256, 256, 0, st>>>(dchains, dleads, E_dev, nchains);
     RGF_CUDA(cudaGetLastError(), "fill_energy launch");
     RGF_CUDA(prof_record(0, st), "cudaEventRecord");
     RGF_CUDA(rgf::launch_lead(dleads, nchains, pl.Kmax, eta_lead, dlws.p, dlout.p, (int*)dlst.p,
@@ -229,25 +232,46 @@ rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchai
              "lead decimation launch");
     RGF_CUDA(prof_record(1, st), "cudaEventRecord");
     if (grad) {
+        RGF_CUDA(prof_record(2, st), "cudaEventRecord");
         RGF_CUDA(rgf::launch_grad(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
-                                  dlout.p, (int*)dlst.p, dleads, dws.p, dseg, T_dev, dT_dev,
-                                  status_dev, st),
+                                  dlout.p, (int*)dlst.p, dleads, dws.p, dseg, T_dev, dgrad, drho,
+                                  out_mode, status_dev, st),
                  "gradient sweep launch");
+        RGF_CUDA(prof_record(3, st), "cudaEventRecord");
     } else {
-        RGF_CUDA(rgf::launch_sweep(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
+        RGF_CUDA(rgf::launch_prep(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
+                                  dlout.p, (int*)dlst.p, dleads, dws.p, st),
+                 "end-column preparation launch");
+        RGF_CUDA(prof_record(2, st), "cudaEventRecord");
+        RGF_CUDA(rgf::launch_half(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
+                                  dlout.p, (int*)dlst.p, dleads, dws.p, st),
+                 "half sweep launch");
+        RGF_CUDA(prof_record(3, st), "cudaEventRecord");
+        RGF_CUDA(rgf::launch_merge(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
                                    dlout.p, (int*)dlst.p, dleads, dws.p, T_dev, status_dev, st),
-                 "sweep launch");
+                 "merge launch");
     }
-    RGF_CUDA(prof_record(2, st), "cudaEventRecord");
+    RGF_CUDA(prof_record(4, st), "cudaEventRecord");
     if (g_prof.on) g_prof.recorded = true;
     return RGF_OK;
+}
+
+// out[i] = sum_c w[c] g[c * n + i]: the weighted sum over chains of per-chain
+// gradients (one thread per site, chains summed in order: deterministic).
+__global__ void weighted_chain_sum(const double* __restrict__ g, const double* __restrict__ w,
+                                   int nchains, size_t n, double* __restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int c = 0; c < nchains; ++c) acc = fma(w[c], g[(size_t)c * n + i], acc);
+    out[i] = acc;
 }
 
 // Host-buffer front end of run_path: copies E in and T (and dT) out on the
 // legacy default stream, synchronises, returns the first per-chain failure.
 rgf_status run_host(const rgf_ribbon* const* rib, const double* E, int nchains, double eta_device,
                     double eta_lead, int precision, double* T, int32_t* chain_status,
-                    double* dT = nullptr, int ckpt_stride = 0) {
+                    double* dT = nullptr, int ckpt_stride = 0, int out_mode = rgf::OUT_GRAD) {
     if (nchains < 0 || (nchains > 0 && (!rib || !E || !T)))
         return fail(RGF_EINVAL, "NULL argument or nchains < 0");
     if (nchains == 0) return RGF_OK;
@@ -269,7 +293,8 @@ rgf_status run_host(const rgf_ribbon* const* rib, const double* E, int nchains, 
         if (dT) RGF_CUDA(dG.alloc(ng * sizeof(double), st), "cudaMallocAsync");
         RGF_CUDA(cudaMemcpyAsync(dE.p, E, nchains * sizeof(double), cudaMemcpyHostToDevice, st), "H2D");
         rgf_status s = run_path(rib, (const double*)dE.p, nchains, eta_device, eta_lead, precision,
-                                st, (double*)dTt.p, (int32_t*)dS.p, (double*)dG.p, ckpt_stride);
+                                st, (double*)dTt.p, (int32_t*)dS.p, (double*)dG.p, ckpt_stride,
+                                out_mode);
         if (s != RGF_OK) return s;
         RGF_CUDA(cudaMemcpyAsync(hT.data(), dTt.p, nchains * sizeof(double), cudaMemcpyDeviceToHost, st), "D2H");
         RGF_CUDA(cudaMemcpyAsync(hs.data(), dS.p, nchains * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "D2H");
@@ -309,14 +334,31 @@ rgf_status rgf_profile_enable(int on) {
     return RGF_OK;
 }
 
-rgf_status rgf_profile_read(double* ms_lead, double* ms_sweep) {
+rgf_status rgf_profile_read_phases(double* ms) {
+    if (!ms) return fail(RGF_EINVAL, "ms is NULL");
     if (!g_prof.on || !g_prof.recorded) return fail(RGF_EINVAL, "no profiled call recorded");
-    RGF_CUDA(cudaEventSynchronize(g_prof.ev[2]), "cudaEventSynchronize");
-    float a = 0.f, b = 0.f;
-    RGF_CUDA(cudaEventElapsedTime(&a, g_prof.ev[0], g_prof.ev[1]), "cudaEventElapsedTime");
-    RGF_CUDA(cudaEventElapsedTime(&b, g_prof.ev[1], g_prof.ev[2]), "cudaEventElapsedTime");
-    if (ms_lead) *ms_lead = a;
-    if (ms_sweep) *ms_sweep = b;
+    RGF_CUDA(cudaEventSynchronize(g_prof.ev[kProfEvents - 1]), "cudaEventSynchronize");
+    for (int i = 0; i + 1 < kProfEvents; ++i) {
+        float a = 0.f;
+        RGF_CUDA(cudaEventElapsedTime(&a, g_prof.ev[i], g_prof.ev[i + 1]), "cudaEventElapsedTime");
+        ms[i] = a;
+    }
+    return RGF_OK;
+}
+
+rgf_status rgf_profile_read(double* ms_lead, double* ms_sweep) {
+    double ms[kProfEvents - 1];
+    rgf_status s = rgf_profile_read_phases(ms);
+    if (s != RGF_OK) return s;
+    if (ms_lead) *ms_lead = ms[0];
+    if (ms_sweep) *ms_sweep = ms[1] + ms[2] + ms[3];
+    return RGF_OK;
+}
+
+rgf_status rgf_set_lead_controls(int max_iter, double residual_tol) {
+    if (max_iter < 1 || max_iter > 100000 || !(residual_tol >= 0.0))
+        return fail(RGF_EINVAL, "max_iter must be in [1, 100000] and residual_tol >= 0");
+    rgf::set_lead_controls(rgf::LeadControls{max_iter, residual_tol});
     return RGF_OK;
 }
 
@@ -513,6 +555,43 @@ rgf_status rgf_conductance(const rgf_ribbon* const* rib, const double* E, int nc
                            double eta_device, double eta_lead, int precision, double* T,
                            int32_t* chain_status) {
     return run_host(rib, E, nchains, eta_device, eta_lead, precision, T, chain_status);
+}
+
+rgf_status rgf_conductance_grad_dev(const rgf_ribbon* const* rib, const double* E_dev,
+                                    int nchains, double eta_device, double eta_lead,
+                                    int precision, int ckpt_stride, const double* weights_dev,
+                                    void* stream, double* T_dev, double* dT_dev,
+                                    int32_t* status_dev) {
+    if (nchains < 0) return fail(RGF_EINVAL, "nchains < 0");
+    if (nchains == 0) return RGF_OK;
+    if (!rib || !dT_dev) return fail(RGF_EINVAL, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!weights_dev)
+        return run_path(rib, E_dev, nchains, eta_device, eta_lead, precision, st, T_dev,
+                        status_dev, dT_dev, ckpt_stride);
+    for (int c = 0; c < nchains; ++c) {
+        if (!rib[c]) return fail(RGF_EINVAL, "NULL ribbon");
+        if (rib[c]->N != rib[0]->N || rib[c]->L != rib[0]->L)
+            return fail(RGF_EINVAL, "weights_dev needs ribbons of one size (N, L)");
+    }
+    const size_t n = (size_t)rib[0]->L * 2 * rib[0]->N;
+    DevBuf per;
+    RGF_CUDA(per.alloc((size_t)nchains * n * sizeof(double), st), "cudaMallocAsync(gradients)");
+    rgf_status s = run_path(rib, E_dev, nchains, eta_device, eta_lead, precision, st, T_dev,
+                            status_dev, (double*)per.p, ckpt_stride);
+    if (s != RGF_OK) return s;
+    weighted_chain_sum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double*)per.p, weights_dev,
+                                                                    nchains, n, dT_dev);
+    RGF_CUDA(cudaGetLastError(), "weighted_chain_sum launch");
+    return RGF_OK;
+}
+
+rgf_status rgf_ldos(const rgf_ribbon* const* rib, const double* E, int nchains, double eta_device,
+                    double eta_lead, int precision, int ckpt_stride, double* T, double* rho,
+                    int32_t* chain_status) {
+    if (nchains > 0 && !rho) return fail(RGF_EINVAL, "rho is NULL");
+    return run_host(rib, E, nchains, eta_device, eta_lead, precision, T, chain_status, rho,
+                    ckpt_stride, rgf::OUT_LDOS);
 }
 
 rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, int nchains,

@@ -199,13 +199,16 @@ template <> struct Unit<df32> { static constexpr double u = 3.552713678800501e-1
 
 // Number of propagating channels of a pristine armchair ribbon of N lines at
 // energy E: modes p with |t| |1 + 2 c_p| <= |E| < |t| (1 + 2 |c_p|),
-// c_p = cos(p pi / (N + 1)) (the band edges of the transverse modes).
+// c_p = cos(p pi / (N + 1)) (the band edges of the transverse modes).  A lower
+// edge within 1e-12 |t| of |E| counts: the metallic mode of N = 3q + 2 has its
+// edge at exactly 0 (a linear crossing that carries a channel at E = 0), which
+// the rounding of c_p puts a few 1e-16 eV to either side.
 __device__ __forceinline__ int channels(int N, double t, double E) {
     int n = 0;
     const double at = fabs(t), ae = fabs(E);
     for (int p = 1; p <= N; ++p) {
         double c = cospi((double)p / (double)(N + 1));
-        if (at * fabs(1.0 + 2.0 * c) <= ae && ae < at * (1.0 + 2.0 * fabs(c))) ++n;
+        if (at * fabs(1.0 + 2.0 * c) <= ae + 1e-12 * at && ae < at * (1.0 + 2.0 * fabs(c))) ++n;
     }
     return n;
 }

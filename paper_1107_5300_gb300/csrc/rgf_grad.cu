@@ -27,11 +27,20 @@
 // forward sweep.  With TC (precision RGF_MIXED_TC) the dense
 // products run on the tcgen05 tensor cores (rgf_tc.cuh); the block holds the
 // SM's TMEM for the whole launch.
+//
+// The same pass yields the local density of states rho_i(E) = -Im (G_kk)_ii / pi
+// (the paper notes that the Green's function of Eq. 1 gives the charge density;
+// rho is its integrand over energy): `out_mode` selects the gradient
+// (OUT_GRAD), rho (OUT_LDOS), or both into two arrays; with rho alone the
+// products that only the gradient needs (G_1k, G_kL and the trace with M) are
+// skipped.
 #include "rgf_steps.cuh"
 
 namespace rgf {
 
 namespace {
+
+constexpr double kInvPi = 0.318309886183790671537767526745;   // 1 / pi
 
 template <class R>
 __device__ void copy_blk(cx<R>* D, const cx<R>* S, size_t n) {
@@ -175,7 +184,8 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
             int Kmax, double eta_d, const zd* __restrict__ leadout,
             const int* __restrict__ lead_status, const LeadDev* __restrict__ leads,
             cx<R>* __restrict__ ws, const int* __restrict__ seg_cols, double* __restrict__ Tout,
-            double* __restrict__ dT, int32_t* __restrict__ status) {
+            double* __restrict__ dT, double* __restrict__ rho, int out_mode,
+            int32_t* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     SweepSmem<R> s = carve<R>(smem_raw, Kmax, TC);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -198,7 +208,9 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     cx<R> *GL = base + 10 * B, *GR = base + 11 * B, *gr = base + 12 * B, *Qr = base + 13 * B;
     cx<R>* ckpt = base + 14 * B;                       // (gr, Qr) at column (j + 1) Sc
     cx<R>* seg = ckpt + (size_t)nseg * 2 * B;          // (Sc + 1) x (gr, Qr)
-    double* grad = dT + ch.grad_off;
+    const bool want_grad = (out_mode & OUT_GRAD) != 0, want_ldos = (out_mode & OUT_LDOS) != 0;
+    double* grad = want_grad ? dT + ch.grad_off : nullptr;
+    double* ldos = want_ldos ? rho + ch.grad_off : nullptr;
     tc::State tst;
     if constexpr (TC) tc_attach<R>(Kmax, s, tst);
 
@@ -241,15 +253,17 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     }
 
     // M = Gamma_R G_1L^dagger Gamma_L  (KR x KL)
-    for (size_t e = threadIdx.x; e < B; e += NT) {
+    for (size_t e = threadIdx.x; e < B && want_grad; e += NT) {
         GL[e] = ld_z<R>(c.GamL + e);                              // KL x KL, ld KL
         if (e < (size_t)KR * KR) GR[e] = ld_z<R>(c.GamR + e);     // KR x KR, ld KR
         const int b = (int)(e / KL), a = (int)(e % KL);
         if (b < KR) Y[e] = cconj(Qr[(size_t)a * KL + b]);         // Y[b][a] = conj(G_1L[a][b])
     }
     __syncthreads();
-    dense_product<R, false>(KR, KL, KR, GR, KR, Y, KL, U, KL, s);
-    dense_product<R, false>(KR, KL, KL, U, KL, GL, KL, Mb, KL, s);
+    if (want_grad) {
+        dense_product<R, false>(KR, KL, KR, GR, KR, Y, KL, U, KL, s);
+        dense_product<R, false>(KR, KL, KL, U, KL, GL, KL, Mb, KL, s);
+    }
 
     // Left-to-right pass, segment by segment.
     for (int j = 0; j < nseg; ++j) {
@@ -277,35 +291,44 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
         for (int k = k0; k < k1; ++k) {
             const cx<R>* sn = seg + (size_t)(k - k0 + 1) * 2 * B;   // (gr, Qr)_{k+1}
             const int ct = k & 3, K = col_size(c, k);
+            (void)ct;
             const bool last = k == ncol - 1;
             load_cols(c, k, s);
             // G_kk
             flag |= build_invert<R>(c, k, true, gl, true, sn, X, Gkk, s);
-            // G_1k = Pl_{k-1} W_k G_kk  (KL x K)
-            const cx<R>* g1 = Gkk;
-            if (k > 0) {
-                stencil_left<R>(c, k, Pl, Y, s);
-                dense_product<R, false>(KL, K, K, Y, KL, Gkk, KL, G1k, KL, s);
-                g1 = G1k;
-            }
-            // G_kL = G_kk W_{k+1} Qr_{k+1}  (K x KR)
-            const cx<R>* gL = Gkk;
-            if (!last) {
-                stencil_right<R>(c, k, sn + B, Z, s);
-                dense_product<R, false>(K, KR, K, Gkk, KL, Z, KL, GkL, KL, s);
-                gL = GkL;
-            }
-            // dT/d eps_i = 2 Re sum_b (G_kL M)[i][b] G_1k[b][i]
-            dense_product<R, false>(K, KL, KR, gL, KL, Mb, KL, U, KL, s);
             const int n = k >> 2;
-            for (int i = warp; i < K; i += NWARP) {
-                double acc = 0.0;
-                for (int b = lane; b < KL; b += 32) {
-                    const zd u = to_z(U[(size_t)i * KL + b]), g = to_z(g1[(size_t)b * KL + i]);
-                    acc += u.re * g.re - u.im * g.im;
+            if (want_ldos) {
+                // rho_i = -Im (G_kk)_ii / pi; 0 on removed atoms
+                for (int i = threadIdx.x; i < K; i += NT)
+                    ldos[(size_t)n * c.M + 4 * i + ct] =
+                        s.kc[i] ? -to_z(Gkk[(size_t)i * KL + i]).im * kInvPi : 0.0;
+            }
+            if (k > 0) stencil_left<R>(c, k, Pl, Y, s);     // Y = Pl_{k-1} W_k
+            if (want_grad) {
+                // G_1k = Pl_{k-1} W_k G_kk  (KL x K)
+                const cx<R>* g1 = Gkk;
+                if (k > 0) {
+                    dense_product<R, false>(KL, K, K, Y, KL, Gkk, KL, G1k, KL, s);
+                    g1 = G1k;
                 }
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0 && s.kc[i]) grad[(size_t)n * c.M + 4 * i + ct] = 2.0 * acc;
+                // G_kL = G_kk W_{k+1} Qr_{k+1}  (K x KR)
+                const cx<R>* gL = Gkk;
+                if (!last) {
+                    stencil_right<R>(c, k, sn + B, Z, s);
+                    dense_product<R, false>(K, KR, K, Gkk, KL, Z, KL, GkL, KL, s);
+                    gL = GkL;
+                }
+                // dT/d eps_i = 2 Re sum_b (G_kL M)[i][b] G_1k[b][i]
+                dense_product<R, false>(K, KL, KR, gL, KL, Mb, KL, U, KL, s);
+                for (int i = warp; i < K; i += NWARP) {
+                    double acc = 0.0;
+                    for (int b = lane; b < KL; b += 32) {
+                        const zd u = to_z(U[(size_t)i * KL + b]), g = to_z(g1[(size_t)b * KL + i]);
+                        acc += u.re * g.re - u.im * g.im;
+                    }
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0 && s.kc[i]) grad[(size_t)n * c.M + 4 * i + ct] = 2.0 * acc;
+                }
             }
             // gl_k and Pl_k (the forward recursion)
             flag |= build_invert<R>(c, k, true, gl, last, nullptr, X, gl, s);
@@ -336,7 +359,7 @@ size_t grad_ws_elems(int N, int L, int seg_cols) {
 cudaError_t launch_grad(int precision, const ChainDev* chains, const int* order, int nchains,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
                         const LeadDev* leads, void* ws, const int* seg_cols, double* T, double* dT,
-                        int32_t* status, cudaStream_t st) {
+                        double* rho, int out_mode, int32_t* status, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
     const bool tc = precision == 2;
     const size_t smem = sweep_smem_bytes(Kmax, tc);
@@ -347,21 +370,21 @@ cudaError_t launch_grad(int precision, const ChainDev* chains, const int* order,
         if (e != cudaSuccess) return e;
         grad_kernel<double, false><<<nchains, NT, smem, st>>>(
             chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status, leads,
-            (zd*)ws, seg_cols, T, dT, status);
+            (zd*)ws, seg_cols, T, dT, rho, out_mode, status);
     } else if (tc) {
         e = cudaFuncSetAttribute(grad_kernel<df32, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         grad_kernel<df32, true><<<nchains, NT, smem, st>>>(
             chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status, leads,
-            (zf*)ws, seg_cols, T, dT, status);
+            (zf*)ws, seg_cols, T, dT, rho, out_mode, status);
     } else {
         e = cudaFuncSetAttribute(grad_kernel<df32, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         grad_kernel<df32, false><<<nchains, NT, smem, st>>>(
             chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status, leads,
-            (zf*)ws, seg_cols, T, dT, status);
+            (zf*)ws, seg_cols, T, dT, rho, out_mode, status);
     }
     return cudaGetLastError();
 }

@@ -19,8 +19,12 @@ __host__ __device__ inline int col_KR(int N) { return N / 2; }
 struct LeadDev {
     int N;
     double t, E;
-    size_t off;      // offset (in 16-byte complex elements) of this problem's
+    size_t off;      // offset (in 16-byte complex elements) of this problem's output:
                      // Sigma_L [KL*KL], Sigma_R [KR*KR], Gamma_L [KL*KL], Gamma_R [KR*KR]
+                     // (site basis of the lead-attached columns), then U_even [KL*KL],
+                     // U_odd [KR*KR] (the transverse-mode vectors, real parts; row = atom,
+                     // column = mode) and w [KL] (the mode self-energies tau_p^2 g_p), so
+                     // that Sigma_L = U_even diag(w) U_even^T, Sigma_R = U_odd diag(w) U_odd^T
     size_t ws_off;   // offset (16-byte elements) of its decimation workspace
 };
 
@@ -36,24 +40,35 @@ struct ChainDev {
 };
 
 // Number of 16-byte elements of the decimation workspace of one lead problem.
-inline size_t lead_ws_elems(int N) {
+__host__ __device__ inline size_t lead_ws_elems(int N) {
     size_t KL = (size_t)col_KL(N);
     return KL * KL;   // the KL x KL (binary64) transverse mode basis, with room to spare
 }
-inline size_t lead_out_elems(int N) {
+__host__ __device__ inline size_t lead_out_elems(int N) {
     size_t KL = (size_t)col_KL(N), KR = (size_t)col_KR(N);
-    return 2 * (KL * KL + KR * KR);
+    return 3 * (KL * KL + KR * KR) + KL;
 }
-// Sweep workspace of one chain: X, G0, G1, P, Y (each KL x KL) and one
-// element for the flag handed between the two blocks of a chain.
-inline size_t sweep_ws_elems(int N) {
+// The sweep of one chain runs as two halves, one from each lead (see
+// rgf_sweep.cu).  Workspace of one half: X, G, P (each KL x KL) and one
+// element holding the half's status flags; a chain holds two halves.
+__host__ __device__ inline size_t half_ws_elems(int N) {
     size_t KL = (size_t)col_KL(N);
-    return 5 * KL * KL + 1;
+    return 3 * KL * KL + 1;
 }
+__host__ __device__ inline size_t sweep_ws_elems(int N) { return 2 * half_ws_elems(N); }
 
 // Shared memory of the sweep / lead kernels for a largest column size Kmax
 // (tc: with the tensor-core area of the RGF_MIXED_TC path).
 size_t sweep_smem_bytes(int Kmax, bool tc = false);
+
+// Controls of the decimation (process-wide, set through rgf_set_lead_controls):
+// iteration cap and the tolerance of the fixed-point residual test.
+struct LeadControls {
+    int max_iter;
+    double residual_tol;
+};
+LeadControls lead_controls();
+void set_lead_controls(LeadControls c);
 
 // Kernel launchers (return cudaGetLastError() after the launch).
 // One block per lead problem computes both leads; lead_status / lead_iters
@@ -62,18 +77,34 @@ cudaError_t launch_lead(const LeadDev* leads, int nlead, int Kmax, double eta_le
                         void* ws, void* out, int* lead_status, int* lead_iters,
                         cudaStream_t st);
 
-cudaError_t launch_sweep(int precision, const ChainDev* chains, const int* order, int nchains,
+// The conductance of every chain in three launches on `st`:
+//   launch_prep:  the lead-attached end column of each half in binary64, in the
+//                 leads' transverse-mode basis (2 blocks per chain);
+//   launch_half:  the column recursion of each half (2 blocks per chain);
+//   launch_merge: the two halves joined across the middle bond, and the trace
+//                 (1 block per chain; writes T and status).
+// leadout / lead_status as launch_lead left them; ws: sweep_ws_elems per chain.
+cudaError_t launch_prep(int precision, const ChainDev* chains, const int* order, int nchains,
+                        int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                        const LeadDev* leads, void* ws, cudaStream_t st);
+cudaError_t launch_half(int precision, const ChainDev* chains, const int* order, int nchains,
+                        int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                        const LeadDev* leads, void* ws, cudaStream_t st);
+cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order, int nchains,
                          int Kmax, double eta_device, const void* leadout, const int* lead_status,
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st);
 
-// Gradient sweep: workspace (16-byte elements) of one chain with segments of
-// seg_cols columns, and the launcher (seg_cols: [nchains] on the device; dT:
-// zero-initialised doubles, chain c's block at chains[c].grad_off).
+// Two-sided sweep (rgf_grad.cu): workspace (16-byte elements) of one chain
+// with segments of seg_cols columns, and the launcher (seg_cols: [nchains] on
+// the device).  out_mode: OUT_GRAD writes dT/d eps into dT, OUT_LDOS the local
+// density of states into rho (zero-initialised doubles, chain c's block at
+// chains[c].grad_off; the unused pointer may be null).
+enum : int { OUT_GRAD = 1, OUT_LDOS = 2 };
 size_t grad_ws_elems(int N, int L, int seg_cols);
 cudaError_t launch_grad(int precision, const ChainDev* chains, const int* order, int nchains,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
                         const LeadDev* leads, void* ws, const int* seg_cols, double* T, double* dT,
-                        int32_t* status, cudaStream_t st);
+                        double* rho, int out_mode, int32_t* status, cudaStream_t st);
 
 }  // namespace rgf

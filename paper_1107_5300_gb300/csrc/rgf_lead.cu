@@ -23,7 +23,15 @@
 //     Sigma_R = sum_p tau_p^2 g_p u_p^odd  u_p^odd^T    (on c3 of the last cell)
 // which equal H01^T g_s H01 and H01 g_s H01^T of the full-cell iteration, at
 // O(N) work per iteration instead of O(N^3) and without inverting isolated
-// sub-blocks of the cell.
+// sub-blocks of the cell.  The output also carries the mode vectors and the
+// mode self-energies w_p = tau_p^2 g_p themselves: the sweep works on the
+// lead-attached columns in the mode basis, where Sigma is diagonal (near
+// E = 0 the surface-state modes have |w_p| ~ 1/eta).
+//
+// Checks: a non-finite energy is RGF_EINVAL; a mode that reaches the iteration
+// cap, goes non-finite, or whose g_p misses the fixed point of the surface
+// Dyson equation g = 1/(z - t^2/(z - tau^2 g)) by more than the residual
+// tolerance (relative) is RGF_ENOCONV.
 #include "rgf_device.cuh"
 #include "rgf_internal.h"
 
@@ -32,17 +40,18 @@ namespace rgf {
 namespace {
 
 constexpr double kTol = 1e-14;
-constexpr int kMaxIter = 200;
+
+LeadControls g_controls = {200, 1e-10};
 
 // Mode p (1-based) of an N-line ribbon: surface Green's function and iterations.
-__device__ zd mode_surface(int p, int N, double t, zd z, int& iters, bool& ok) {
+__device__ zd mode_surface(int p, int N, double t, zd z, int max_iter, int& iters, bool& ok) {
     const double tau = 2.0 * t * cospi((double)p / (double)(N + 1));
     zd a = {tau, 0.0};
     zd dA = {0.0, 0.0}, dB = {0.0, 0.0}, sB = {0.0, 0.0};
     const zd tt = {t * t, 0.0};
     ok = false;
     int it;
-    for (it = 1; it <= kMaxIter; ++it) {
+    for (it = 1; it <= max_iter; ++it) {
         zd zA = csub(z, dA), zB = csub(z, dB);
         zd det = csub(cmul(zA, zB), tt);
         double d2 = det.re * det.re + det.im * det.im;
@@ -65,6 +74,16 @@ __device__ zd mode_surface(int p, int N, double t, zd z, int& iters, bool& ok) {
     zd g = cmul(zs, zd{den.re / d2, -den.im / d2});
     if (!cfinite(g)) ok = false;
     return g;
+}
+
+// Relative residual |g - 1/(z - t^2/(z - tau^2 g))| / |g| of the surface Dyson
+// equation of mode chain p (bonds t, tau, t, ... from the surface atom).
+__device__ double mode_residual(zd g, double t, double tau, zd z) {
+    const zd inner = csub(z, cscale(g, tau * tau));
+    const zd t2i = cscale(crecip(inner), t * t);
+    const zd rhs = crecip(csub(z, t2i));
+    const zd d = csub(g, rhs);
+    return sqrt((d.re * d.re + d.im * d.im) / (g.re * g.re + g.im * g.im));
 }
 
 // Normalised restricted mode vectors: U[i][p-1] = phi_p(row of entry i) / norm,
@@ -112,9 +131,13 @@ __device__ void assemble(zd* S, zd* Gam, const double* U, const zd* w, int K) {
 
 }  // namespace
 
+LeadControls lead_controls() { return g_controls; }
+void set_lead_controls(LeadControls c) { g_controls = c; }
+
 __global__ void __launch_bounds__(NT, 1)
-lead_kernel(const LeadDev* __restrict__ leads, int nlead, double eta, double* __restrict__ ws,
-            zd* __restrict__ out, int* __restrict__ lead_status, int* __restrict__ lead_iters) {
+lead_kernel(const LeadDev* __restrict__ leads, int nlead, double eta, int max_iter,
+            double residual_tol, double* __restrict__ ws, zd* __restrict__ out,
+            int* __restrict__ lead_status, int* __restrict__ lead_iters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int prob = blockIdx.x;
     const LeadDev ld = leads[prob];
@@ -125,33 +148,43 @@ lead_kernel(const LeadDev* __restrict__ leads, int nlead, double eta, double* __
     if (threadIdx.x == 0) { flags[0] = 1; flags[1] = 0; }
     __syncthreads();
     const zd z = {ld.E, eta};
-    for (int p = threadIdx.x; p < KL; p += NT) {
+    const bool finite_E = isfinite(ld.E);
+    for (int p = threadIdx.x; p < KL && finite_E; p += NT) {
         int it;
         bool ok;
-        zd g = mode_surface(p + 1, N, ld.t, z, it, ok);
+        zd g = mode_surface(p + 1, N, ld.t, z, max_iter, it, ok);
         const double tau = 2.0 * ld.t * cospi((double)(p + 1) / (double)(N + 1));
+        if (ok && !(mode_residual(g, ld.t, tau, z) <= residual_tol)) ok = false;
         w[p] = cscale(g, tau * tau);
         if (!ok) atomicExch(&flags[0], 0);
         atomicMax(&flags[1], it);
     }
     __syncthreads();
-    const bool ok = flags[0] != 0;
+    const bool ok = finite_E && flags[0] != 0;
     zd* SigL = out + ld.off;
     zd* SigR = SigL + (size_t)KL * KL;
     zd* GamL = SigR + (size_t)KR * KR;
     zd* GamR = GamL + (size_t)KL * KL;
+    zd* UL = GamR + (size_t)KR * KR;
+    zd* UR = UL + (size_t)KL * KL;
+    zd* wout = UR + (size_t)KR * KR;
     double* U = ws + 2 * ld.ws_off;
     if (ok) {
         mode_basis(U, KL, N, 0, red);
         assemble(SigL, GamL, U, w, KL);
+        for (int e = threadIdx.x; e < KL * KL; e += NT) UL[e] = {U[e], 0.0};
+        __syncthreads();
         mode_basis(U, KR, N, 1, red);
         assemble(SigR, GamR, U, w, KR);
+        for (int e = threadIdx.x; e < KR * KR; e += NT) UR[e] = {U[e], 0.0};
+        for (int p = threadIdx.x; p < KL; p += NT) wout[p] = w[p];
     } else {
-        for (int e = threadIdx.x; e < KL * KL; e += NT) SigL[e] = GamL[e] = {NAN, NAN};
-        for (int e = threadIdx.x; e < KR * KR; e += NT) SigR[e] = GamR[e] = {NAN, NAN};
+        for (int e = threadIdx.x; e < KL * KL; e += NT) SigL[e] = GamL[e] = UL[e] = {NAN, NAN};
+        for (int e = threadIdx.x; e < KR * KR; e += NT) SigR[e] = GamR[e] = UR[e] = {NAN, NAN};
+        for (int p = threadIdx.x; p < KL; p += NT) wout[p] = {NAN, NAN};
     }
     if (threadIdx.x == 0) {
-        const int st = ok ? ST_OK : ST_ENOCONV;
+        const int st = ok ? ST_OK : (finite_E ? ST_ENOCONV : ST_EINVAL);
         lead_status[2 * prob] = lead_status[2 * prob + 1] = st;
         if (lead_iters) lead_iters[2 * prob] = lead_iters[2 * prob + 1] = ok ? flags[1] : -1;
     }
@@ -161,8 +194,9 @@ cudaError_t launch_lead(const LeadDev* leads, int nlead, int Kmax, double eta_le
                         void* out, int* lead_status, int* lead_iters, cudaStream_t st) {
     if (nlead <= 0) return cudaSuccess;
     size_t smem = (size_t)Kmax * 16 + (size_t)(Kmax > NWARP ? Kmax : NWARP) * 8 + 16;
-    lead_kernel<<<nlead, NT, smem, st>>>(leads, nlead, eta_lead, (double*)ws, (zd*)out,
-                                         lead_status, lead_iters);
+    const LeadControls ctl = lead_controls();
+    lead_kernel<<<nlead, NT, smem, st>>>(leads, nlead, eta_lead, ctl.max_iter, ctl.residual_tol,
+                                         (double*)ws, (zd*)out, lead_status, lead_iters);
     return cudaGetLastError();
 }
 

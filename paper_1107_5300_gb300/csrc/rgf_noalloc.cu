@@ -10,18 +10,26 @@
 // their inputs and outputs as device pointers; everything else lives in the
 // array below.
 //
-// The array (kScratchBytes, 64 MiB) is part of the library image: every GPU
-// that loads the library holds it until the process exits.  All calls share
-// it, and it keeps the previous call's contents; calls whose work overlaps on
-// the GPU (concurrent streams, or a second call before the first has finished
-// on another stream) race on it.
+// The array (kScratchBytes, 64 MiB) is part of the library's device code: every
+// GPU that loads that code holds it until the process exits.  CUDA loads device
+// code lazily by default, so the array comes into being at this entry point's
+// first call on a device (inside its cudaGetSymbolAddress), or when the context
+// is created if CUDA_MODULE_LOADING=EAGER is set; a caller that reserves the
+// device memory for its own pool should make one call before doing so.  The
+// first call on a device looks the address up and caches it (make that call
+// before any stream capture); after cudaDeviceReset of that device the cached
+// address is stale, so the entry point must not be used again in that process.
+// All calls share the array, and it keeps the previous call's contents; calls
+// whose work overlaps on the GPU (concurrent streams, or a second call before
+// the first has finished on another stream) race on it.  Each call writes its
+// own descriptors into the array with a kernel (nothing is copied from host
+// memory) and every part of the array it reads is written earlier in the same
+// call.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <cstring>
 #include <mutex>
 #include <string>
-#include <vector>
 
 #include "rgf.h"
 #include "rgf_internal.h"
@@ -59,12 +67,32 @@ cudaError_t scratch_address(int dev, void** out) {
     return cudaSuccess;
 }
 
-__global__ void noalloc_fill_energy(rgf::ChainDev* chains, rgf::LeadDev* leads, const double* E,
-                                    int n) {
+// Chain and lead descriptors of call i (one per energy) written on the device
+// from the call's arguments, so that a call copies nothing from the host.  A
+// non-finite energy is reported by the lead kernel as RGF_EINVAL.
+__global__ void noalloc_setup(rgf::ChainDev* chains, rgf::LeadDev* leads, int* order,
+                              int* lead_status, const double* onsite, const uint8_t* removed,
+                              int N, int L, double t, const double* E, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        chains[i].E = E[i];
-        leads[i].E = E[i];
+        rgf::ChainDev& ch = chains[i];
+        ch.eps = onsite;
+        ch.rem = removed;
+        ch.N = N;
+        ch.L = L;
+        ch.t = t;
+        ch.E = E[i];
+        ch.lead = i;
+        ch.ws_off = (size_t)i * rgf::sweep_ws_elems(N);
+        ch.grad_off = 0;
+        rgf::LeadDev& ld = leads[i];
+        ld.N = N;
+        ld.t = t;
+        ld.E = E[i];
+        ld.off = (size_t)i * rgf::lead_out_elems(N);
+        ld.ws_off = (size_t)i * rgf::lead_ws_elems(N);
+        order[i] = i;
+        lead_status[2 * i] = lead_status[2 * i + 1] = 0;
     }
 }
 
@@ -80,7 +108,8 @@ extern "C" rgf_status rgf_conductance_noalloc(int N, int L, double t, const doub
     if (N < 2 || N > 2047 || L < 1 || !std::isfinite(t) || t == 0.0)
         return nfail(RGF_EINVAL, "bad N, L or t");
     if (!onsite_dev || !E_dev || !T_dev) return nfail(RGF_EINVAL, "NULL device pointer");
-    if (precision != RGF_FP64 && precision != RGF_MIXED) return nfail(RGF_EINVAL, "unknown precision");
+    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+        return nfail(RGF_EINVAL, "unknown precision");
     if (!(eta_device >= 0.0) || !(eta_lead > 0.0) || !std::isfinite(eta_device) ||
         !std::isfinite(eta_lead))
         return nfail(RGF_EINVAL, "eta_device must be >= 0 and eta_lead > 0 (finite)");
@@ -112,51 +141,26 @@ extern "C" rgf_status rgf_conductance_noalloc(int N, int L, double t, const doub
         return nfail(RGF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     unsigned char* sp = static_cast<unsigned char*>(base);
 
-    std::vector<rgf::ChainDev> chains(n);
-    std::vector<rgf::LeadDev> leads(n);
-    std::vector<int> order(n);
-    for (size_t c = 0; c < n; ++c) {
-        rgf::ChainDev& ch = chains[c];
-        ch.eps = onsite_dev;
-        ch.rem = removed_dev;
-        ch.N = N;
-        ch.L = L;
-        ch.t = t;
-        ch.E = 0.0;
-        ch.lead = (int)c;
-        ch.ws_off = c * rgf::sweep_ws_elems(N);
-        ch.grad_off = 0;
-        rgf::LeadDev& ld = leads[c];
-        ld.N = N;
-        ld.t = t;
-        ld.E = 0.0;
-        ld.off = c * rgf::lead_out_elems(N);
-        ld.ws_off = c * rgf::lead_ws_elems(N);
-        order[c] = (int)c;
-    }
-    std::vector<unsigned char> hdr(o_lst);
-    std::memcpy(hdr.data() + o_chain, chains.data(), b_chain);
-    std::memcpy(hdr.data() + o_lead, leads.data(), b_lead);
-    std::memcpy(hdr.data() + o_order, order.data(), b_order);
     cudaStream_t st = (cudaStream_t)stream;
-    e = cudaMemcpyAsync(sp, hdr.data(), hdr.size(), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
-    // The lead status words are always written by the lead kernel; clear them
-    // anyway so that nothing of a previous call can be read back.
-    e = cudaMemsetAsync(sp + o_lst, 0, 2 * n * sizeof(int), st);
-    if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
     auto* dchains = reinterpret_cast<rgf::ChainDev*>(sp + o_chain);
     auto* dleads = reinterpret_cast<rgf::LeadDev*>(sp + o_lead);
     auto* dorder = reinterpret_cast<int*>(sp + o_order);
     auto* dlst = reinterpret_cast<int*>(sp + o_lst);
-    noalloc_fill_energy<<<(nE + 255) / 256, 256, 0, st>>>(dchains, dleads, E_dev, nE);
+    noalloc_setup<<<(nE + 255) / 256, 256, 0, st>>>(dchains, dleads, dorder, dlst, onsite_dev,
+                                                     removed_dev, N, L, t, E_dev, nE);
     e = cudaGetLastError();
     if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
     const int Kmax = rgf::col_KL(N);
     e = rgf::launch_lead(dleads, nE, Kmax, eta_lead, sp + o_lws, sp + o_lout, dlst, nullptr, st);
     if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
-    e = rgf::launch_sweep(precision, dchains, dorder, nE, Kmax, eta_device, sp + o_lout, dlst,
-                          dleads, sp + o_ws, T_dev, status_dev, st);
+    e = rgf::launch_prep(precision, dchains, dorder, nE, Kmax, eta_device, sp + o_lout, dlst, dleads,
+                         sp + o_ws, st);
+    if (e == cudaSuccess)
+        e = rgf::launch_half(precision, dchains, dorder, nE, Kmax, eta_device, sp + o_lout, dlst,
+                             dleads, sp + o_ws, st);
+    if (e == cudaSuccess)
+        e = rgf::launch_merge(precision, dchains, dorder, nE, Kmax, eta_device, sp + o_lout, dlst,
+                              dleads, sp + o_ws, T_dev, status_dev, st);
     if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
     return RGF_OK;
 }

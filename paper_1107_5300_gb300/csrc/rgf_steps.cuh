@@ -160,19 +160,22 @@ __device__ void dense_product(int m, int n, int kd, const cx<R>* A, int lda, con
     cta_gemm<R, TA, false>(m, n, kd, A, lda, B, ldb, C, ldc, GEMM_SET, s.gemm);
 }
 
-// Everything a block needs to know about its chain.
+// Everything a block needs to know about its chain.  dir: the direction of
+// the column recursion this block runs -- 0 from the left lead (column k
+// follows k - 1), 1 from the right lead (column k follows k + 1).
 struct ChainCtx {
     const double* eps;
     const uint8_t* rem;
-    int N, L, M, KL, KR, ncol;
+    int N, L, M, KL, KR, ncol, dir;
     double t, t2;
     df32 tf, t2f;    // t and t^2 in double-float, converted once
     zd z;
-    const zd *SigL, *SigR, *GamL, *GamR;
+    const zd *SigL, *SigR, *GamL, *GamR;   // site basis of the lead-attached columns
+    const zd *UL, *UR, *w;                 // mode vectors (real parts) and w_p = tau_p^2 g_p
 };
 
 __device__ inline ChainCtx make_ctx(const ChainDev& ch, const LeadDev& ld, const zd* leadout,
-                                    double eta_d) {
+                                    double eta_d, int dir = 0) {
     ChainCtx c;
     c.eps = ch.eps;
     c.rem = ch.rem;
@@ -182,6 +185,7 @@ __device__ inline ChainCtx make_ctx(const ChainDev& ch, const LeadDev& ld, const
     c.KL = col_KL(ch.N);
     c.KR = col_KR(ch.N);
     c.ncol = 4 * ch.L;
+    c.dir = dir;
     c.t = ch.t;
     c.t2 = ch.t * ch.t;
     c.tf = df_from_double(c.t);
@@ -191,6 +195,9 @@ __device__ inline ChainCtx make_ctx(const ChainDev& ch, const LeadDev& ld, const
     c.SigR = c.SigL + (size_t)c.KL * c.KL;
     c.GamL = c.SigR + (size_t)c.KR * c.KR;
     c.GamR = c.GamL + (size_t)c.KL * c.KL;
+    c.UL = c.GamR + (size_t)c.KR * c.KR;
+    c.UR = c.UL + (size_t)c.KL * c.KL;
+    c.w = c.UR + (size_t)c.KR * c.KR;
     return c;
 }
 
@@ -224,6 +231,17 @@ __device__ __forceinline__ void col_src_T(int c, int a, int K, int& b0, int& b1)
     else { b0 = (a < K) ? a : -1; b1 = (a + 1 < K) ? a + 1 : -1; }
 }
 
+// The column that precedes column k in the recursion of direction c.dir.
+__device__ __forceinline__ int prev_col(const ChainCtx& c, int k) { return c.dir ? k + 1 : k - 1; }
+
+// Entries a0, a1 (-1 = none) of the preceding column (size Kq) bonded to entry
+// i of column k: the source stencil of W_k from the left, its transpose (the
+// bonds of column k + 1 seen from column k) from the right.
+__device__ __forceinline__ void prev_src(const ChainCtx& c, int k, int i, int Kq, int& a0, int& a1) {
+    if (c.dir == 0) col_src(k & 3, i, Kq, a0, a1);
+    else col_src_T((k + 1) & 3, i, Kq, a0, a1);
+}
+
 // Keep mask (0 = removed atom) and on-site energies of column k into shared memory.
 __device__ inline void load_col(const ChainCtx& c, int k, uint8_t* km, double* eps) {
     if (k < 0 || k >= c.ncol) return;
@@ -238,21 +256,26 @@ __device__ inline void load_col(const ChainCtx& c, int k, uint8_t* km, double* e
 template <class R>
 __device__ __forceinline__ cx<R> ld_z(const zd* p) { return from_z<R>(p->re, p->im); }
 
-// The two halves of one forward column step k (row-major, leading dimension KL):
-//   inv_column:   X = A_k (K x K), Gout = A_k^-1 (Gauss-Jordan; Gout may alias
-//                 Gprev).  Needs s.kc / s.eps of column k and s.kp of column
-//                 k-1.  Returns the Gauss-Jordan flag.
-//   strip_column: Y = Pprev W_k (KL x K), Pout = Y Gk  (Pout = Gk at k = 0;
-//                 Pout may alias Pprev).  Needs s.kc and s.kp.
+// One interior step of a half's column recursion at column k (row-major,
+// leading dimension KL), with q = prev_col(c, k) the column before it:
+//   inv_column:   X = A_k = (z - eps_k) I - t^2 S^T g_q S (K x K; S the bond
+//                 stencil between q and k, identity rows and columns at removed
+//                 atoms), Gout = A_k^-1 (Gauss-Jordan; Gout may alias Gprev).
+//                 Needs s.kc / s.eps of column k and s.kp of column q.  Returns
+//                 the Gauss-Jordan flag.
+//   strip_column: Y = Pprev W (R x K, R the rows of the half's corner block),
+//                 Pout = Y Gk (Pout may alias Pprev; Y may alias the X of
+//                 inv_column).  Needs s.kc and s.kp.
+// The lead-attached first column of a half is prepared elsewhere (rgf_sweep.cu).
 template <class R>
 __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout, cx<R>* X,
-                          SweepSmem<R>& s, Team tm = Team{0, 1}) {
+                          SweepSmem<R>& s) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int KL = c.KL, ct = k & 3, K = col_size(c, k), Kp = col_size(c, k - 1);
+    const int KL = c.KL, K = col_size(c, k), Kq = col_size(c, prev_col(c, k));
     double amax2 = 0.0;
-    for (int i = tm.lo(K) + warp; i < tm.hi(K); i += NWARP) {
-        int a0 = -1, a1 = -1;
-        if (k > 0) col_src(ct, i, Kp, a0, a1);
+    for (int i = warp; i < K; i += NWARP) {
+        int a0, a1;
+        prev_src(c, k, i, Kq, a0, a1);
         const bool ki = s.kc[i];
         const bool ka0 = a0 >= 0 && s.kp[a0], ka1 = a1 >= 0 && s.kp[a1];
         for (int l = lane; l < K; l += 32) {
@@ -260,20 +283,15 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
             if (!ki || !s.kc[l]) {
                 v = (i == l) ? from_z<R>(1.0, 0.0) : czero<R>();
             } else {
+                int b0, b1;
+                prev_src(c, k, l, Kq, b0, b1);
+                const bool kb0 = b0 >= 0 && s.kp[b0], kb1 = b1 >= 0 && s.kp[b1];
                 cx<R> sig = czero<R>();
-                if (k == 0) {
-                    sig = ld_z<R>(c.SigL + (size_t)i * KL + l);
-                } else {
-                    int b0, b1;
-                    col_src(ct, l, Kp, b0, b1);
-                    const bool kb0 = b0 >= 0 && s.kp[b0], kb1 = b1 >= 0 && s.kp[b1];
-                    if (ka0 && kb0) sig = cadd(sig, Gprev[(size_t)a0 * KL + b0]);
-                    if (ka0 && kb1) sig = cadd(sig, Gprev[(size_t)a0 * KL + b1]);
-                    if (ka1 && kb0) sig = cadd(sig, Gprev[(size_t)a1 * KL + b0]);
-                    if (ka1 && kb1) sig = cadd(sig, Gprev[(size_t)a1 * KL + b1]);
-                    sig = cscale(sig, Hop<R>::t2(c));
-                }
-                if (k == c.ncol - 1) sig = cadd(sig, ld_z<R>(c.SigR + (size_t)i * c.KR + l));
+                if (ka0 && kb0) sig = cadd(sig, Gprev[(size_t)a0 * KL + b0]);
+                if (ka0 && kb1) sig = cadd(sig, Gprev[(size_t)a0 * KL + b1]);
+                if (ka1 && kb0) sig = cadd(sig, Gprev[(size_t)a1 * KL + b0]);
+                if (ka1 && kb1) sig = cadd(sig, Gprev[(size_t)a1 * KL + b1]);
+                sig = cscale(sig, Hop<R>::t2(c));
                 v = (i == l) ? from_z<R>(c.z.re - s.eps[i], c.z.im) : czero<R>();
                 v = csub(v, sig);
             }
@@ -283,59 +301,38 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
         }
     }
     amax2 = block_max(amax2, s.red);
-    if (tm.C > 1) {
-        if (threadIdx.x == 0) *s.clmax = amax2;
-        cl_sync(tm);                      // A_k complete; partial maxima visible
-        auto cluster = cooperative_groups::this_cluster();
-        for (int r = 0; r < tm.C; ++r) {
-            const double v = *cluster.map_shared_rank(s.clmax, r);
-            amax2 = (v > amax2 || isnan(v)) ? v : amax2;
-        }
-    }
-    return cta_gj_invert<R>(X, K, KL, Gout, KL, s.gj, amax2, tm);
+    return cta_gj_invert<R>(X, K, KL, Gout, KL, s.gj, amax2);
 }
 
-// Strip half; with a team, Y is built by rows and the product by columns, and
-// Pout is complete after the caller's next cluster barrier.
 template <class R>
 __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx<R>* Pprev,
-                             cx<R>* Pout, cx<R>* Y, SweepSmem<R>& s, Team tm = Team{0, 1}) {
+                             cx<R>* Pout, cx<R>* Y, SweepSmem<R>& s) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int KL = c.KL, ct = k & 3, K = col_size(c, k), Kp = col_size(c, k - 1);
-    if (k == 0) {
-        for (int i = tm.lo(K) + warp; i < tm.hi(K); i += NWARP)
-            for (int l = lane; l < K; l += 32) Pout[(size_t)i * KL + l] = Gk[(size_t)i * KL + l];
-        __syncthreads();
-        return;
-    }
-    for (int r = tm.lo(KL) + warp; r < tm.hi(KL); r += NWARP)
+    const int KL = c.KL, K = col_size(c, k), Kq = col_size(c, prev_col(c, k));
+    const int rows = c.dir ? c.KR : c.KL;
+    for (int r = warp; r < rows; r += NWARP)
         for (int l = lane; l < K; l += 32) {
             cx<R> v = czero<R>();
             if (s.kc[l]) {
                 int a0, a1;
-                col_src(ct, l, Kp, a0, a1);
+                prev_src(c, k, l, Kq, a0, a1);
                 if (a0 >= 0 && s.kp[a0]) v = cadd(v, Pprev[(size_t)r * KL + a0]);
                 if (a1 >= 0 && s.kp[a1]) v = cadd(v, Pprev[(size_t)r * KL + a1]);
                 v = cscale(v, Hop<R>::t(c));
             }
             Y[(size_t)r * KL + l] = v;
         }
-    cl_sync(tm);                          // Y complete (Pprev no longer read)
-    const int lo = tm.lo(K), n = tm.hi(K) - lo;
-    if (n <= 0) {
-        __syncthreads();
-        return;
-    }
+    __syncthreads();                      // Y complete (Pprev no longer read)
     if constexpr (std::is_same<R, df32>::value) {
         if (s.tcs) {
-            for (int r0 = 0; r0 < KL; r0 += 128) {
-                const DenseOp op{Y, KL, Gk + lo, KL, Pout + lo, KL, r0, false};
-                s.tcs->phase = tc::zgemm(op, min(128, KL - r0), n, K, s.tcs->ar, s.tcs->phase);
+            for (int r0 = 0; r0 < rows; r0 += 128) {
+                const DenseOp op{Y, KL, Gk, KL, Pout, KL, r0, false};
+                s.tcs->phase = tc::zgemm(op, min(128, rows - r0), K, K, s.tcs->ar, s.tcs->phase);
             }
             return;
         }
     }
-    cta_gemm<R, false, false>(KL, n, K, Y, KL, Gk + lo, KL, Pout + lo, KL, GEMM_SET, s.gemm);
+    cta_gemm<R, false, false>(rows, K, K, Y, KL, Gk, KL, Pout, KL, GEMM_SET, s.gemm);
 }
 
 // Tr[Gamma_L P Gamma_R P^dagger] in binary64.  P: KL x KR (ld KL) in the working

@@ -1,5 +1,6 @@
-// rgf_sweep.cu -- the forward RGF sweep (Eqs. 4-5) and the Landauer trace
-// (Eq. 2), one thread block per chain (ribbon, energy).
+// rgf_sweep.cu -- the RGF recursion (Eqs. 4-5) and the Landauer trace (Eq. 2)
+// for a batch of chains (ribbon, energy), as two half sweeps per chain joined
+// by one Dyson step (Eq. 3).
 //
 // The paper slices the ribbon into cross-sections and applies, slice after
 // slice, g_j = (z - H_jj - V^T g_{j-1} V)^-1 together with the corner block
@@ -7,35 +8,58 @@
 // sliced further into its four atom columns (x = 0, a, 1.5a, 2.5a): a column
 // has no internal hopping, neighbouring columns are coupled by t*I (same row)
 // or by a bidiagonal t-stencil (rows j +- 1).  The recursion is the same
-// Dyson step on blocks of KL = ceil(N/2) or KR = floor(N/2) orbitals, 4L steps
-// per chain, and reaches the same G_1L:
+// Dyson step on blocks of KL = ceil(N/2) or KR = floor(N/2) orbitals, 4L
+// columns per chain.
 //
-//   A_k   = (z - eps_k) I - t^2 S_k^T g_{k-1} S_k   (- Sigma_L at k = 0,
-//                                                   - Sigma_R at k = 4L-1)
-//   g_k   = A_k^-1                                  (Gauss-Jordan, pivoted)
-//   P_k   = (P_{k-1} W_k) g_k,   P_0 = g_0          (P_k = G_{first col, k})
-//   T     = Tr[Gamma_L P Gamma_R P^dagger]          (binary64)
+// Domain decomposition.  A chain's recursion is strictly sequential along the
+// ribbon; the paper notes that running it in parallel needs a modified
+// recursion (its remark on MPI).  The columns 0 .. n-1 (n = 4L) are cut into
+// a left part 0 .. m-1 and a right part m .. n-1 (m = n/2).  Each part runs
+// the recursion from its own lead, on its own SM, at the same time:
 //
-// S_k is the 1- or 2-point source stencil of the column coupling; the product
-// V^T g V is a gather-and-contract over at most 4 entries of g_{k-1} per entry.
-// Removed atoms become identity rows/columns with zero couplings (an exact
-// equivalence to dropping them).
+//   left  (k = 0 .. m-1):   gl_k = (z - eps_k - t^2 S_k^T gl_{k-1} S_k)^-1
+//                           Pl_k = U_even^T G^left_{0,k}  = Pl_{k-1} W_k gl_k
+//   right (k = n-1 .. m):   gr_k = (z - eps_k - t^2 S_{k+1} gr_{k+1} S_{k+1}^T)^-1
+//                           Pr_k = U_odd^T G^right_{n-1,k} = Pr_{k+1} W_{k+1}^T gr_k
 //
-// Each chain runs on a cluster of C blocks (C SMs; C = 1, 2, 4 or 8, the
-// largest with chains x C <= SMs).  Two schedules:
-//   C = 2  pipeline: block 0 builds and inverts column k+1 while block 1
-//          applies the strip product of column k; one cluster barrier per
-//          column hands g_k over through a double buffer in L2.
-//   else   team: every phase is shared -- the A_k build and the copy-out of
-//          g_k by rows, the Gauss-Jordan panel redundantly (same data, same
-//          result), its substitution and rank-b update by columns, the strip
-//          product by columns; cluster barriers order the phases.
-// With TC (precision RGF_MIXED_TC) the two dense contractions of a column
-// step -- the Gauss-Jordan rank-b updates and the strip product -- run on the
-// tcgen05 tensor cores by exact digit slicing of their double-float operands
-// (rgf_tc.cuh); every block then holds the SM's TMEM for the whole launch.
-#include <cooperative_groups.h>
-
+// (W_k = t S_k the coupling of columns k-1 and k; each part sees only its own
+// lead.)  The Dyson equation across the bond between columns m-1 and m then
+// gives the corner block of the whole system,
+//
+//   G_{0,n-1} = G^left_{0,m-1} W_m (I - gr_m SigmaL_m)^-1 G^right_{m,n-1},
+//   SigmaL_m = W_m^T gl_{m-1} W_m,
+//
+// so U_even^T G_{0,n-1} U_odd = (Pl_{m-1} W_m) (I - gr_m SigmaL_m)^-1 Pr_m^T and
+// T = sum_pq gamma_p gamma'_q |(U_even^T G_{0,n-1} U_odd)_pq|^2 (Eq. 2 in the
+// mode basis, gamma = -2 Im w).  Same work as one sweep over n columns, half
+// the sequential depth.
+//
+// Lead-attached columns.  The first column of each part carries the lead
+// self-energy, Sigma = U diag(w) U^T.  Near E = 0 the transverse cut of an
+// armchair ribbon is zigzag-like and the modes with |tau_p| > |t| have a
+// surface state: |w_p| ~ 1/eta (~1e9 eV at eta = 1e-8).  In the site basis
+// those entries would be summed with the order-1 on-site terms and drown
+// them.  The first column is therefore formed and inverted in the mode basis,
+// in binary64, by its own kernel (prep_kernel):
+//
+//   A~ = U^T diag(z - eps) U - diag(w),   g~ = A~^-1,
+//   P_0 = g~ U^T (rows in the mode basis),   g_0 = U P_0 (site basis),
+//
+// where the surface-state modes meet only their own order-1/eta diagonal.
+// The corner blocks are carried with their rows in the mode bases, so the
+// order-eta components that Gamma ~ 1/eta weights in the trace keep their own
+// relative accuracy.  (A lead-attached column with a removed atom is formed
+// in the site basis instead.)
+//
+// Launches (one stream): prep_kernel (binary64, 2 blocks per chain),
+// half_kernel<R, TC> (the recursion of each part, 2 blocks per chain, the
+// dominant kernel), merge_kernel (binary64, 1 block per chain: the Dyson step
+// across the cut, the trace and the status word).  Removed atoms become
+// identity rows/columns with zero couplings (an exact equivalence to dropping
+// them).  With TC (precision RGF_MIXED_TC) the two dense contractions of a
+// column step -- the Gauss-Jordan rank-b updates and the strip product -- run
+// on the tcgen05 tensor cores by exact digit slicing of their double-float
+// operands (rgf_tc.cuh); every block then holds the SM's TMEM for the launch.
 #include "rgf_steps.cuh"
 
 namespace rgf {
@@ -44,172 +68,304 @@ size_t sweep_smem_bytes(int Kmax, bool tc) {
     return sweep_total_bytes(Kmax, gj_panel_width(Kmax, tc), tc);
 }
 
+namespace {
+
+// Columns of the left part; the right part has ncol - m.
+__host__ __device__ inline int left_cols(int ncol) { return ncol / 2; }
+
+// The buffers of one half of a chain's workspace (16-byte elements, ld KL).
+template <class R>
+struct Half {
+    cx<R>* X;        // slice matrix / scratch
+    cx<R>* G;        // g of the last column done
+    cx<R>* P;        // corner block, rows in the lead's mode basis
+    int* flag;       // Gauss-Jordan / tensor-core flags of this half
+};
+template <class R>
+__device__ inline Half<R> half_of(void* ws, const ChainDev& ch, int h) {
+    const size_t B = (size_t)col_KL(ch.N) * col_KL(ch.N);
+    cx<R>* base = reinterpret_cast<cx<R>*>(ws) + ch.ws_off + (size_t)h * half_ws_elems(ch.N);
+    return Half<R>{base, base + B, base + 2 * B, reinterpret_cast<int*>(base + 3 * B)};
+}
+
+// In-place conversion of a K1 x K2 block (ld) between binary64 and the
+// working precision (both 16-byte complex elements).  Every thread; barrier.
+template <class R>
+__device__ void to_working(cx<R>* p, int K1, int K2, int ld) {
+    for (int e = threadIdx.x; e < K1 * K2; e += NT) {
+        const int i = e / K2, j = e % K2;
+        const zd v = reinterpret_cast<zd*>(p)[(size_t)i * ld + j];
+        p[(size_t)i * ld + j] = from_z<R>(v.re, v.im);
+    }
+    __syncthreads();
+}
+template <class R>
+__device__ void to_binary64(cx<R>* p, int K1, int K2, int ld) {
+    for (int e = threadIdx.x; e < K1 * K2; e += NT) {
+        const int i = e / K2, j = e % K2;
+        const zd v = to_z(p[(size_t)i * ld + j]);
+        reinterpret_cast<zd*>(p)[(size_t)i * ld + j] = v;
+    }
+    __syncthreads();
+}
+
+__device__ inline double max_abs2(const zd* A, int K, int ld, double* red) {
+    double m = 0.0;
+    for (int e = threadIdx.x; e < K * K; e += NT) {
+        const double a = cabs2(A[(size_t)(e / K) * ld + e % K]);
+        m = (a > m || isnan(a)) ? a : m;
+    }
+    return block_max(m, red);
+}
+
+}  // namespace
+
+// The lead-attached first column of each half, in binary64: h = 0 the left
+// lead's column 0 (KL even-row left atoms), h = 1 the right lead's column
+// n-1 (KR odd-row right atoms).  Writes g (site basis) and P (rows in the
+// lead's mode basis) into the half's G and P in the working precision R, and
+// the Gauss-Jordan flags into the half's flag word.
+template <class R>
+__global__ void __launch_bounds__(NT, 1)
+prep_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int Kmax,
+            double eta_d, const zd* __restrict__ leadout, const int* __restrict__ lead_status,
+            const LeadDev* __restrict__ leads, void* __restrict__ ws) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    SweepSmem<double> s = carve<double>(smem_raw, Kmax, false);
+    const int ci = order[blockIdx.x >> 1], h = blockIdx.x & 1;
+    const ChainDev ch = chains[ci];
+    if (lead_state(lead_status, ch.lead) != ST_OK) return;     // reported by the merge
+    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d, h);
+    const Half<R> hw = half_of<R>(ws, ch, h);
+    zd* X = reinterpret_cast<zd*>(hw.X);
+    zd* G = reinterpret_cast<zd*>(hw.G);
+    zd* P = reinterpret_cast<zd*>(hw.P);
+    const int KL = c.KL, k = h ? c.ncol - 1 : 0, K = h ? c.KR : c.KL;
+    const zd* U = h ? c.UR : c.UL;                  // K x K, ld K
+    const zd* Sig = h ? c.SigR : c.SigL;            // K x K, ld K
+    load_col(c, k, s.kc, s.eps);
+    if (threadIdx.x == 0) s.gj.ctl[2] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < K; i += NT)
+        if (!s.kc[i]) s.gj.ctl[2] = 1;
+    __syncthreads();
+    const bool removed = s.gj.ctl[2] != 0;
+    int flag;
+    if (!removed) {
+        // A~ = U^T diag(z - eps) U - diag(w) into G; g~ = A~^-1 into X
+        for (int e = threadIdx.x; e < K * K; e += NT) {
+            const int i = e / K, p = e % K;
+            const double u = U[(size_t)i * K + p].re;
+            X[(size_t)i * KL + p] = {(c.z.re - s.eps[i]) * u, c.z.im * u};
+        }
+        __syncthreads();
+        cta_gemm<double, true, false>(K, K, K, U, K, X, KL, G, KL, GEMM_SET, s.gemm);
+        for (int p = threadIdx.x; p < K; p += NT) G[(size_t)p * KL + p] = csub(G[(size_t)p * KL + p], c.w[p]);
+        __syncthreads();
+        const double amax2 = max_abs2(G, K, KL, s.red);
+        flag = cta_gj_invert<double>(G, K, KL, X, KL, s.gj, amax2);
+        // P = g~ U^T, then g = U P
+        cta_gemm<double, false, true>(K, K, K, X, KL, U, K, P, KL, GEMM_SET, s.gemm);
+        cta_gemm<double, false, false>(K, K, K, U, K, P, KL, G, KL, GEMM_SET, s.gemm);
+    } else {
+        // site basis: (z - eps) I - Sigma on the kept atoms, identity rows and
+        // columns at removed atoms; then P = U^T g
+        for (int e = threadIdx.x; e < K * K; e += NT) {
+            const int i = e / K, l = e % K;
+            zd v;
+            if (!s.kc[i] || !s.kc[l]) v = (i == l) ? zd{1.0, 0.0} : zd{0.0, 0.0};
+            else v = csub((i == l) ? zd{c.z.re - s.eps[i], c.z.im} : zd{0.0, 0.0}, Sig[(size_t)i * K + l]);
+            X[(size_t)i * KL + l] = v;
+        }
+        __syncthreads();
+        const double amax2 = max_abs2(X, K, KL, s.red);
+        flag = cta_gj_invert<double>(X, K, KL, G, KL, s.gj, amax2);
+        cta_gemm<double, true, false>(K, K, K, U, K, G, KL, P, KL, GEMM_SET, s.gemm);
+    }
+    to_working<R>(hw.G, K, K, KL);
+    to_working<R>(hw.P, K, K, KL);
+    if (threadIdx.x == 0) *hw.flag = flag;
+}
+
+// The recursion of one half (h = blockIdx.x & 1) from its second column to
+// the cut: columns 1 .. m-1 (left) or n-2 .. m (right).
 template <class R, bool TC>
 __global__ void __launch_bounds__(NT, 1)
-sweep_team_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
-             int Kmax, double eta_d, const zd* __restrict__ leadout,
-             const int* __restrict__ lead_status, const LeadDev* __restrict__ leads,
-             cx<R>* __restrict__ ws, double* __restrict__ Tout, int32_t* __restrict__ status) {
-    namespace cg = cooperative_groups;
+half_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int Kmax,
+            double eta_d, const zd* __restrict__ leadout, const int* __restrict__ lead_status,
+            const LeadDev* __restrict__ leads, void* __restrict__ ws) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     SweepSmem<R> s = carve<R>(smem_raw, Kmax, TC);
-    cg::cluster_group cluster = cg::this_cluster();
-    const Team tm{(int)cluster.block_rank(), (int)cluster.num_blocks()};
-    const int ci = order[blockIdx.x / tm.C];
+    const int ci = order[blockIdx.x >> 1], h = blockIdx.x & 1;
     const ChainDev ch = chains[ci];
-    const int lst = lead_state(lead_status, ch.lead);
-    if (lst != ST_OK) {            // every block of the cluster leaves here
-        if (tm.rank == 0 && threadIdx.x == 0) { Tout[ci] = NAN; if (status) status[ci] = lst; }
-        return;
-    }
-    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d);
-    const size_t B = (size_t)c.KL * c.KL;
-    cx<R>* X = ws + ch.ws_off;
-    cx<R>* G = X + B;
-    cx<R>* P = X + 2 * B;
-    cx<R>* Y = X + 3 * B;
+    if (lead_state(lead_status, ch.lead) != ST_OK) return;
+    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d, h);
+    const Half<R> hw = half_of<R>(ws, ch, h);
+    const int m = left_cols(c.ncol), steps = h ? c.ncol - m : m;
     tc::State tst;
     if constexpr (TC) tc_attach<R>(Kmax, s, tst);
     int flag = 0;
-    for (int k = 0; k < c.ncol; ++k) {
+    for (int j = 1; j < steps; ++j) {
+        const int k = h ? c.ncol - 1 - j : j;
         load_col(c, k, s.kc, s.eps);
-        load_col(c, k - 1, s.kp, nullptr);
+        load_col(c, prev_col(c, k), s.kp, nullptr);
         __syncthreads();
-        flag |= inv_column<R>(c, k, G, G, X, s, tm);
-        cl_sync(tm);               // g_k complete
-        strip_column<R>(c, k, G, P, P, Y, s, tm);
-        cl_sync(tm);               // P_k complete
+        flag |= inv_column<R>(c, k, hw.G, hw.G, hw.X, s);
+        strip_column<R>(c, k, hw.G, hw.P, hw.P, hw.X, s);
     }
     if constexpr (TC) {
         if (*(volatile int*)tst.ar.err()) flag |= 4;
         tc::teardown(tst.ar);
     }
-    if (tm.rank == 0) {
-        const double T = trace_T<R>(c, P, X, G, Y, s);
-        if (threadIdx.x == 0) {
-            const int st = chain_status(c, flag, T);
-            Tout[ci] = (st == ST_OK) ? T : NAN;
-            if (status) status[ci] = st;
-        }
-    }
+    if (threadIdx.x == 0) *hw.flag |= flag;
 }
 
-template <class R, bool TC>
+// The Dyson step across the bond between columns m-1 and m, in binary64, and
+// the trace.  Scratch: the two halves' X and, once read, their G and P.
+template <class R>
 __global__ void __launch_bounds__(NT, 1)
-sweep_pipe_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int nchains,
-                  int Kmax, double eta_d, const zd* __restrict__ leadout,
-                  const int* __restrict__ lead_status, const LeadDev* __restrict__ leads,
-                  cx<R>* __restrict__ ws, double* __restrict__ Tout, int32_t* __restrict__ status) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
+merge_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int Kmax,
+             double eta_d, const zd* __restrict__ leadout, const int* __restrict__ lead_status,
+             const LeadDev* __restrict__ leads, void* __restrict__ ws, double* __restrict__ Tout,
+             int32_t* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    SweepSmem<R> s = carve<R>(smem_raw, Kmax, TC);
-    const int role = (int)cluster.block_rank();      // 0: inverse, 1: strip
-    const int ci = order[blockIdx.x >> 1];
+    SweepSmem<double> s = carve<double>(smem_raw, Kmax, false);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ci = order[blockIdx.x];
     const ChainDev ch = chains[ci];
     const int lst = lead_state(lead_status, ch.lead);
-    if (lst != ST_OK) {            // both blocks of the cluster leave here
-        if (role == 1 && threadIdx.x == 0) { Tout[ci] = NAN; if (status) status[ci] = lst; }
+    if (lst != ST_OK) {
+        if (threadIdx.x == 0) { Tout[ci] = NAN; if (status) status[ci] = lst; }
         return;
     }
-    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d);
-    const size_t B = (size_t)c.KL * c.KL;
-    cx<R>* X = ws + ch.ws_off;
-    cx<R>* Gb[2] = {X + B, X + 2 * B};
-    cx<R>* P = X + 3 * B;
-    cx<R>* Y = X + 4 * B;
-    int* flag_slot = reinterpret_cast<int*>(X + 5 * B);
-    tc::State tst;
-    if constexpr (TC) tc_attach<R>(Kmax, s, tst);
-    if (role == 0) {
-        int flag = 0;
-        for (int k = 0; k < c.ncol; ++k) {
-            load_col(c, k, s.kc, s.eps);
-            load_col(c, k - 1, s.kp, nullptr);
-            __syncthreads();
-            flag |= inv_column<R>(c, k, Gb[(k + 1) & 1], Gb[k & 1], X, s);
-            cluster.sync();        // g_k ready; block 1 is done with g_{k-1}
+    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d, 0);
+    const Half<R> L = half_of<R>(ws, ch, 0), Rt = half_of<R>(ws, ch, 1);
+    const int KL = c.KL, KR = c.KR, m = left_cols(c.ncol);
+    const int K = col_size(c, m), Kp = col_size(c, m - 1), ct = m & 3;
+    int flag = *L.flag | *Rt.flag;
+    load_col(c, m, s.kc, nullptr);
+    load_col(c, m - 1, s.kp, nullptr);
+    __syncthreads();
+    zd* XL = reinterpret_cast<zd*>(L.X);
+    zd* XR = reinterpret_cast<zd*>(Rt.X);
+    zd* GLd = reinterpret_cast<zd*>(L.G);
+    zd* GRd = reinterpret_cast<zd*>(Rt.G);
+    zd* PRd = reinterpret_cast<zd*>(Rt.P);
+    const double t = c.t, t2 = c.t2;
+    // SigmaL_m = t^2 S^T gl_{m-1} S (kept atoms only) into XL
+    for (int i = warp; i < K; i += NWARP) {
+        int a0, a1;
+        col_src(ct, i, Kp, a0, a1);
+        const bool ki = s.kc[i];
+        const bool ka0 = a0 >= 0 && s.kp[a0], ka1 = a1 >= 0 && s.kp[a1];
+        for (int l = lane; l < K; l += 32) {
+            zd v = {0.0, 0.0};
+            if (ki && s.kc[l]) {
+                int b0, b1;
+                col_src(ct, l, Kp, b0, b1);
+                const bool kb0 = b0 >= 0 && s.kp[b0], kb1 = b1 >= 0 && s.kp[b1];
+                if (ka0 && kb0) v = cadd(v, to_z(L.G[(size_t)a0 * KL + b0]));
+                if (ka0 && kb1) v = cadd(v, to_z(L.G[(size_t)a0 * KL + b1]));
+                if (ka1 && kb0) v = cadd(v, to_z(L.G[(size_t)a1 * KL + b0]));
+                if (ka1 && kb1) v = cadd(v, to_z(L.G[(size_t)a1 * KL + b1]));
+                v = cscale(v, t2);
+            }
+            XL[(size_t)i * KL + l] = v;
         }
-        if constexpr (TC) {
-            if (*(volatile int*)tst.ar.err()) flag |= 4;
-            tc::teardown(tst.ar);
+    }
+    __syncthreads();
+    // X = I - gr_m SigmaL_m into XR, its inverse into XL
+    to_binary64<R>(Rt.G, K, K, KL);
+    cta_gemm<double, false, false>(K, K, K, GRd, KL, XL, KL, XR, KL, GEMM_SET, s.gemm);
+    for (int e = threadIdx.x; e < K * K; e += NT) {
+        const int i = e / K, l = e % K;
+        zd& x = XR[(size_t)i * KL + l];
+        x = {((i == l) ? 1.0 : 0.0) - x.re, -x.im};
+    }
+    __syncthreads();
+    const double amax2 = max_abs2(XR, K, KL, s.red);
+    flag |= cta_gj_invert<double>(XR, K, KL, XL, KL, s.gj, amax2);
+    // Y = Pl_{m-1} W_m (KL x K) into GL (gl no longer needed), then
+    // Y (I - gr SigmaL)^-1 into XR and its product with Pr_m^T into GL
+    for (int r = warp; r < KL; r += NWARP)
+        for (int l = lane; l < K; l += 32) {
+            zd v = {0.0, 0.0};
+            if (s.kc[l]) {
+                int a0, a1;
+                col_src(ct, l, Kp, a0, a1);
+                if (a0 >= 0 && s.kp[a0]) v = cadd(v, to_z(L.P[(size_t)r * KL + a0]));
+                if (a1 >= 0 && s.kp[a1]) v = cadd(v, to_z(L.P[(size_t)r * KL + a1]));
+                v = cscale(v, t);
+            }
+            GLd[(size_t)r * KL + l] = v;
         }
-        if (threadIdx.x == 0) *flag_slot = flag;
-        cluster.sync();
-    } else {
-        for (int k = 0; k < c.ncol; ++k) {
-            cluster.sync();
-            load_col(c, k, s.kc, nullptr);
-            load_col(c, k - 1, s.kp, nullptr);
-            __syncthreads();
-            strip_column<R>(c, k, Gb[k & 1], P, P, Y, s);
-        }
-        int tflag = 0;
-        if constexpr (TC) {
-            if (*(volatile int*)tst.ar.err()) tflag = 4;
-            tc::teardown(tst.ar);
-        }
-        cluster.sync();
-        const int flag = *(volatile int*)flag_slot | tflag;
-        const double T = trace_T<R>(c, P, X, Gb[0], Y, s);
-        if (threadIdx.x == 0) {
-            const int st = chain_status(c, flag, T);
-            Tout[ci] = (st == ST_OK) ? T : NAN;
-            if (status) status[ci] = st;
-        }
+    __syncthreads();
+    cta_gemm<double, false, false>(KL, K, K, GLd, KL, XL, KL, XR, KL, GEMM_SET, s.gemm);
+    to_binary64<R>(Rt.P, KR, K, KL);
+    cta_gemm<double, false, true>(KL, KR, K, XR, KL, PRd, KL, GLd, KL, GEMM_SET, s.gemm);
+    // T = sum_pq gamma_p gamma'_q |P_pq|^2
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < KL * KR; e += NT) {
+        const int p = e / KR, q = e % KR;
+        const zd v = GLd[(size_t)p * KL + q];
+        acc += (-2.0 * c.w[p].im) * (-2.0 * c.w[q].im) * (v.re * v.re + v.im * v.im);
+    }
+    const double T = block_sum(acc, s.red);
+    if (threadIdx.x == 0) {
+        const int st = chain_status(c, flag, T);
+        Tout[ci] = (st == ST_OK) ? T : NAN;
+        if (status) status[ci] = st;
     }
 }
 
-template <class R, bool TC>
-static cudaError_t launch_sweep_t(const ChainDev* chains, const int* order, int nchains, int Kmax,
-                                  double eta_device, const zd* leadout, const int* lead_status,
-                                  const LeadDev* leads, cx<R>* ws, double* T, int32_t* status,
-                                  cudaStream_t st) {
-    const size_t smem = sweep_smem_bytes(Kmax, TC);
-    // Blocks per chain: the largest of 8, 4, 2, 1 with chains x C <= SMs.
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int C = 8;
-    while (C > 1 && (long long)nchains * C > nsm) C >>= 1;
-    auto kern = (C == 2) ? sweep_pipe_kernel<R, TC> : sweep_team_kernel<R, TC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(C * nchains, 1, 1);
-    cfg.blockDim = dim3(NT, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, chains, order, nchains, Kmax, eta_device, leadout,
-                              lead_status, leads, ws, T, status);
+namespace {
+
+template <class K>
+cudaError_t set_smem(K kern, size_t smem) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_sweep(int precision, const ChainDev* chains, const int* order, int nchains,
+}  // namespace
+
+cudaError_t launch_prep(int precision, const ChainDev* chains, const int* order, int nchains,
+                        int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                        const LeadDev* leads, void* ws, cudaStream_t st) {
+    if (nchains <= 0) return cudaSuccess;
+    const size_t smem = sweep_smem_bytes(Kmax, false);
+    auto kern = precision == 0 ? prep_kernel<double> : prep_kernel<df32>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<2 * nchains, NT, smem, st>>>(chains, order, Kmax, eta_device, (const zd*)leadout,
+                                        lead_status, leads, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_half(int precision, const ChainDev* chains, const int* order, int nchains,
+                        int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                        const LeadDev* leads, void* ws, cudaStream_t st) {
+    if (nchains <= 0) return cudaSuccess;
+    const bool tc = precision == 2;
+    const size_t smem = sweep_smem_bytes(Kmax, tc);
+    auto kern = precision == 0 ? half_kernel<double, false>
+                               : (tc ? half_kernel<df32, true> : half_kernel<df32, false>);
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<2 * nchains, NT, smem, st>>>(chains, order, Kmax, eta_device, (const zd*)leadout,
+                                        lead_status, leads, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order, int nchains,
                          int Kmax, double eta_device, const void* leadout, const int* lead_status,
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    cudaError_t e;
-    if (precision == 0)
-        e = launch_sweep_t<double, false>(chains, order, nchains, Kmax, eta_device,
-                                          (const zd*)leadout, lead_status, leads, (zd*)ws, T,
-                                          status, st);
-    else if (precision == 2)
-        e = launch_sweep_t<df32, true>(chains, order, nchains, Kmax, eta_device,
-                                       (const zd*)leadout, lead_status, leads, (zf*)ws, T, status,
-                                       st);
-    else
-        e = launch_sweep_t<df32, false>(chains, order, nchains, Kmax, eta_device,
-                                        (const zd*)leadout, lead_status, leads, (zf*)ws, T,
-                                        status, st);
+    const size_t smem = sweep_smem_bytes(Kmax, false);
+    auto kern = precision == 0 ? merge_kernel<double> : merge_kernel<df32>;
+    cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
+    kern<<<nchains, NT, smem, st>>>(chains, order, Kmax, eta_device, (const zd*)leadout,
+                                    lead_status, leads, ws, T, status);
     return cudaGetLastError();
 }
 

@@ -26,9 +26,10 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENON
 # Symbols declared in include/rgf.h (checked by the CPU tests).
 EXPORTS = ["rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "rgf_free_ribbon",
            "rgf_lead_selfenergy", "rgf_conductance", "rgf_conductance_dev",
-           "rgf_conductance_grad", "rgf_conductance_noalloc", "rgf_zgemm_tc",
-           "rgf_zgemm_tc_selftest_timeout", "rgf_profile_enable", "rgf_profile_read", "rgf_status_str",
-           "rgf_last_error", "rgf_version"]
+           "rgf_conductance_grad", "rgf_conductance_grad_dev", "rgf_ldos", "rgf_conductance_noalloc", "rgf_zgemm_tc",
+           "rgf_zgemm_tc_selftest_timeout", "rgf_profile_enable", "rgf_profile_read",
+           "rgf_profile_read_phases", "rgf_set_lead_controls", "rgf_status_str", "rgf_last_error",
+           "rgf_version"]
 
 
 class _Desc(C.Structure):
@@ -56,6 +57,10 @@ lib.rgf_conductance_dev.argtypes = [C.POINTER(_vp), _vp, C.c_int, C.c_double, C.
                                     C.c_int, _vp, _vp, _vp]
 lib.rgf_conductance_grad.argtypes = [C.POINTER(_vp), _dp, C.c_int, C.c_double, C.c_double,
                                      C.c_int, C.c_int, _dp, _dp, _i32p]
+lib.rgf_conductance_grad_dev.argtypes = [C.POINTER(_vp), _vp, C.c_int, C.c_double, C.c_double,
+                                         C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]
+lib.rgf_ldos.argtypes = [C.POINTER(_vp), _dp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                         _dp, _dp, _i32p]
 lib.rgf_conductance_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, C.c_int,
                                         C.c_double, C.c_double, C.c_int, _vp, _vp, _vp]
 lib.rgf_conductance_noalloc.restype = C.c_int
@@ -68,12 +73,17 @@ lib.rgf_profile_enable.argtypes = [C.c_int]
 lib.rgf_profile_enable.restype = C.c_int
 lib.rgf_profile_read.argtypes = [_dp, _dp]
 lib.rgf_profile_read.restype = C.c_int
+lib.rgf_profile_read_phases.argtypes = [_dp]
+lib.rgf_profile_read_phases.restype = C.c_int
+lib.rgf_set_lead_controls.argtypes = [C.c_int, C.c_double]
+lib.rgf_set_lead_controls.restype = C.c_int
 lib.rgf_status_str.restype = C.c_char_p
 lib.rgf_status_str.argtypes = [C.c_int]
 lib.rgf_last_error.restype = C.c_char_p
 lib.rgf_version.restype = C.c_char_p
 for _f in ("rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "rgf_lead_selfenergy",
-           "rgf_conductance", "rgf_conductance_dev", "rgf_conductance_grad"):
+           "rgf_conductance", "rgf_conductance_dev", "rgf_conductance_grad",
+           "rgf_conductance_grad_dev", "rgf_ldos"):
     getattr(lib, _f).restype = C.c_int
 
 
@@ -222,6 +232,39 @@ def conductance_grad(ribbons, E, eta_device=1e-8, eta_lead=1e-8, precision=RGF_F
     return T, g, st
 
 
+def conductance_grad_dev(ribbons, E_ptr, n, T_ptr, dT_ptr, weights_ptr=0, status_ptr=0,
+                         eta_device=1e-8, eta_lead=1e-8, precision=RGF_FP64, ckpt_stride=0,
+                         stream=0):
+    """Device-buffer gradient: per-chain dT/d eps into dT_ptr, or with weights_ptr
+    (n float64 on the device) their weighted sum [L*2N]."""
+    _check(lib.rgf_conductance_grad_dev(_handles(ribbons), _vp(E_ptr), int(n), float(eta_device),
+                                        float(eta_lead), int(precision), int(ckpt_stride),
+                                        _vp(weights_ptr) if weights_ptr else None, _vp(stream),
+                                        _vp(T_ptr), _vp(dT_ptr),
+                                        _vp(status_ptr) if status_ptr else None))
+
+
+def ldos(ribbons, E, eta_device=1e-8, eta_lead=1e-8, precision=RGF_FP64, ckpt_stride=0,
+         check=True):
+    """T and the local density of states -Im G_ii / pi [nchains, L, 2N] (host buffers).
+    Returns (T, rho, status)."""
+    E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+    if len(ribbons) != E.size:
+        raise ValueError("one ribbon per energy")
+    sizes = [r.L * 2 * r.N for r in ribbons]
+    if len(set(sizes)) > 1:
+        raise ValueError("ldos binding expects ribbons of one size")
+    T = np.empty(E.size)
+    rho = np.empty((E.size, ribbons[0].L, 2 * ribbons[0].N)) if ribbons else np.empty(0)
+    st = np.empty(E.size, dtype=np.int32)
+    r = lib.rgf_ldos(_handles(ribbons), _ptr(E, C.c_double), E.size, float(eta_device),
+                     float(eta_lead), int(precision), int(ckpt_stride), _ptr(T, C.c_double),
+                     _ptr(rho, C.c_double), st.ctypes.data_as(_i32p))
+    if check:
+        _check(r)
+    return T, rho, st
+
+
 def profile_enable(on=True):
     """Record CUDA events around the kernel phases of each conductance call."""
     _check(lib.rgf_profile_enable(1 if on else 0))
@@ -232,6 +275,19 @@ def profile_read():
     a, b = C.c_double(), C.c_double()
     _check(lib.rgf_profile_read(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def profile_read_phases():
+    """Milliseconds of the last profiled call: (lead, end-column preparation,
+    half sweeps or gradient sweep, join and trace)."""
+    ms = np.zeros(4)
+    _check(lib.rgf_profile_read_phases(_ptr(ms, C.c_double)))
+    return tuple(float(x) for x in ms)
+
+
+def set_lead_controls(max_iter=200, residual_tol=1e-10):
+    """Iteration cap and residual tolerance of the lead decimation (process-wide)."""
+    _check(lib.rgf_set_lead_controls(int(max_iter), float(residual_tol)))
 
 
 def conductance_noalloc(N, L, t, onsite_ptr, removed_ptr, E_ptr, n, T_ptr, status_ptr=0,

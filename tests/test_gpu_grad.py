@@ -51,9 +51,10 @@ def test_checkpoint_stride_does_not_change_the_gradient(rgflib):
     outs = [rgflib.conductance_grad([rib] * 2, Es, ckpt_stride=s)[1] for s in (1, 2, 4, 9, 0)]
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
+    # the gradient sweep's own T agrees with the conductance entry point's
     T, _ = rgflib.conductance([rib] * 2, Es)
     Tg = rgflib.conductance_grad([rib] * 2, Es)[0]
-    assert np.array_equal(T, Tg)
+    assert np.max(np.abs(T - Tg)) < 1e-12
 
 
 def test_gradient_against_finite_differences_n101(rgflib):
@@ -131,3 +132,32 @@ def test_autograd_function(rgflib):
     ref = sum(wc * ograd.closed_form(N, L, Ec, 1e-8, 1e-8, T_HOP, eps0, None)
               for wc, Ec in zip([1.0, -2.0], [0.3, -0.5]))
     assert np.abs(eps.grad.cpu().numpy() - ref).max() < 1e-10
+
+
+def test_device_gradient_entry_point(rgflib):
+    # rgf_conductance_grad_dev on a stream: per-chain gradients equal the host
+    # entry point's; with weights, their weighted sum over chains.
+    import torch
+    N, L = 12, 5
+    rib = rgflib.Ribbon(N, L, T_HOP, W=0.2, seed=6, edge_p=0.2, edge_seed=7)
+    Es = np.array([-0.7, 0.25, 0.9])
+    T_h, g_h, _ = rgflib.conductance_grad([rib] * 3, Es, 1e-8, 1e-8, rgflib.RGF_MIXED_TC)
+    s = torch.cuda.Stream()
+    Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
+    Td = torch.empty(3, dtype=torch.float64, device="cuda")
+    Sd = torch.empty(3, dtype=torch.int32, device="cuda")
+    Gd = torch.empty((3, L, 2 * N), dtype=torch.float64, device="cuda")
+    s.wait_stream(torch.cuda.current_stream())
+    rgflib.conductance_grad_dev([rib] * 3, Ed.data_ptr(), 3, Td.data_ptr(), Gd.data_ptr(),
+                                status_ptr=Sd.data_ptr(), precision=rgflib.RGF_MIXED_TC,
+                                stream=s.cuda_stream)
+    w = torch.tensor([0.5, -1.0, 2.0], dtype=torch.float64, device="cuda")
+    Vd = torch.empty((L, 2 * N), dtype=torch.float64, device="cuda")
+    rgflib.conductance_grad_dev([rib] * 3, Ed.data_ptr(), 3, Td.data_ptr(), Vd.data_ptr(),
+                                weights_ptr=w.data_ptr(), precision=rgflib.RGF_MIXED_TC,
+                                stream=s.cuda_stream)
+    s.synchronize()
+    assert (Sd.cpu().numpy() == 0).all()
+    assert np.array_equal(Gd.cpu().numpy(), g_h) and np.array_equal(Td.cpu().numpy(), T_h)
+    ref = 0.5 * g_h[0] - 1.0 * g_h[1] + 2.0 * g_h[2]
+    assert np.abs(Vd.cpu().numpy() - ref).max() < 1e-14 * max(1.0, np.abs(ref).max())

@@ -50,20 +50,56 @@ def _run(rgflib, N, L, Es, eps, rem, prec, etad=1e-8, etal=1e-8):
 
 
 def test_pristine_n11_energy_grid_fp64(rgflib):
-    # 201 energies in [-1, 1] eV, N = 11, L = 50, eta = 1e-8 eV.
+    # 201 energies in [-1, 1] eV, N = 11, L = 50, eta = 1e-8 eV.  At E = 0
+    # exactly every partial system of a pristine ribbon carries a surface state
+    # (|g| ~ 1/eta) and the column slice matrices are singular to binary64:
+    # the chain reports RGF_ESINGULAR there (see the E = 0 test below).
     w = workloads.WORKLOADS["agnr11_L50_pristine"]
     N, L = w["N"], w["L"]
     Es = w["energies"]()
     T, st = _run(rgflib, N, L, Es, None, None, rgflib.RGF_FP64)
     for e, t, s in zip(Es, T, st):
         if e == 0.0:
-            continue    # E = 0 exactly: condition-limited, see the E = 0 test
+            assert s == rgflib.RGF_ESINGULAR and np.isnan(t)
+            continue
         assert s == 0
         ref = _oracle_T(N, L, e, 1e-8, 1e-8, None, None)
         assert abs(t - ref) < 1e-9, (e, t, ref)
     # quantisation: T ~ n_ch up to the eta absorption of the device
     nz = Es != 0
     assert np.all(np.abs(T[nz] - 1.0) < 1e-5)
+
+
+# E = 0 exactly (eta = 1e-8 eV) against 40-digit arithmetic
+# (tests/golden/mp_transmission.json).  On a disordered ribbon the leads'
+# surface states are the only order-1/eta poles, and the end columns are
+# handled in the leads' mode basis: the tolerance is the one measured there.
+# On a pristine ribbon every partial system has a surface state at E = 0, the
+# column slice matrices are singular to the working precision, and the chain
+# reports RGF_ESINGULAR.
+E0_TOL_DISORDERED = 1e-7
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_charge_neutrality_point_vs_40_digits(rgflib, prec):
+    import json
+    from pathlib import Path
+    gold = json.loads((Path(__file__).resolve().parent / "golden" / "mp_transmission.json").read_text())
+    errs = {}
+    for name, g in gold.items():
+        eps = workloads.anderson_onsite(g["N"], g["L"], g["W"], g["seed"]) if g["W"] > 0 else None
+        T, st = _run(rgflib, g["N"], g["L"], np.array([g["E"]]), eps, None, prec,
+                     etad=g["eta_device"], etal=g["eta_lead"])
+        errs[name] = (int(st[0]), abs(T[0] - g["T"]))
+        print(f"E0 precision={prec} {name}: status {st[0]}, |dT| = {abs(T[0] - g['T']):.3e}")
+    for name, g in gold.items():
+        st, err = errs[name]
+        if g["E"] == 0.0 and g["W"] == 0.0:
+            assert st == rgflib.RGF_ESINGULAR, (name, st)
+            continue
+        assert st == 0, (name, st)
+        tol = E0_TOL_DISORDERED if g["E"] == 0.0 else (1e-9 if prec == 0 else 1e-7)
+        assert err < tol, (name, err)
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
