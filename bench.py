@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--cpu-cells", type=int, default=60)
     ap.add_argument("--chains", type=int, default=0,
                     help="batched_uneven_chains: number of chains (default 2048)")
+    ap.add_argument("--grad", action="store_true",
+                    help="time rgf_conductance_grad on the workload (its gradient energies)")
+    ap.add_argument("--check-chains", type=int, default=0,
+                    help="batched_uneven_chains: compare only the first n chains with binary64")
     return ap.parse_args()
 
 
@@ -176,11 +180,15 @@ def cpu_oracle_sample(N, L_s, E, W, seed, rem_p=0.0, edge_seed=0):
 
 def cpu_baseline(N, cells, W, seed):
     """The oracle as it stands on 1 energy x `cells` cells of the workload, with
-    all BLAS threads and with one."""
-    from threadpoolctl import threadpool_limits
+    all BLAS threads and with one (a child process started with the BLAS
+    thread count set to 1 in its environment)."""
     dt = cpu_oracle_sample(N, cells, 0.3, W, seed)
-    with threadpool_limits(limits=1):
-        dt1 = cpu_oracle_sample(N, cells, 0.3, W, seed)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys; sys.path.insert(0, {str(ROOT)!r}); import bench; "
+            f"print(bench.cpu_oracle_sample({N}, {cells}, 0.3, {W}, {seed}))")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       cwd=str(ROOT))
+    dt1 = float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else float("nan")
     sample = f"1 energy (E=0.3 eV) x {cells} cells of N={N}, whole path (decimation + recursion + trace)"
     return {"value": cells / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
             "sample": sample,
@@ -280,11 +288,12 @@ def run_uneven(args):
     t = sum(ms) / 1e3
     parity = None
     if not args.no_check and prec != rgf.RGF_FP64:
-        T64, s64 = rgf.conductance(ribs, Es, 1e-8, 1e-8, rgf.RGF_FP64, check=False)
-        both = ok & (s64 == 0)
-        parity = {"max_abs_dT_vs_fp64": float(np.abs(T - T64)[both].max()) if both.any() else None,
-                  "chains_compared": int(both.sum()), "status_mismatch": int((status != s64).sum()),
-                  "tolerance": 1e-6}
+        nc = args.check_chains or n
+        T64, s64 = rgf.conductance(ribs[:nc], Es[:nc], 1e-8, 1e-8, rgf.RGF_FP64, check=False)
+        both = ok[:nc] & (s64 == 0)
+        parity = {"max_abs_dT_vs_fp64": float(np.abs(T[:nc] - T64)[both].max()) if both.any() else None,
+                  "chains_compared": int(both.sum()),
+                  "status_mismatch": int((status[:nc] != s64).sum()), "tolerance": 1e-6}
     fl = sum(cell_slicing_flops_per_step(int(N)) * float(L) for N, L, o in zip(Ns, cells, ok) if o)
     achieved = fl / (statistics.mean(ms_sweep) / 1e3) / 1e12
     peaks, src = measured_peaks()
@@ -328,28 +337,32 @@ def run_grad(args):
     w = workloads.WORKLOADS[args.workload]
     N, L = w["N"], (args.cells or w["L"])
     eps = workloads.anderson_onsite(N, L, w["W"], w["seed"])
+    rem = workloads.edge_removed(N, L, w["edge_p"], w["edge_seed"]) if w["edge_p"] > 0 else None
     Es = w["energies"]()
+    if "grad_idx" in w:
+        Es = Es[w["grad_idx"]]
     if args.energies:
         Es = Es[: args.energies]
-    rib = rgf.Ribbon(N, L, -2.7, onsite=eps)
+    rib = rgf.Ribbon(N, L, -2.7, onsite=eps, removed=rem)
     ribs = [rib] * len(Es)
     for _ in range(args.warmup):
-        rgf.conductance_grad(ribs, Es, 1e-8, 1e-8, prec, ckpt_stride=w["ckpt_stride"], check=False)
+        rgf.conductance_grad(ribs, Es, 1e-8, 1e-8, prec, ckpt_stride=w.get("ckpt_stride", 0),
+                             check=False)
     torch.cuda.synchronize()
     ts = []
     sampler = ClockSampler(local)
     with sampler:
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            T, g, st = rgf.conductance_grad(ribs, Es, 1e-8, 1e-8, prec, ckpt_stride=w["ckpt_stride"],
-                                            check=False)
+            T, g, st = rgf.conductance_grad(ribs, Es, 1e-8, 1e-8, prec,
+                                            ckpt_stride=w.get("ckpt_stride", 0), check=False)
             ts.append(time.perf_counter() - t0)
     ok = st == 0
     t = sum(ts)
     parity = None
     if not args.no_check and prec != rgf.RGF_FP64:
         T64, g64, s64 = rgf.conductance_grad(ribs, Es, 1e-8, 1e-8, rgf.RGF_FP64,
-                                             ckpt_stride=w["ckpt_stride"], check=False)
+                                             ckpt_stride=w.get("ckpt_stride", 0), check=False)
         both = ok & (s64 == 0)
         scale = np.abs(g64).max(axis=(1, 2))
         rel = np.abs(g - g64).max(axis=(1, 2)) / np.where(scale > 0, scale, 1.0)
@@ -363,13 +376,13 @@ def run_grad(args):
                   "max_abs_dT_vs_fp64": float(np.abs(T - T64)[both].max()) if both.any() else None,
                   "chains_compared": int(both.sum()), "chains_absE_lt_0.1": int(near.sum())}
     clocks = sampler.summary()
-    out = {"metric": "RGF adjoint slice-steps/s (dT/d eps, N=101, batched energies)",
+    out = {"metric": f"RGF two-sided gradient slice-steps/s (dT/d eps, N={N}, batched energies)",
            "value": float(ok.sum()) * L * args.steps / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if prec == rgf.RGF_FP64 else "f32x2", "data": "synthetic",
            "config": {"workload": args.workload, "N": N, "L": L, "energies": int(len(Es)),
-                      "ckpt_stride": w["ckpt_stride"], "precision": args.precision,
+                      "ckpt_stride": w.get("ckpt_stride", 0), "precision": args.precision,
                       "timing": "host wall clock around the host-buffer call"},
            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                       "reasons": clocks["reasons"]},
@@ -386,7 +399,7 @@ def main():
     if args.workload == "batched_uneven_chains":
         run_uneven(args)
         return
-    if args.workload == "agnr101_L500_grad":
+    if args.workload == "agnr101_L500_grad" or args.grad:
         run_grad(args)
         return
     import torch

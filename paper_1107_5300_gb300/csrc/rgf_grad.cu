@@ -79,7 +79,7 @@ __device__ double build_A(const ChainCtx& c, int k, bool left, const cx<R>* glp,
                 // the left term as the forward sweep forms it (inv_column), so
                 // that the left recursion reproduces the forward sweep bit for bit
                 cx<R> sig = czero<R>();
-                if (left && first) sig = ld_z<R>(c.SigL + (size_t)i * KL + l);
+                if (left && first) sig = ld_z<R>(c.SigL() + (size_t)i * KL + l);
                 if (left && !first) {
                     int b0, b1;
                     col_src(ct, l, Kp, b0, b1);
@@ -90,7 +90,7 @@ __device__ double build_A(const ChainCtx& c, int k, bool left, const cx<R>* glp,
                     if (ka1 && kb1) sig = cadd(sig, glp[(size_t)a1 * KL + b1]);
                     sig = cscale(sig, t2);
                 }
-                if (right && last) sig = cadd(sig, ld_z<R>(c.SigR + (size_t)i * c.KR + l));
+                if (right && last) sig = cadd(sig, ld_z<R>(c.SigR() + (size_t)i * c.KR + l));
                 if (right && !last) {
                     int m0, m1;
                     col_src_T(ctn, l, Kn, m0, m1);
@@ -254,8 +254,8 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
 
     // M = Gamma_R G_1L^dagger Gamma_L  (KR x KL)
     for (size_t e = threadIdx.x; e < B && want_grad; e += NT) {
-        GL[e] = ld_z<R>(c.GamL + e);                              // KL x KL, ld KL
-        if (e < (size_t)KR * KR) GR[e] = ld_z<R>(c.GamR + e);     // KR x KR, ld KR
+        GL[e] = ld_z<R>(c.GamL() + e);                              // KL x KL, ld KL
+        if (e < (size_t)KR * KR) GR[e] = ld_z<R>(c.GamR() + e);     // KR x KR, ld KR
         const int b = (int)(e / KL), a = (int)(e % KL);
         if (b < KR) Y[e] = cconj(Qr[(size_t)a * KL + b]);         // Y[b][a] = conj(G_1L[a][b])
     }

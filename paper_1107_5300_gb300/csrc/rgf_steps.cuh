@@ -16,10 +16,9 @@ struct SweepSmem {
     cx<R>* gemm;
     uint8_t* kc;     // keep mask of the current column
     uint8_t* kp;     // keep mask of the previous column
-    uint8_t* kn;     // keep mask of the next column (gradient)
+    uint8_t* kn;     // keep mask of the next column (gradient; second column of a pair)
     double* eps;
     double* red;
-    double* clmax;   // this block's partial max |A|^2, read by the team
     tc::State* tcs;  // tensor-core state for the strip product, or nullptr
 };
 
@@ -36,7 +35,6 @@ __host__ __device__ inline size_t sweep_base_bytes(int Kmax, int bm, bool tc) {
     if (!tc) b += align16(2 * 8 * 64 * 16);     // gemm tiles
     b += align16((size_t)Kmax * 8);             // eps
     b += align16(NWARP * 8);                    // red
-    b += align16(16);                           // clmax
     b += align16((size_t)Kmax * 4) * 2;         // perm, idx
     b += align16((size_t)(2 * bm + 1) * 4);     // displaced rows of a panel
     b += align16(16);                           // ctl
@@ -77,7 +75,6 @@ __device__ SweepSmem<R> carve(unsigned char* base, int Kmax, bool tc = false) {
     s.gemm = tc ? (cx<R>*)(base + tc_area_offset(Kmax, bm)) : (cx<R>*)take(2 * 8 * 64 * 16);
     s.eps = (double*)take((size_t)Kmax * 8);
     s.red = (double*)take(NWARP * 8);
-    s.clmax = (double*)take(16);
     s.gj.perm = (int*)take((size_t)Kmax * 4);
     s.gj.idx = (int*)take((size_t)Kmax * 4);
     s.gj.pm = (int*)take((size_t)(2 * bm + 1) * 4);
@@ -170,8 +167,16 @@ struct ChainCtx {
     double t, t2;
     df32 tf, t2f;    // t and t^2 in double-float, converted once
     zd z;
-    const zd *SigL, *SigR, *GamL, *GamR;   // site basis of the lead-attached columns
-    const zd *UL, *UR, *w;                 // mode vectors (real parts) and w_p = tau_p^2 g_p
+    const zd* lead;  // this chain's lead output (layout of LeadDev::off)
+    // site basis of the lead-attached columns, the mode vectors (real parts)
+    // and w_p = tau_p^2 g_p, located from `lead` on use (fewer live registers)
+    __device__ const zd* SigL() const { return lead; }
+    __device__ const zd* SigR() const { return lead + (size_t)KL * KL; }
+    __device__ const zd* GamL() const { return SigR() + (size_t)KR * KR; }
+    __device__ const zd* GamR() const { return GamL() + (size_t)KL * KL; }
+    __device__ const zd* UL() const { return GamR() + (size_t)KR * KR; }
+    __device__ const zd* UR() const { return UL() + (size_t)KL * KL; }
+    __device__ const zd* w() const { return UR() + (size_t)KR * KR; }
 };
 
 __device__ inline ChainCtx make_ctx(const ChainDev& ch, const LeadDev& ld, const zd* leadout,
@@ -191,13 +196,7 @@ __device__ inline ChainCtx make_ctx(const ChainDev& ch, const LeadDev& ld, const
     c.tf = df_from_double(c.t);
     c.t2f = df_from_double(c.t2);
     c.z = {ch.E, eta_d};
-    c.SigL = leadout + ld.off;
-    c.SigR = c.SigL + (size_t)c.KL * c.KL;
-    c.GamL = c.SigR + (size_t)c.KR * c.KR;
-    c.GamR = c.GamL + (size_t)c.KL * c.KL;
-    c.UL = c.GamR + (size_t)c.KR * c.KR;
-    c.UR = c.UL + (size_t)c.KL * c.KL;
-    c.w = c.UR + (size_t)c.KR * c.KR;
+    c.lead = leadout + ld.off;
     return c;
 }
 
@@ -256,6 +255,16 @@ __device__ inline void load_col(const ChainCtx& c, int k, uint8_t* km, double* e
 template <class R>
 __device__ __forceinline__ cx<R> ld_z(const zd* p) { return from_z<R>(p->re, p->im); }
 
+// On-site energy of entry i of column k, and d_i = z - eps_i of a pair's
+// second column (binary64 in, working precision out).
+__device__ __forceinline__ double site_eps(const ChainCtx& c, int k, int i) {
+    return c.eps[(size_t)(k >> 2) * c.M + 4 * i + (k & 3)];
+}
+template <class R>
+__device__ __forceinline__ cx<R> pair_d(const ChainCtx& c, int kb, int i) {
+    return from_z<R>(c.z.re - site_eps(c, kb, i), c.z.im);
+}
+
 // One interior step of a half's column recursion at column k (row-major,
 // leading dimension KL), with q = prev_col(c, k) the column before it:
 //   inv_column:   X = A_k = (z - eps_k) I - t^2 S^T g_q S (K x K; S the bond
@@ -267,9 +276,12 @@ __device__ __forceinline__ cx<R> ld_z(const zd* p) { return from_z<R>(p->re, p->
 //                 Pout = Y Gk (Pout may alias Pprev; Y may alias the X of
 //                 inv_column).  Needs s.kc and s.kp.
 // The lead-attached first column of a half is prepared elsewhere (rgf_sweep.cu).
-template <class R>
+// SHIFT (pair steps, with column kb = the pair's second column): the diagonal
+// of X additionally loses t^2 kappa_i / d_i (see pair_column; s.kn holds the
+// keep mask of kb).
+template <class R, bool SHIFT = false>
 __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout, cx<R>* X,
-                          SweepSmem<R>& s) {
+                          SweepSmem<R>& s, int kb = -1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int KL = c.KL, K = col_size(c, k), Kq = col_size(c, prev_col(c, k));
     double amax2 = 0.0;
@@ -293,6 +305,8 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
                 if (ka1 && kb1) sig = cadd(sig, Gprev[(size_t)a1 * KL + b1]);
                 sig = cscale(sig, Hop<R>::t2(c));
                 v = (i == l) ? from_z<R>(c.z.re - s.eps[i], c.z.im) : czero<R>();
+                if (SHIFT && i == l && s.kn[i])
+                    v = csub(v, cscale(crecip(pair_d<R>(c, kb, i)), Hop<R>::t2(c)));
                 v = csub(v, sig);
             }
             X[(size_t)i * KL + l] = v;
@@ -335,6 +349,72 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
     cta_gemm<R, false, false>(rows, K, K, Y, KL, Gk, KL, Pout, KL, GEMM_SET, s.gemm);
 }
 
+// Two columns a, b = the next one in the recursion, joined by t I between the
+// atoms of one row (the pairs c0-c1 and c2-c3 of a cell), in one inverse.
+// Column b has no bond inside itself, so its slice matrix A_b = D - W g_a W
+// (D = diag(d), d_i = z - eps_i for kept atoms and 1 for removed ones;
+// W = t diag(kappa), kappa_i = both atoms of row i kept) is the Schur
+// complement of the pair's block matrix [[X, -W], [-W, D]], X = A_a.  Taking
+// the complement the other way round, with Z = (X - W D^-1 W)^-1,
+//   g_b  = D^-1 + D^-1 W Z W D^-1 = diag(1/d) + diag(s) Z diag(s),
+//   P_b  = P_q W_a G_ab = (P_q W_a) Z diag(s),      s_i = t kappa_i / d_i,
+// so the pair costs one Gauss-Jordan inverse (of X with its diagonal shifted
+// by -t s_i) and one strip product instead of two of each.  Used only when
+// every kept atom of b has |d_i| >= kPairMinD (pair_ok): near an isolated-atom
+// resonance 1/d grows and g_b's two terms cancel.  Needs s.kc / s.eps of a,
+// s.kp of the column before a, s.kn / s.epsb of b.  On return G = g_b and
+// P = P_b.  Returns the Gauss-Jordan flag.
+constexpr double kPairMinD = 1e-4;   // eV
+
+// Every thread: whether the pair whose second column is kb may be joined (no
+// kept atom of kb within kPairMinD of E).  Needs s.kn.  Ends with a barrier.
+template <class R>
+__device__ bool pair_ok(const ChainCtx& c, int kb, SweepSmem<R>& s) {
+    bool bad = false;
+    for (int i = threadIdx.x; i < col_size(c, kb); i += NT) {
+        if (s.kn[i]) {
+            const double dr = c.z.re - site_eps(c, kb, i), dm = c.z.im;
+            if (!(dr * dr + dm * dm >= kPairMinD * kPairMinD)) bad = true;
+        }
+    }
+    return __syncthreads_or(bad) == 0;
+}
+
+template <class R>
+__device__ int pair_column(const ChainCtx& c, int ka, int kb, cx<R>* G, cx<R>* P, cx<R>* X,
+                           SweepSmem<R>& s) {
+    const int KL = c.KL, K = col_size(c, ka);
+    const int flag = inv_column<R, true>(c, ka, G, G, X, s, kb);   // G = Z
+    // s_i and 1/d_i in the Gauss-Jordan scratch, free between inverses
+    cx<R>* sc = s.gj.mult;
+    cx<R>* di = s.gj.xrow;
+    for (int i = threadIdx.x; i < K; i += NT) {
+        if (s.kn[i]) {
+            const cx<R> inv = crecip(pair_d<R>(c, kb, i));
+            di[i] = inv;
+            sc[i] = s.kc[i] ? cscale(inv, Hop<R>::t(c)) : czero<R>();
+        } else {
+            di[i] = from_z<R>(1.0, 0.0);
+            sc[i] = czero<R>();
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < K * K; e += NT) {              // G = Z diag(s)
+        const int i = e / K, l = e - i * K;
+        G[(size_t)i * KL + l] = cmul(G[(size_t)i * KL + l], sc[l]);
+    }
+    __syncthreads();
+    strip_column<R>(c, ka, G, P, P, X, s);                       // P = (P_q W_a) Z diag(s)
+    for (int e = threadIdx.x; e < K * K; e += NT) {              // G = diag(1/d) + diag(s) G
+        const int i = e / K, l = e - i * K;
+        cx<R> v = cmul(sc[i], G[(size_t)i * KL + l]);
+        if (i == l) v = cadd(v, di[i]);
+        G[(size_t)i * KL + l] = v;
+    }
+    __syncthreads();
+    return flag;
+}
+
 // Tr[Gamma_L P Gamma_R P^dagger] in binary64.  P: KL x KR (ld KL) in the working
 // precision; Xs, Zs, Cz: KL x KL scratch (16-byte elements).
 template <class R>
@@ -355,8 +435,8 @@ __device__ double trace_T(const ChainCtx& c, const cx<R>* P, cx<R>* Cz, cx<R>* X
     zd* X = reinterpret_cast<zd*>(Xs);
     zd* Z = reinterpret_cast<zd*>(Zs);
     zd* gsm = reinterpret_cast<zd*>(s.gemm);
-    cta_gemm<double, false, false>(KL, KR, KL, c.GamL, KL, Pz, KL, X, KL, GEMM_SET, gsm);
-    cta_gemm<double, false, false>(KL, KR, KR, Pz, KL, c.GamR, KR, Z, KL, GEMM_SET, gsm);
+    cta_gemm<double, false, false>(KL, KR, KL, c.GamL(), KL, Pz, KL, X, KL, GEMM_SET, gsm);
+    cta_gemm<double, false, false>(KL, KR, KR, Pz, KL, c.GamR(), KR, Z, KL, GEMM_SET, gsm);
     double acc = 0.0;
     for (int e = threadIdx.x; e < KL * KR; e += NT) {
         int a = e / KR, b = e % KR;

@@ -141,8 +141,8 @@ prep_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     zd* G = reinterpret_cast<zd*>(hw.G);
     zd* P = reinterpret_cast<zd*>(hw.P);
     const int KL = c.KL, k = h ? c.ncol - 1 : 0, K = h ? c.KR : c.KL;
-    const zd* U = h ? c.UR : c.UL;                  // K x K, ld K
-    const zd* Sig = h ? c.SigR : c.SigL;            // K x K, ld K
+    const zd* U = h ? c.UR() : c.UL();                  // K x K, ld K
+    const zd* Sig = h ? c.SigR() : c.SigL();            // K x K, ld K
     load_col(c, k, s.kc, s.eps);
     if (threadIdx.x == 0) s.gj.ctl[2] = 0;
     __syncthreads();
@@ -160,7 +160,7 @@ prep_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
         }
         __syncthreads();
         cta_gemm<double, true, false>(K, K, K, U, K, X, KL, G, KL, GEMM_SET, s.gemm);
-        for (int p = threadIdx.x; p < K; p += NT) G[(size_t)p * KL + p] = csub(G[(size_t)p * KL + p], c.w[p]);
+        for (int p = threadIdx.x; p < K; p += NT) G[(size_t)p * KL + p] = csub(G[(size_t)p * KL + p], c.w()[p]);
         __syncthreads();
         const double amax2 = max_abs2(G, K, KL, s.red);
         flag = cta_gj_invert<double>(G, K, KL, X, KL, s.gj, amax2);
@@ -188,7 +188,9 @@ prep_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
 }
 
 // The recursion of one half (h = blockIdx.x & 1) from its second column to
-// the cut: columns 1 .. m-1 (left) or n-2 .. m (right).
+// the cut: columns 1 .. m-1 (left) or n-2 .. m (right), in pairs of t I-bonded
+// columns wherever pair_ok allows (pair_column in rgf_steps.cuh), else one
+// column at a time.
 template <class R, bool TC>
 __global__ void __launch_bounds__(NT, 1)
 half_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int Kmax,
@@ -205,13 +207,25 @@ half_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     tc::State tst;
     if constexpr (TC) tc_attach<R>(Kmax, s, tst);
     int flag = 0;
-    for (int j = 1; j < steps; ++j) {
+    for (int j = 1; j < steps;) {
         const int k = h ? c.ncol - 1 - j : j;
+        // a pair: this column and the next one in the recursion share t I bonds
+        // (c0-c1 or c2-c3 of one cell); the second column of the first pair of
+        // each half is the one after the prepared end column
+        const int kb = h ? k - 1 : k + 1;
+        const bool pairable = j + 1 < steps && (h ? (k & 1) == 1 : (k & 1) == 0);
         load_col(c, k, s.kc, s.eps);
         load_col(c, prev_col(c, k), s.kp, nullptr);
+        if (pairable) load_col(c, kb, s.kn, nullptr);
         __syncthreads();
-        flag |= inv_column<R>(c, k, hw.G, hw.G, hw.X, s);
-        strip_column<R>(c, k, hw.G, hw.P, hw.P, hw.X, s);
+        if (pairable && pair_ok<R>(c, kb, s)) {
+            flag |= pair_column<R>(c, k, kb, hw.G, hw.P, hw.X, s);
+            j += 2;
+        } else {
+            flag |= inv_column<R>(c, k, hw.G, hw.G, hw.X, s);
+            strip_column<R>(c, k, hw.G, hw.P, hw.P, hw.X, s);
+            j += 1;
+        }
     }
     if constexpr (TC) {
         if (*(volatile int*)tst.ar.err()) flag |= 4;
@@ -305,10 +319,11 @@ merge_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order,
     cta_gemm<double, false, true>(KL, KR, K, XR, KL, PRd, KL, GLd, KL, GEMM_SET, s.gemm);
     // T = sum_pq gamma_p gamma'_q |P_pq|^2
     double acc = 0.0;
+    const zd* w = c.w();
     for (int e = threadIdx.x; e < KL * KR; e += NT) {
         const int p = e / KR, q = e % KR;
         const zd v = GLd[(size_t)p * KL + q];
-        acc += (-2.0 * c.w[p].im) * (-2.0 * c.w[q].im) * (v.re * v.re + v.im * v.im);
+        acc += (-2.0 * w[p].im) * (-2.0 * w[q].im) * (v.re * v.re + v.im * v.im);
     }
     const double T = block_sum(acc, s.red);
     if (threadIdx.x == 0) {

@@ -1,11 +1,17 @@
-"""The bench workload at its full size, in the launch the benchmark times (69
-chains, two-block clusters): the W = 30 nm ribbon (N = 245, M = 490 orbitals
-per cell), L = 4000 cells, Anderson disorder +-0.25 eV, 69 energies.  The
-oracle cannot sweep 4000 cells of this ribbon in a test, so every chain is
-checked against the binary64 GPU path (|dT| <= 1e-6 per energy, the target of
-the mixed-precision paths) and against the bounds 0 <= T <= n_ch(E); both
-mixed paths must report the same status as binary64 (E = 0 exactly is
-condition-limited and is flagged RGF_EBOUNDS rather than returned)."""
+"""The bench ribbon (W = 30 nm: N = 245, M = 490 orbitals per cell, Anderson
+disorder +-0.25 eV from seed 1, 69 energies) against the oracle.
+
+* In the launch configuration the benchmark times (69 chains in one call), on
+  the first 4 cells of the ribbon: every energy against oracle values
+  (tests/golden/agnr245_golden.json, written by make_agnr245_golden.py from
+  the oracle alone).
+* At the full size (L = 4000 cells): six energies (-0.5 eV, 0.294 eV, +-1 meV,
+  +5 meV and E = 0) against oracle values, and every energy of the mixed paths
+  against the binary64 GPU path (|dT| <= 1e-6, the target of the mixed
+  paths)."""
+import json
+from pathlib import Path
+
 import numpy as np
 import pytest
 
@@ -13,28 +19,73 @@ import workloads
 from oracle import bands
 
 pytestmark = pytest.mark.gpu
+GOLD = json.loads((Path(__file__).resolve().parent / "golden" / "agnr245_golden.json").read_text())
+W = workloads.WORKLOADS["agnr245_L4000_anderson"]
+
+# |dT| per energy.  binary64: the paper's CPU accuracy (better than 1e-9);
+# mixed paths: 1e-7 on the 4-cell ribbon, 1e-6 (the target) on 4000 cells.
+# E = 0 exactly: the oracle's own value there (mode-basis end slices) is
+# condition-limited; the bound is the one measured on small disordered
+# ribbons against 40 digits (tests/test_gpu_parity.py).
+TOL = {(0, 4): 1e-9, (1, 4): 1e-7, (2, 4): 1e-7, (0, 4000): 1e-9, (1, 4000): 1e-6, (2, 4000): 1e-6}
+TOL_E0 = 1e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_bench_launch_configuration_vs_oracle(rgflib, prec):
+    N = W["N"]
+    Es = W["energies"]()
+    eps = workloads.anderson_onsite(N, 4, W["W"], W["seed"])
+    rib = rgflib.Ribbon(N, 4, -2.7, onsite=eps)
+    T, st = rgflib.conductance([rib] * len(Es), Es, 1e-8, 1e-8, prec, check=False)
+    assert (st == 0).all(), st
+    g = GOLD["L4"]
+    d = np.abs(T[g["energy_index"]] - np.array(g["T"]))
+    print(f"L4 precision={prec}: max |dT| = {d.max():.3e} over {d.size} energies")
+    assert d.max() < TOL[(prec, 4)], d.max()
+    e0 = GOLD["L4_E0"]
+    print(f"L4 precision={prec}: |dT(E=0)| = {abs(T[e0['energy_index']] - e0['T']):.3e}")
+    assert abs(T[e0["energy_index"]] - e0["T"]) < TOL_E0
 
 
 @pytest.fixture(scope="module")
-def bench_case(rgflib):
-    w = workloads.WORKLOADS["agnr245_L4000_anderson"]
-    N, L = w["N"], w["L"]
-    eps = workloads.anderson_onsite(N, L, w["W"], w["seed"])
-    Es = w["energies"]()
-    rib = rgflib.Ribbon(N, L, -2.7, onsite=eps)
-    T64, s64 = rgflib.conductance([rib] * len(Es), Es, 1e-8, 1e-8, rgflib.RGF_FP64, check=False)
-    return rib, N, Es, T64, s64
+def full_ribbon(rgflib):
+    N, L = W["N"], W["L"]
+    eps = workloads.anderson_onsite(N, L, W["W"], W["seed"])
+    return rgflib.Ribbon(N, L, -2.7, onsite=eps)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_full_size_vs_oracle(rgflib, full_ribbon, prec):
+    g, e0 = GOLD["L4000"], GOLD["L4000_E0"]
+    Es = np.array(g["E"] + [e0["E"]])
+    ref = np.array(g["T"] + [e0["T"]])
+    T, st = rgflib.conductance([full_ribbon] * len(Es), Es, 1e-8, 1e-8, prec, check=False)
+    assert (st == 0).all(), st
+    d = np.abs(T - ref)
+    print(f"L4000 precision={prec}: |dT| = {np.array2string(d, precision=3)} at E = {Es}")
+    assert d[:-1].max() < TOL[(prec, 4000)], d
+    assert d[-1] < TOL_E0, d
+
+
+@pytest.fixture(scope="module")
+def bench_fp64(rgflib, full_ribbon):
+    Es = W["energies"]()
+    T64, s64 = rgflib.conductance([full_ribbon] * len(Es), Es, 1e-8, 1e-8, rgflib.RGF_FP64,
+                                  check=False)
+    return Es, T64, s64
+
+
+@pytest.mark.slow
 @pytest.mark.parametrize("prec", [1, 2])
-def test_mixed_paths_match_binary64_at_full_size(rgflib, bench_case, prec):
-    rib, N, Es, T64, s64 = bench_case
-    T, st = rgflib.conductance([rib] * len(Es), Es, 1e-8, 1e-8, prec, check=False)
-    assert np.array_equal(st, s64)
-    ok = s64 == 0
-    assert ok.sum() >= len(Es) - 1                      # only E = 0 may be flagged
-    assert np.all(s64[Es != 0.0] == 0)
-    d = np.abs(T[ok] - T64[ok])
+def test_mixed_paths_match_binary64_at_full_size(rgflib, full_ribbon, bench_fp64, prec):
+    Es, T64, s64 = bench_fp64
+    T, st = rgflib.conductance([full_ribbon] * len(Es), Es, 1e-8, 1e-8, prec, check=False)
+    assert (s64 == 0).all() and (st == 0).all()
+    d = np.abs(T - T64)
+    print(f"L4000 precision={prec} vs binary64: max |dT| = {d.max():.3e}, "
+          f"at |E| <= 5 meV {d[np.abs(Es) <= 5e-3].max():.3e}")
     assert d.max() <= 1e-6, d.max()
-    nch = np.array([bands.channels_closed_form(N, e) for e in Es[ok]])
-    assert np.all(T64[ok] >= -1e-9) and np.all(T64[ok] <= nch + 1e-9)
+    nch = np.array([bands.channels_closed_form(W["N"], e) for e in Es])
+    assert np.all(T64 >= -1e-9) and np.all(T64 <= nch + 1e-9)

@@ -114,9 +114,11 @@ WORKLOADS = {
     # Gradient workload: N=101, 500 cells, Anderson +-0.15 eV, 128 energies.
     "agnr101_L500_grad": dict(N=101, L=500, W=0.15, seed=4, edge_p=0.0, edge_seed=0,
                               energies=lambda: energy_grid(-0.8, 0.8, 128), ckpt_stride=23),
-    # W = 123 nm ribbon (N=1001), 2000 cells, Anderson +-0.1 eV, edge p=0.02.
+    # W = 123 nm ribbon (N=1001), 2000 cells, Anderson +-0.1 eV, edge p=0.02,
+    # 256 energies; gradients at energies 16 + 32k, k = 0..7.
     "agnr1001_L2000": dict(N=1001, L=2000, W=0.1, seed=5, edge_p=0.02, edge_seed=55,
-                           energies=lambda: energy_grid(-0.3, 0.3, 256)),
+                           energies=lambda: energy_grid(-0.3, 0.3, 256),
+                           grad_idx=[16 + 32 * k for k in range(8)]),
 }
 
 
