@@ -276,10 +276,10 @@ __device__ __forceinline__ cx<R> pair_d(const ChainCtx& c, int kb, int i) {
 //                 Pout = Y Gk (Pout may alias Pprev; Y may alias the X of
 //                 inv_column).  Needs s.kc and s.kp.
 // The lead-attached first column of a half is prepared elsewhere (rgf_sweep.cu).
-// SHIFT (pair steps, with column kb = the pair's second column): the diagonal
-// of X additionally loses t^2 kappa_i / d_i (see pair_column; s.kn holds the
-// keep mask of kb).
-template <class R, bool SHIFT = false>
+// kb >= 0 (pair steps, kb = the pair's second column): the diagonal of X
+// additionally loses t^2 kappa_i / d_i (see pair_scales; s.kn holds the keep
+// mask of kb).
+template <class R>
 __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout, cx<R>* X,
                           SweepSmem<R>& s, int kb = -1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -305,7 +305,7 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
                 if (ka1 && kb1) sig = cadd(sig, Gprev[(size_t)a1 * KL + b1]);
                 sig = cscale(sig, Hop<R>::t2(c));
                 v = (i == l) ? from_z<R>(c.z.re - s.eps[i], c.z.im) : czero<R>();
-                if (SHIFT && i == l && s.kn[i])
+                if (kb >= 0 && i == l && s.kn[i])
                     v = csub(v, cscale(crecip(pair_d<R>(c, kb, i)), Hop<R>::t2(c)));
                 v = csub(v, sig);
             }
@@ -380,12 +380,14 @@ __device__ bool pair_ok(const ChainCtx& c, int kb, SweepSmem<R>& s) {
     return __syncthreads_or(bad) == 0;
 }
 
+// The two elementwise halves of a pair step around the strip product (the
+// inverse of the shifted A_a is inv_column with kb): pair_scales sets up
+// s_i and 1/d_i in the Gauss-Jordan scratch (free between inverses) and
+// scales G = Z into Z diag(s); pair_finish turns it into
+// g_b = diag(1/d) + diag(s) Z diag(s).  Every thread; barriers at the end.
 template <class R>
-__device__ int pair_column(const ChainCtx& c, int ka, int kb, cx<R>* G, cx<R>* P, cx<R>* X,
-                           SweepSmem<R>& s) {
+__device__ void pair_scales(const ChainCtx& c, int ka, int kb, cx<R>* G, SweepSmem<R>& s) {
     const int KL = c.KL, K = col_size(c, ka);
-    const int flag = inv_column<R, true>(c, ka, G, G, X, s, kb);   // G = Z
-    // s_i and 1/d_i in the Gauss-Jordan scratch, free between inverses
     cx<R>* sc = s.gj.mult;
     cx<R>* di = s.gj.xrow;
     for (int i = threadIdx.x; i < K; i += NT) {
@@ -399,20 +401,25 @@ __device__ int pair_column(const ChainCtx& c, int ka, int kb, cx<R>* G, cx<R>* P
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < K * K; e += NT) {              // G = Z diag(s)
+    for (int e = threadIdx.x; e < K * K; e += NT) {
         const int i = e / K, l = e - i * K;
         G[(size_t)i * KL + l] = cmul(G[(size_t)i * KL + l], sc[l]);
     }
     __syncthreads();
-    strip_column<R>(c, ka, G, P, P, X, s);                       // P = (P_q W_a) Z diag(s)
-    for (int e = threadIdx.x; e < K * K; e += NT) {              // G = diag(1/d) + diag(s) G
+}
+
+template <class R>
+__device__ void pair_finish(const ChainCtx& c, int ka, cx<R>* G, SweepSmem<R>& s) {
+    const int KL = c.KL, K = col_size(c, ka);
+    const cx<R>* sc = s.gj.mult;
+    const cx<R>* di = s.gj.xrow;
+    for (int e = threadIdx.x; e < K * K; e += NT) {
         const int i = e / K, l = e - i * K;
         cx<R> v = cmul(sc[i], G[(size_t)i * KL + l]);
         if (i == l) v = cadd(v, di[i]);
         G[(size_t)i * KL + l] = v;
     }
     __syncthreads();
-    return flag;
 }
 
 // Tr[Gamma_L P Gamma_R P^dagger] in binary64.  P: KL x KR (ld KL) in the working

@@ -218,14 +218,13 @@ half_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
         load_col(c, prev_col(c, k), s.kp, nullptr);
         if (pairable) load_col(c, kb, s.kn, nullptr);
         __syncthreads();
-        if (pairable && pair_ok<R>(c, kb, s)) {
-            flag |= pair_column<R>(c, k, kb, hw.G, hw.P, hw.X, s);
-            j += 2;
-        } else {
-            flag |= inv_column<R>(c, k, hw.G, hw.G, hw.X, s);
-            strip_column<R>(c, k, hw.G, hw.P, hw.P, hw.X, s);
-            j += 1;
-        }
+        const bool pair = pairable && pair_ok<R>(c, kb, s);
+        // one call site each for the inverse and the strip product (inlined)
+        flag |= inv_column<R>(c, k, hw.G, hw.G, hw.X, s, pair ? kb : -1);
+        if (pair) pair_scales<R>(c, k, kb, hw.G, s);
+        strip_column<R>(c, k, hw.G, hw.P, hw.P, hw.X, s);
+        if (pair) pair_finish<R>(c, k, hw.G, s);
+        j += pair ? 2 : 1;
     }
     if constexpr (TC) {
         if (*(volatile int*)tst.ar.err()) flag |= 4;
