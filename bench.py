@@ -80,6 +80,14 @@ def parse():
                     help="batched_uneven_chains: number of chains (default 2048)")
     ap.add_argument("--grad", action="store_true",
                     help="time rgf_conductance_grad on the workload (its gradient energies)")
+    ap.add_argument("--schedule", default="persistent", choices=["persistent", "phased"],
+                    help="persistent: the batch kernel with its work queue (default); phased: "
+                         "three launches per step")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="persistent schedule through rgf_conductance_dev instead of a prepared "
+                         "CUDA-graph batch")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default schedule instead of the autotuner's choice for the width")
     ap.add_argument("--check-chains", type=int, default=0,
                     help="batched_uneven_chains: compare only the first n chains with binary64")
     return ap.parse_args()
@@ -265,15 +273,35 @@ def run_uneven(args):
     Sd = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step():
-        rgf.conductance_dev(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8, prec,
-                            stream.cuda_stream)
+    # autotuned schedule per column size (eight widths spanning N in [51, 401]),
+    # then the batch as one prepared CUDA graph (persistent kernel per engine)
+    rgf.set_schedule(rgf.RGF_SCHED_PHASED if args.schedule == "phased" else rgf.RGF_SCHED_PERSISTENT)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        widths = [51, 101, 151, 201, 251, 301, 351, 401]
+        table, _ = rgf.autotune(prec, widths, cells=4, reps=2)
+        tuned = {"table": table, "tuning_s": round(time.perf_counter() - t0, 2)}
+    groups = 1
+    if prec == rgf.RGF_MIXED_TC:
+        eng = {rgf.tune_lookup(prec, int(N))["engine"] for N in Ns}
+        groups = len(eng)
+    rgf.profile_enable(True)
+    use_graph = args.schedule == "persistent" and not args.no_graph
+    if use_graph:
+        batch = rgf.Batch(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8, prec)
+
+        def step():
+            batch.launch(stream.cuda_stream)
+    else:
+        def step():
+            rgf.conductance_dev(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8,
+                                prec, stream.cuda_stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
     stream.synchronize()
-    rgf.profile_enable(True)
     ms, ms_sweep = [], []
     sampler = ClockSampler(local)
     with sampler:
@@ -317,13 +345,16 @@ def run_uneven(args):
            "vs_baseline": None, "dtype": "f64" if prec == rgf.RGF_FP64 else "f32x2", "data": "synthetic",
            "config": {"workload": "batched_uneven_chains", "chains": n, "chains_ok": int(ok.sum()),
                       "cells_cap": args.cells or None, "cells_total": int(cells.sum()),
-                      "precision": args.precision, "l2": "flushed (256 MB write) between steps"},
+                      "precision": args.precision, "l2": "flushed (256 MB write) between steps",
+                      "schedule": args.schedule + (" (CUDA graph)" if use_graph else ""),
+                      "launch_groups": groups, "tuning": tuned},
            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                       "reasons": clocks["reasons"]},
-           "gpu_launches": 5 * args.steps,
+           "gpu_launches": (2 + groups * (1 if args.schedule == "persistent" else 3)) * args.steps,
            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": None,
-                        "kernel": "half_kernel (the half sweeps alone)",
+                        "kernel": ("batch_kernel (end columns, half sweeps and joins)"
+                                   if args.schedule == "persistent" else "half_kernel (the half sweeps alone)"),
                         "flops_note": "F_alg(M = 2N) per unit-cell slice step of each chain",
                         "peak_source": peak_src},
            "parity": parity,
@@ -447,15 +478,34 @@ def main():
     Sd = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step():
-        rgf.conductance_dev(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8,
-                            prec, stream.cuda_stream)
+    # The schedule: the autotuner's choice for this width (untimed, before the
+    # warm-up), then either one prepared CUDA graph per step (energy fill,
+    # lead decimation, work-queue reset, persistent batch kernel) or the same
+    # launches through rgf_conductance_dev.
+    rgf.set_schedule(rgf.RGF_SCHED_PHASED if args.schedule == "phased" else rgf.RGF_SCHED_PERSISTENT)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        table, tms = rgf.autotune(prec, [N], cells=8 if N <= 300 else 2, reps=2)
+        tuned = {"entry": table[0], "candidates_half_ms": [round(float(x), 3) for x in tms[0]],
+                 "candidates": "engine (tensor, pipes) x panel (16, 8, 4) x pairs (1, 0)",
+                 "tuning_s": round(time.perf_counter() - t0, 2)}
+    rgf.profile_enable(True)
+    use_graph = args.schedule == "persistent" and not args.no_graph
+    if use_graph:
+        batch = rgf.Batch(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8, prec)
+
+        def step():
+            batch.launch(stream.cuda_stream)
+    else:
+        def step():
+            rgf.conductance_dev(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8,
+                                prec, stream.cuda_stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
         stream.synchronize()
-    rgf.profile_enable(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -539,9 +589,10 @@ def main():
         e2e = {"value": e2e_units / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
-    # Roofline of the dominant kernel (the half sweeps): algorithmic flops of
-    # the slice steps it processes (the unit-cell count F_alg(M)) over its
-    # CUDA-event duration, against the measured sustained bf16 tensor peak.
+    # Roofline of the dominant kernel (the persistent batch kernel, or the half
+    # sweeps of the phased schedule): algorithmic flops of the slice steps it
+    # processes (the unit-cell count F_alg(M)) over its CUDA-event duration,
+    # against the measured sustained bf16 tensor peak.
     ph = np.array(phases)                       # [steps, 4]: lead, prep, half, merge
     half_s = float(ph[:, 2].mean()) / 1e3
     steps_ok = float(ok.sum()) * L
@@ -554,12 +605,13 @@ def main():
     else:
         bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         peak_src = f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peaks_src})"
+    kernel_tag = "batch" if args.schedule == "persistent" else "half"
     traffic_file = ROOT / "profiles" / "traffic.json"
     traffic, traffic_note = None, "no DRAM counters recorded for this kernel and workload"
     if traffic_file.exists():
         try:
             rec = json.loads(traffic_file.read_text())
-            traffic = rec.get(f"half_{args.precision}_{args.workload}")
+            traffic = rec.get(f"{kernel_tag}_{args.precision}_{args.workload}")
             if traffic is not None:
                 traffic = float(traffic) * (L / float(rec.get("_cells", L)))
             if traffic is not None and rec.get("_sources_sha256") != kernel_sources_digest():
@@ -571,10 +623,11 @@ def main():
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             **({} if traffic is not None else {"traffic_note": traffic_note}),
-            "kernel": {0: "half_kernel<double>", 1: "half_kernel<df32>", 2: "half_kernel<df32,tc>"}[prec],
+            "kernel": f"{kernel_tag}_kernel" + {0: "<double>", 1: "<df32>", 2: "<df32,tc>"}[prec],
             "flops_per_step": F_alg,
             "flops_note": "F_alg(M) = 8/3 M^3 + 8 M^2 floor(N/2) + 8 ceil(N/2)^2 floor(N/2) per unit-cell "
-                          "slice step (M = 2N); achieved = F_alg x slice steps / half-sweep kernel time",
+                          "slice step (M = 2N); achieved = F_alg x slice steps / time of the kernel "
+                          "(persistent: end columns, half sweeps and joins in one kernel)",
             "peak_source": peak_src,
             "algorithmic_bytes_per_launch": algo_bytes,
             "executed_flops_per_step": pair_step_flops_per_cell(N),
@@ -583,14 +636,22 @@ def main():
             "achieved_at_column_slicing_count": flops_per_cell(N) * steps_ok / half_s / 1e12,
             "alu_peak_double_float": alu_peak,
             "frac_of_alu_peak_at_column_slicing_count": flops_per_cell(N) * steps_ok / half_s / 1e12 / alu_peak,
-            "ms_half": float(ph[:, 2].mean()), "ms_lead": float(ph[:, 0].mean()),
-            "ms_prep": float(ph[:, 1].mean()), "ms_merge": float(ph[:, 3].mean())}
+            "ms_kernel": float(ph[:, 2].mean()), "ms_lead": float(ph[:, 0].mean()),
+            "ms_prep": float(ph[:, 1].mean()), "ms_merge": float(ph[:, 3].mean()),
+            "phases_note": ("persistent: ms_kernel = the batch kernel (end columns, half sweeps, joins), "
+                            "ms_prep = the work-queue reset, ms_merge = 0"
+                            if kernel_tag == "batch" else
+                            "phased: ms_kernel = the half-sweep launch")}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(N, args.cpu_cells, w["W"], w["seed"])
 
     clocks = sampler.summary()
+    # our kernels per step: energy fill, lead decimation, then the batch kernel
+    # (persistent) or preparation, half sweeps and join (phased); one width,
+    # so one launch group
+    launches_per_step = 2 + (1 if args.schedule == "persistent" else 3)
     if rank == 0:
         T_all = np.full(len(job), np.nan)
         for idx, Tr, _ in gathered:
@@ -605,10 +666,12 @@ def main():
                           "chains_ok": int(ok.sum()), "W_eV": w["W"], "eta_eV": 1e-8,
                           "precision": args.precision, "l2": "flushed (256 MB write) between steps",
                           "parallelism": f"chains sharded over {world} rank(s) (LPT), one disorder "
-                                         "realisation per rank"},
+                                         "realisation per rank",
+                          "schedule": args.schedule + (" (CUDA graph)" if use_graph else ""),
+                          "tuning": tuned},
                "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                           "reasons": clocks["reasons"]},
-               "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roof,
+               "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roof,
                "cpu_baseline": cpu, "parity": parity,
                "T_gathered_finite": int(np.isfinite(T_all).sum()),
                "status_counts": {rgf.STATUS_NAMES[s]: int((status == s).sum()) for s in set(status.tolist())}}

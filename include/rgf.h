@@ -174,6 +174,56 @@ rgf_status rgf_conductance_dev(const rgf_ribbon* const* rib, const double* E_dev
                                void* stream, double* T_dev, int32_t* status_dev);
 
 /*
+ * Schedule of the forward sweep of rgf_conductance[_dev] (no counterpart in
+ * the paper; process-wide, default RGF_SCHED_PERSISTENT).  Both run the same
+ * arithmetic in separately compiled kernels, so their T agree to rounding (the
+ * compiler may fuse a product and a sum into one FMA in one of them only);
+ * each is deterministic, whatever order the queue hands the work out in.
+ *   RGF_SCHED_PERSISTENT: after the lead decimation, one persistent kernel per
+ *     launch group (one block per SM) takes the halves of the chains from a
+ *     device work queue, longest chain first; the block that finishes the
+ *     second half of a chain joins the two and writes T.  No block waits for
+ *     another, so there is no queue wait that could time out.
+ *   RGF_SCHED_PHASED: three launches (end-column preparation, half sweeps,
+ *     joins), blocks in the same order.
+ * A launch group is the set of chains on one engine: with RGF_MIXED_TC, the
+ * chains that the tuning table (rgf_set_tuning) sends to the FP32 pipes run
+ * after the tensor-core group, as RGF_MIXED.  Errors: RGF_EINVAL.
+ */
+typedef enum { RGF_SCHED_PERSISTENT = 0, RGF_SCHED_PHASED = 1 } rgf_schedule;
+rgf_status rgf_set_schedule(int schedule);
+int rgf_get_schedule(void);
+
+/*
+ * A prepared batch: the conductance of a fixed list of chains as one CUDA
+ * graph (energies into the descriptors, lead decimation, work-queue reset,
+ * persistent sweep), built once and launched any number of times.
+ * rgf_batch_create plans the chains (schedule from the tuning table in force),
+ * allocates and uploads the batch's descriptors and workspace (cudaMalloc;
+ * about the device memory of one rgf_conductance_dev call), and captures the
+ * launches on a private stream.  The graph keeps the pointers it was created
+ * with: every launch reads the energies in E_dev [nchains] and the ribbons'
+ * on-site energies as they are when it runs, and writes T_dev [nchains] and
+ * status_dev [nchains] (may be NULL); the caller keeps them, and the ribbons,
+ * alive until rgf_batch_free.  The decimation controls (rgf_set_lead_controls)
+ * are those in force at creation.  With profiling on at creation
+ * (rgf_profile_enable) the graph records the profile events, and
+ * rgf_profile_read_phases reads them after a launch.  rgf_batch_launch
+ * enqueues the graph on `stream` and returns; launches of one batch share its
+ * workspace and must not overlap (one stream, or events between streams).
+ * Results equal those of rgf_conductance_dev with RGF_SCHED_PERSISTENT bit for
+ * bit.  Errors:
+ * RGF_EINVAL (as rgf_conductance_dev; nchains must be >= 1), RGF_ENOMEM,
+ * RGF_ECUDA (the capture or the launch failed).
+ */
+typedef struct rgf_batch rgf_batch;   /* opaque */
+rgf_status rgf_batch_create(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
+                            double eta_device, double eta_lead, int precision, double* T_dev,
+                            int32_t* status_dev, rgf_batch** out);
+rgf_status rgf_batch_launch(rgf_batch* batch, void* stream);
+void rgf_batch_free(rgf_batch* batch);
+
+/*
  * Conductance and its gradient dT/d eps for every on-site energy of the
  * scattering region: dT/d eps_i = 2 Re (G_iL Gamma_R G_1L^dagger Gamma_L G_1i)
  * (from Eqs. 1-2), with the blocks of G assembled slice by slice through the
@@ -288,8 +338,10 @@ rgf_status rgf_zgemm_tc_selftest_timeout(void);
  * onsite_dev [L][2N] (binary64) and removed_dev [L][2N] (uint8, or NULL),
  * evaluated at nE energies E_dev [nE] (device).  Outputs on the device:
  * T_dev [nE], status_dev [nE] (int32, or NULL), as rgf_conductance_dev, in any
- * precision (RGF_FP64, RGF_MIXED, RGF_MIXED_TC).  Asynchronous on `stream`;
- * results are valid once the stream has passed the call.  Returns RGF_EINVAL,
+ * precision (RGF_FP64, RGF_MIXED, RGF_MIXED_TC), by the three launches of
+ * RGF_SCHED_PHASED with the default schedule of every chain (the tuning table
+ * is not read).  Asynchronous on `stream`; results are valid once the stream
+ * has passed the call.  Returns RGF_EINVAL,
  * with a message naming the limit, when the scratch the call needs exceeds
  * 64 MiB (21 energies at N = 245, more at smaller N); split the energies over
  * several calls then.
@@ -321,8 +373,11 @@ rgf_status rgf_profile_read(double* ms_lead, double* ms_sweep);
 
 /* The phases of the last profiled rgf_conductance* call, in milliseconds:
  * ms[0] lead decimation, ms[1] end-column preparation, ms[2] half sweeps (the
- * gradient sweep for rgf_conductance_grad), ms[3] join and trace.
- * rgf_profile_read's ms_sweep is ms[1] + ms[2] + ms[3].  ms: host [4]. */
+ * gradient sweep for rgf_conductance_grad), ms[3] join and trace.  Under
+ * RGF_SCHED_PERSISTENT the preparation and the join run inside the persistent
+ * kernel: ms[2] is that kernel (all launch groups), ms[1] the work-queue reset
+ * and ms[3] zero.  rgf_profile_read's ms_sweep is ms[1] + ms[2] + ms[3].
+ * ms: host [4]. */
 rgf_status rgf_profile_read_phases(double* ms);
 
 /*
@@ -335,6 +390,52 @@ rgf_status rgf_profile_read_phases(double* ms);
  * [1, 100000], residual_tol negative or NaN).
  */
 rgf_status rgf_set_lead_controls(int max_iter, double residual_tol);
+
+/*
+ * Tuning of the forward sweep per column size (no counterpart in the paper;
+ * process-wide, one table per precision).  Entry i applies to the chains whose
+ * column size K = ceil(N/2) is at most K_max[i] and above K_max[i-1]; chains
+ * wider than the last entry take the last entry; with no table every chain
+ * takes the default {engine RGF_ENGINE_TENSOR, panel 0, pairs 1}.
+ *   engine: RGF_ENGINE_TENSOR (the dense products on the tcgen05 tensor cores)
+ *           or RGF_ENGINE_PIPES (on the FP32 pipes); only RGF_MIXED_TC reads it.
+ *   panel:  Gauss-Jordan panel width 2, 4, 8 or 16, capped by the shared memory
+ *           of the launch; 0 = the widest that fits.
+ *   pairs:  1 = t I-bonded column pairs share one inverse (where no atom of the
+ *           second column is within 1e-4 eV of resonance), 0 = one column at a
+ *           time.
+ * Every schedule computes the same recursion; results differ only by rounding.
+ * rgf_set_tuning installs a table of n <= RGF_TUNE_MAX_ENTRIES entries with
+ * K_max strictly increasing (n = 0 removes it); rgf_get_tuning copies the
+ * installed table (*n its length; RGF_EINVAL if cap is smaller);
+ * rgf_tune_lookup returns the entry a ribbon of width N gets.  Plain host
+ * calls (no device needed).  Errors: RGF_EINVAL.
+ *
+ * rgf_autotune measures, for each width N[i], one Anderson-disordered chain
+ * (W = 0.1 eV) of `cells` unit cells at E = 0.3 eV under every candidate --
+ * engine (both with RGF_MIXED_TC) x panel {16, 8, 4} x pairs {1, 0}, *ncand
+ * of them -- as the device time of its half sweeps (the middle launch of
+ * RGF_SCHED_PHASED, CUDA events; the minimum of `reps` runs after one
+ * warm-up), writes
+ * the fastest into best[i] (K_max = ceil(N[i]/2)) and the times into ms
+ * [nN][*ncand] (may be NULL), and installs the table.  The widths must have
+ * distinct column sizes.  Synchronous; uses the current device.  Errors:
+ * RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA.
+ */
+#define RGF_TUNE_MAX_ENTRIES 64
+#define RGF_TUNE_MAX_CANDIDATES 12
+typedef enum { RGF_ENGINE_PIPES = 0, RGF_ENGINE_TENSOR = 1 } rgf_engine;
+typedef struct {
+    int K_max;
+    int engine;
+    int panel;
+    int pairs;
+} rgf_tune_entry;
+rgf_status rgf_set_tuning(int precision, const rgf_tune_entry* table, int n);
+rgf_status rgf_get_tuning(int precision, rgf_tune_entry* table, int cap, int* n);
+rgf_status rgf_tune_lookup(int precision, int N, rgf_tune_entry* out);
+rgf_status rgf_autotune(int precision, const int* N, int nN, int cells, int reps,
+                        rgf_tune_entry* best, double* ms, int* ncand);
 
 const char* rgf_status_str(int status);
 const char* rgf_last_error(void);

@@ -46,13 +46,15 @@ struct Profile {
 };
 Profile g_prof;
 
-cudaError_t prof_record(int i, cudaStream_t st) {
+// external: record as an event node of a graph being captured on `st`.
+cudaError_t prof_record(int i, cudaStream_t st, bool external = false) {
     if (!g_prof.on) return cudaSuccess;
     if (!g_prof.ev[i]) {
         cudaError_t e = cudaEventCreate(&g_prof.ev[i]);
         if (e != cudaSuccess) return e;
     }
-    return cudaEventRecord(g_prof.ev[i], st);
+    return external ? cudaEventRecordWithFlags(g_prof.ev[i], st, cudaEventRecordExternal)
+                    : cudaEventRecord(g_prof.ev[i], st);
 }
 
 rgf_status fail(rgf_status st, const std::string& msg) {
@@ -105,25 +107,62 @@ struct DevBuf {
     }
 };
 
+// Schedule of the forward sweep and the tuning tables (process-wide).  A
+// table, per precision, maps the column size K = ceil(N/2) of a chain to its
+// schedule: the first entry with K <= K_max, else the last entry; an empty
+// table means the default (tensor cores with RGF_MIXED_TC, widest panel,
+// pair steps).  The autotuner's timing runs force one entry for every chain
+// (thread-local).
+std::mutex g_tune_mu;
+std::vector<rgf_tune_entry> g_tune[3];
+int g_schedule = RGF_SCHED_PERSISTENT;
+thread_local const rgf_tune_entry* g_force = nullptr;
+thread_local int g_force_schedule = -1;
+
+rgf_tune_entry default_entry() { return rgf_tune_entry{0x7fffffff, RGF_ENGINE_TENSOR, 0, 1}; }
+
+rgf_tune_entry lookup_tune(int precision, int K) {
+    if (g_force) return *g_force;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const std::vector<rgf_tune_entry>& t = g_tune[precision];
+    if (t.empty()) return default_entry();
+    for (const rgf_tune_entry& e : t)
+        if (K <= e.K_max) return e;
+    return t.back();
+}
+
+// One launch group of the forward sweep: the chains that run on one engine,
+// longest first.  RGF_MIXED_TC chains tuned to the FP32 pipes form a second
+// group that runs as RGF_MIXED (same double-float arithmetic, products on the
+// pipes).
+struct Group {
+    int precision = 0;
+    int Kmax = 1;
+    std::vector<int> order;
+};
+
 struct Plan {
     std::vector<rgf::ChainDev> chains;
     std::vector<rgf::LeadDev> leads;
-    std::vector<int> order;
+    std::vector<int> order;          // all chains, longest first (gradient sweep)
+    std::vector<Group> groups;       // forward sweep
     std::vector<int> seg_cols;
     size_t ws_elems = 0, lead_ws_elems = 0, lead_out_elems = 0, grad_elems = 0;
     int Kmax = 1;
 };
 
 // grad: size the gradient workspace with checkpoints every ckpt_stride cells
-// (<= 0: ceil(sqrt(L))).
-rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl, bool grad = false,
-                     int ckpt_stride = 0) {
+// (<= 0: ceil(sqrt(L))).  precision: that of the call (picks the tuning table
+// and the forward sweep's groups).
+rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, int precision, Plan& pl,
+                     bool grad = false, int ckpt_stride = 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     pl.chains.resize(nchains);
     pl.leads.resize(nchains);
     pl.seg_cols.resize(nchains);
     std::vector<double> cost(nchains);
+    std::vector<int> engine(nchains, 0);
     for (int c = 0; c < nchains; ++c) {
         const rgf_ribbon* r = rib[c];
         if (!r) return fail(RGF_EINVAL, "rib[" + std::to_string(c) + "] is NULL");
@@ -138,6 +177,7 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl, bool g
         ch.lead = c;
         ch.ws_off = pl.ws_elems;
         ch.grad_off = pl.grad_elems;
+        rgf::default_sched(ch);
         if (grad) {
             int stride = ckpt_stride > 0 ? std::min(ckpt_stride, r->L)
                                          : std::max(1, (int)std::ceil(std::sqrt((double)r->L)));
@@ -145,6 +185,11 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl, bool g
             pl.ws_elems += rgf::grad_ws_elems(r->N, r->L, pl.seg_cols[c]);
             pl.grad_elems += (size_t)r->L * 2 * r->N;
         } else {
+            const rgf_tune_entry te = lookup_tune(precision, rgf::col_KL(r->N));
+            ch.panel = (int8_t)te.panel;
+            ch.pairs = (int8_t)(te.pairs != 0);
+            ch.tc = (int8_t)(precision == RGF_MIXED_TC && te.engine == RGF_ENGINE_TENSOR);
+            engine[c] = ch.tc;
             pl.seg_cols[c] = 0;
             pl.ws_elems += rgf::sweep_ws_elems(r->N);
         }
@@ -160,10 +205,25 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, Plan& pl, bool g
         double KL = rgf::col_KL(r->N);
         cost[c] = KL * KL * KL * (double)r->L;
     }
+    // longest processing time first: the queue (or the block scheduler) then
+    // hands the remaining work to whichever SM frees up first
     pl.order.resize(nchains);
     for (int c = 0; c < nchains; ++c) pl.order[c] = c;
     std::stable_sort(pl.order.begin(), pl.order.end(),
                      [&](int a, int b) { return cost[a] > cost[b]; });
+    if (!grad) {
+        const bool split = precision == RGF_MIXED_TC;
+        for (int pass = 0; pass < (split ? 2 : 1); ++pass) {
+            Group g;
+            g.precision = split ? (pass == 0 ? RGF_MIXED_TC : RGF_MIXED) : precision;
+            for (int c : pl.order)
+                if (!split || engine[c] == (pass == 0 ? 1 : 0)) {
+                    g.order.push_back(c);
+                    g.Kmax = std::max(g.Kmax, rgf::col_KL(pl.chains[c].N));
+                }
+            if (!g.order.empty()) pl.groups.push_back(std::move(g));
+        }
+    }
     return RGF_OK;
 }
 
@@ -178,6 +238,151 @@ __global__ void fill_energy(rgf::ChainDev* chains, rgf::LeadDev* leads, const do
     }
 }
 
+// The device side of a plan: one allocation holding the descriptors, the
+// groups' orders and work queues, the lead buffers and the sweep workspace
+// (each part 256-byte aligned).
+struct DevLayout {
+    size_t o_chain = 0, o_lead = 0, o_order = 0, o_seg = 0, o_queue = 0, o_lst = 0, o_lws = 0,
+           o_lout = 0, o_ws = 0, total = 0, queue_bytes = 0, hdr_bytes = 0;
+};
+inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+DevLayout layout_of(const Plan& pl) {
+    const size_t n = pl.chains.size();
+    DevLayout d;
+    d.o_chain = 0;
+    d.o_lead = up256(n * sizeof(rgf::ChainDev));
+    d.o_order = d.o_lead + up256(n * sizeof(rgf::LeadDev));
+    d.o_seg = d.o_order + up256(n * sizeof(int));   // groups' orders, concatenated
+    d.hdr_bytes = d.o_seg + n * sizeof(int);
+    d.o_queue = up256(d.hdr_bytes);
+    d.queue_bytes = std::max<size_t>(1, pl.groups.size()) * rgf::batch_queue_ints((int)n) * sizeof(int);
+    d.o_lst = d.o_queue + up256(d.queue_bytes);
+    d.o_lws = d.o_lst + up256(2 * n * sizeof(int));
+    d.o_lout = d.o_lws + up256(pl.lead_ws_elems * 16);
+    d.o_ws = d.o_lout + up256(pl.lead_out_elems * 16);
+    d.total = d.o_ws + std::max<size_t>(pl.ws_elems, 1) * 16;
+    return d;
+}
+
+// Host image of the header part of the layout (descriptors, orders, segments).
+std::vector<unsigned char> header_of(const Plan& pl, const DevLayout& d) {
+    std::vector<unsigned char> h(d.hdr_bytes, 0);
+    const size_t n = pl.chains.size();
+    std::memcpy(h.data() + d.o_chain, pl.chains.data(), n * sizeof(rgf::ChainDev));
+    std::memcpy(h.data() + d.o_lead, pl.leads.data(), n * sizeof(rgf::LeadDev));
+    if (pl.groups.empty()) {
+        std::memcpy(h.data() + d.o_order, pl.order.data(), n * sizeof(int));
+    } else {
+        size_t k = 0;
+        for (const Group& g : pl.groups) {
+            std::memcpy(h.data() + d.o_order + k * sizeof(int), g.order.data(), g.order.size() * sizeof(int));
+            k += g.order.size();
+        }
+    }
+    std::memcpy(h.data() + d.o_seg, pl.seg_cols.data(), n * sizeof(int));
+    return h;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+// Sets the shared-memory limits of every kernel a plan's forward sweep
+// launches (before a stream capture, and by every launcher anyway).
+cudaError_t configure_groups(const Plan& pl) {
+    for (const Group& g : pl.groups) {
+        cudaError_t e = rgf::configure_sweep(g.precision, g.Kmax);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Enqueues the forward path of a plan on `st`: energies into the descriptors,
+// lead decimation, then per group the persistent batch kernel (or, with the
+// phased schedule, the three launches; all groups' preparations, then their
+// recursions, then their joins).  base: the plan's device allocation.
+// prof: 0 no profile events, 1 events on the stream, 2 event nodes of the
+// graph being captured on `st`.
+rgf_status enqueue_forward(const Plan& pl, const DevLayout& d, unsigned char* base,
+                           const double* E_dev, double eta_device, double eta_lead,
+                           cudaStream_t st, double* T_dev, int32_t* status_dev, int schedule,
+                           int prof) {
+    const int n = (int)pl.chains.size();
+    auto* dchains = (rgf::ChainDev*)(base + d.o_chain);
+    auto* dleads = (rgf::LeadDev*)(base + d.o_lead);
+    auto* dorder = (int*)(base + d.o_order);
+    auto* dqueue = (int*)(base + d.o_queue);
+    auto* dlst = (int*)(base + d.o_lst);
+    void* dlws = base + d.o_lws;
+    void* dlout = base + d.o_lout;
+    void* dws = base + d.o_ws;
+    auto rec = [&](int i) { return prof ? prof_record(i, st, prof == 2) : cudaSuccess; };
+    fill_energy<<<(n + 255) / 256, 256, 0, st>>>(dchains, dleads, E_dev, n);
+    RGF_CUDA(cudaGetLastError(), "fill_energy launch");
+    RGF_CUDA(rec(0), "cudaEventRecord");
+    RGF_CUDA(rgf::launch_lead(dleads, n, pl.Kmax, eta_lead, dlws, dlout, dlst, nullptr, st),
+             "lead decimation launch");
+    RGF_CUDA(rec(1), "cudaEventRecord");
+    if (schedule == RGF_SCHED_PERSISTENT) {
+        RGF_CUDA(cudaMemsetAsync(dqueue, 0, d.queue_bytes, st), "cudaMemsetAsync(work queue)");
+        RGF_CUDA(rec(2), "cudaEventRecord");
+        const int nsm = sm_count();
+        size_t k = 0;
+        for (size_t gi = 0; gi < pl.groups.size(); ++gi) {
+            const Group& g = pl.groups[gi];
+            RGF_CUDA(rgf::launch_batch(g.precision, dchains, dorder + k, (int)g.order.size(), g.Kmax,
+                                       eta_device, dlout, dlst, dleads, dws, T_dev, status_dev,
+                                       dqueue + gi * rgf::batch_queue_ints(n), nsm, st),
+                     "persistent sweep launch");
+            k += g.order.size();
+        }
+        RGF_CUDA(rec(3), "cudaEventRecord");
+    } else {
+        size_t k = 0;
+        for (const Group& g : pl.groups) {
+            RGF_CUDA(rgf::launch_prep(g.precision, dchains, dorder + k, (int)g.order.size(), g.Kmax,
+                                      eta_device, dlout, dlst, dleads, dws, st),
+                     "end-column preparation launch");
+            k += g.order.size();
+        }
+        RGF_CUDA(rec(2), "cudaEventRecord");
+        k = 0;
+        for (const Group& g : pl.groups) {
+            RGF_CUDA(rgf::launch_half(g.precision, dchains, dorder + k, (int)g.order.size(), g.Kmax,
+                                      eta_device, dlout, dlst, dleads, dws, st),
+                     "half sweep launch");
+            k += g.order.size();
+        }
+        RGF_CUDA(rec(3), "cudaEventRecord");
+        k = 0;
+        for (const Group& g : pl.groups) {
+            RGF_CUDA(rgf::launch_merge(g.precision, dchains, dorder + k, (int)g.order.size(), g.Kmax,
+                                       eta_device, dlout, dlst, dleads, dws, T_dev, status_dev, st),
+                     "merge launch");
+            k += g.order.size();
+        }
+    }
+    RGF_CUDA(rec(4), "cudaEventRecord");
+    if (prof == 1 && g_prof.on) g_prof.recorded = true;
+    return RGF_OK;
+}
+
+rgf_status check_call(const rgf_ribbon* const* rib, const void* E_dev, const void* T_dev,
+                      int nchains, int precision, double eta_device, double eta_lead) {
+    if (nchains < 0) return fail(RGF_EINVAL, "nchains < 0");
+    if (nchains > 0 && (!rib || !E_dev || !T_dev)) return fail(RGF_EINVAL, "NULL argument");
+    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+        return fail(RGF_EINVAL, "unknown precision");
+    if (!(eta_device >= 0.0) || !(eta_lead > 0.0) || !std::isfinite(eta_device) ||
+        !std::isfinite(eta_lead))
+        return fail(RGF_EINVAL, "eta_device must be >= 0 and eta_lead > 0 (finite)");
+    return RGF_OK;
+}
+
 // Runs the whole path on `st`: lead decimation, then the forward sweep (or,
 // with dT_dev, the checkpointed two-sided gradient sweep).  E_dev, T_dev, status_dev,
 // dT_dev: device.
@@ -185,72 +390,51 @@ rgf_status run_path(const rgf_ribbon* const* rib, const double* E_dev, int nchai
                     double eta_device, double eta_lead, int precision, cudaStream_t st,
                     double* T_dev, int32_t* status_dev, double* dT_dev = nullptr,
                     int ckpt_stride = 0, int out_mode = rgf::OUT_GRAD) {
-    if (nchains < 0) return fail(RGF_EINVAL, "nchains < 0");
-    if (nchains == 0) return RGF_OK;
-    if (!rib || !E_dev || !T_dev) return fail(RGF_EINVAL, "NULL argument");
-    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
-        return fail(RGF_EINVAL, "unknown precision");
-    if (!(eta_device >= 0.0) || !(eta_lead > 0.0) || !std::isfinite(eta_device) ||
-        !std::isfinite(eta_lead))
-        return fail(RGF_EINVAL, "eta_device must be >= 0 and eta_lead > 0 (finite)");
+    rgf_status s = check_call(rib, E_dev, T_dev, nchains, precision, eta_device, eta_lead);
+    if (s != RGF_OK || nchains == 0) return s;
     const bool grad = dT_dev != nullptr;
     Plan pl;
-    rgf_status s = make_plan(rib, nchains, pl, grad, ckpt_stride);
+    s = make_plan(rib, nchains, precision, pl, grad, ckpt_stride);
     if (s != RGF_OK) return s;
-
-    const size_t nC = pl.chains.size() * sizeof(rgf::ChainDev);
-    const size_t nL = pl.leads.size() * sizeof(rgf::LeadDev);
-    const size_t nO = pl.order.size() * sizeof(int);
-    std::vector<unsigned char> hdr(nC + nL + 2 * nO);
-    std::memcpy(hdr.data(), pl.chains.data(), nC);
-    std::memcpy(hdr.data() + nC, pl.leads.data(), nL);
-    std::memcpy(hdr.data() + nC + nL, pl.order.data(), nO);
-    std::memcpy(hdr.data() + nC + nL + nO, pl.seg_cols.data(), nO);
-
-    DevBuf dhdr, dws, dlws, dlout, dlst;
-    RGF_CUDA(dhdr.alloc(hdr.size(), st), "cudaMallocAsync(descriptors)");
-    cudaError_t ae = dws.alloc(pl.ws_elems * 16, st);
+    const DevLayout d = layout_of(pl);
+    const std::vector<unsigned char> hdr = header_of(pl, d);
+    DevBuf dmem;
+    cudaError_t ae = dmem.alloc(d.total, st);
     if (ae == cudaErrorMemoryAllocation) return fail(RGF_ENOMEM, "workspace allocation failed");
     RGF_CUDA(ae, "cudaMallocAsync(workspace)");
-    RGF_CUDA(dlws.alloc(pl.lead_ws_elems * 16, st), "cudaMallocAsync(lead workspace)");
-    RGF_CUDA(dlout.alloc(pl.lead_out_elems * 16, st), "cudaMallocAsync(lead output)");
-    RGF_CUDA(dlst.alloc(2 * sizeof(int) * nchains, st), "cudaMallocAsync(lead status)");
-    RGF_CUDA(cudaMemcpyAsync(dhdr.p, hdr.data(), hdr.size(), cudaMemcpyHostToDevice, st),
+    unsigned char* base = (unsigned char*)dmem.p;
+    RGF_CUDA(cudaMemcpyAsync(base, hdr.data(), hdr.size(), cudaMemcpyHostToDevice, st),
              "cudaMemcpyAsync(descriptors)");
-    if (grad) RGF_CUDA(cudaMemsetAsync(dT_dev, 0, pl.grad_elems * sizeof(double), st), "cudaMemsetAsync");
+    if (!grad) {
+        int sched = g_force_schedule;
+        if (sched < 0) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            sched = g_schedule;
+        }
+        return enqueue_forward(pl, d, base, E_dev, eta_device, eta_lead, st, T_dev, status_dev,
+                               sched, 1);
+    }
+    RGF_CUDA(cudaMemsetAsync(dT_dev, 0, pl.grad_elems * sizeof(double), st), "cudaMemsetAsync");
     double* dgrad = (out_mode & rgf::OUT_GRAD) ? dT_dev : nullptr;
     double* drho = (out_mode & rgf::OUT_LDOS) ? dT_dev : nullptr;
-    auto* dchains = (rgf::ChainDev*)dhdr.p;
-    auto* dleads = (rgf::LeadDev*)((unsigned char*)dhdr.p + nC);
-    auto* dorder = (int*)((unsigned char*)dhdr.p + nC + nL);
-    auto* dseg = (int*)((unsigned char*)dhdr.p + nC + nL + nO);
+    auto* dchains = (rgf::ChainDev*)(base + d.o_chain);
+    auto* dleads = (rgf::LeadDev*)(base + d.o_lead);
+    auto* dorder = (int*)(base + d.o_order);
+    auto* dseg = (int*)(base + d.o_seg);
+    auto* dlst = (int*)(base + d.o_lst);
     fill_energy<<<(nchains + 255) / 256, 256, 0, st>>>(dchains, dleads, E_dev, nchains);
     RGF_CUDA(cudaGetLastError(), "fill_energy launch");
     RGF_CUDA(prof_record(0, st), "cudaEventRecord");
-    RGF_CUDA(rgf::launch_lead(dleads, nchains, pl.Kmax, eta_lead, dlws.p, dlout.p, (int*)dlst.p,
-                              nullptr, st),
+    RGF_CUDA(rgf::launch_lead(dleads, nchains, pl.Kmax, eta_lead, base + d.o_lws, base + d.o_lout,
+                              dlst, nullptr, st),
              "lead decimation launch");
     RGF_CUDA(prof_record(1, st), "cudaEventRecord");
-    if (grad) {
-        RGF_CUDA(prof_record(2, st), "cudaEventRecord");
-        RGF_CUDA(rgf::launch_grad(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
-                                  dlout.p, (int*)dlst.p, dleads, dws.p, dseg, T_dev, dgrad, drho,
-                                  out_mode, status_dev, st),
-                 "gradient sweep launch");
-        RGF_CUDA(prof_record(3, st), "cudaEventRecord");
-    } else {
-        RGF_CUDA(rgf::launch_prep(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
-                                  dlout.p, (int*)dlst.p, dleads, dws.p, st),
-                 "end-column preparation launch");
-        RGF_CUDA(prof_record(2, st), "cudaEventRecord");
-        RGF_CUDA(rgf::launch_half(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
-                                  dlout.p, (int*)dlst.p, dleads, dws.p, st),
-                 "half sweep launch");
-        RGF_CUDA(prof_record(3, st), "cudaEventRecord");
-        RGF_CUDA(rgf::launch_merge(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
-                                   dlout.p, (int*)dlst.p, dleads, dws.p, T_dev, status_dev, st),
-                 "merge launch");
-    }
+    RGF_CUDA(prof_record(2, st), "cudaEventRecord");
+    RGF_CUDA(rgf::launch_grad(precision, dchains, dorder, nchains, pl.Kmax, eta_device,
+                              base + d.o_lout, dlst, dleads, base + d.o_ws, dseg, T_dev, dgrad,
+                              drho, out_mode, status_dev, st),
+             "gradient sweep launch");
+    RGF_CUDA(prof_record(3, st), "cudaEventRecord");
     RGF_CUDA(prof_record(4, st), "cudaEventRecord");
     if (g_prof.on) g_prof.recorded = true;
     return RGF_OK;
@@ -601,6 +785,235 @@ rgf_status rgf_conductance_grad(const rgf_ribbon* const* rib, const double* E, i
     if (nchains > 0 && !dT_deps) return fail(RGF_EINVAL, "dT_deps is NULL");
     return run_host(rib, E, nchains, eta_device, eta_lead, precision, T, chain_status, dT_deps,
                     ckpt_stride);
+}
+
+rgf_status rgf_set_schedule(int schedule) {
+    if (schedule != RGF_SCHED_PERSISTENT && schedule != RGF_SCHED_PHASED)
+        return fail(RGF_EINVAL, "unknown schedule");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_schedule = schedule;
+    return RGF_OK;
+}
+
+int rgf_get_schedule(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_schedule;
+}
+
+rgf_status rgf_set_tuning(int precision, const rgf_tune_entry* table, int n) {
+    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+        return fail(RGF_EINVAL, "unknown precision");
+    if (n < 0 || n > RGF_TUNE_MAX_ENTRIES || (n > 0 && !table))
+        return fail(RGF_EINVAL, "n must be in [0, RGF_TUNE_MAX_ENTRIES] with a table");
+    for (int i = 0; i < n; ++i) {
+        const rgf_tune_entry& e = table[i];
+        if (e.K_max < 1 || (i > 0 && e.K_max <= table[i - 1].K_max))
+            return fail(RGF_EINVAL, "K_max must be >= 1 and strictly increasing");
+        if (e.engine != RGF_ENGINE_PIPES && e.engine != RGF_ENGINE_TENSOR)
+            return fail(RGF_EINVAL, "engine must be RGF_ENGINE_PIPES or RGF_ENGINE_TENSOR");
+        if (e.panel != 0 && e.panel != 2 && e.panel != 4 && e.panel != 8 && e.panel != 16)
+            return fail(RGF_EINVAL, "panel must be 0, 2, 4, 8 or 16");
+        if (e.pairs != 0 && e.pairs != 1) return fail(RGF_EINVAL, "pairs must be 0 or 1");
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[precision].assign(table, table + n);
+    return RGF_OK;
+}
+
+rgf_status rgf_get_tuning(int precision, rgf_tune_entry* table, int cap, int* n) {
+    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+        return fail(RGF_EINVAL, "unknown precision");
+    if (!n || cap < 0 || (cap > 0 && !table)) return fail(RGF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const std::vector<rgf_tune_entry>& t = g_tune[precision];
+    *n = (int)t.size();
+    if ((int)t.size() > cap) return fail(RGF_EINVAL, "table capacity too small");
+    std::copy(t.begin(), t.end(), table);
+    return RGF_OK;
+}
+
+rgf_status rgf_tune_lookup(int precision, int N, rgf_tune_entry* out) {
+    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+        return fail(RGF_EINVAL, "unknown precision");
+    if (!out || N < 2) return fail(RGF_EINVAL, "bad argument");
+    *out = lookup_tune(precision, rgf::col_KL(N));
+    return RGF_OK;
+}
+
+rgf_status rgf_autotune(int precision, const int* N, int nN, int cells, int reps,
+                        rgf_tune_entry* best, double* ms, int* ncand) {
+    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+        return fail(RGF_EINVAL, "unknown precision");
+    if (nN < 1 || nN > RGF_TUNE_MAX_ENTRIES || !N || !best || cells < 1 || reps < 1)
+        return fail(RGF_EINVAL, "bad argument to rgf_autotune");
+    for (int i = 0; i < nN; ++i)
+        if (N[i] < 2 || N[i] > 2047) return fail(RGF_EINVAL, "N must be in [2, 2047]");
+    // widths by column size; idx[b] = the caller's index of the b-th
+    std::vector<int> idx(nN);
+    for (int i = 0; i < nN; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return rgf::col_KL(N[a]) < rgf::col_KL(N[b]); });
+    std::vector<int> Ns(nN);
+    for (int b = 0; b < nN; ++b) Ns[b] = N[idx[b]];
+    for (int i = 1; i < nN; ++i)
+        if (rgf::col_KL(Ns[i]) == rgf::col_KL(Ns[i - 1]))
+            return fail(RGF_EINVAL, "two widths with the same column size ceil(N/2)");
+    // the candidates: engine x panel width x pair steps
+    std::vector<rgf_tune_entry> cand;
+    const int engines = precision == RGF_MIXED_TC ? 2 : 1;
+    for (int en = 0; en < engines; ++en)
+        for (int panel : {16, 8, 4})
+            for (int pairs : {1, 0})
+                cand.push_back(rgf_tune_entry{0, precision == RGF_MIXED_TC ? 1 - en : 0, panel, pairs});
+    if (ncand) *ncand = (int)cand.size();
+    const bool prof_was = g_prof.on;
+    g_prof.on = true;
+    rgf_status result = RGF_OK;
+    std::vector<rgf_tune_entry> table;
+    for (int b = 0; b < nN && result == RGF_OK; ++b) {
+        // one chain: an Anderson-disordered ribbon of `cells` unit cells at
+        // 0.3 eV; the time of its half sweeps (the three-launch schedule's
+        // middle launch, the only step the candidates change)
+        rgf_ribbon_desc desc{};
+        desc.N = Ns[b];
+        desc.L = cells;
+        desc.t = -2.7;
+        desc.anderson_W = 0.1;
+        desc.seed = 12345;
+        rgf_ribbon* r = nullptr;
+        result = rgf_build_ribbon(&desc, &r);
+        if (result != RGF_OK) break;
+        double* dE = nullptr;
+        double* dT = nullptr;
+        const double E = 0.3;
+        cudaError_t e = cudaMalloc(&dE, sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&dT, sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(dE, &E, sizeof(double), cudaMemcpyHostToDevice);
+        double best_ms = INFINITY;
+        rgf_tune_entry win = cand[0];
+        for (size_t ci = 0; ci < cand.size() && e == cudaSuccess && result == RGF_OK; ++ci) {
+            double t_min = INFINITY;
+            for (int rep = 0; rep <= reps && result == RGF_OK; ++rep) {   // rep 0: warm-up
+                g_force = &cand[ci];
+                g_force_schedule = RGF_SCHED_PHASED;
+                result = run_path(&r, dE, 1, 1e-8, 1e-8, precision, 0, dT, nullptr);
+                g_force = nullptr;
+                g_force_schedule = -1;
+                if (result != RGF_OK) break;
+                double ph[kProfEvents - 1];
+                result = rgf_profile_read_phases(ph);
+                if (rep > 0) t_min = std::min(t_min, ph[2]);
+            }
+            if (ms) ms[(size_t)idx[b] * cand.size() + ci] = t_min;
+            if (t_min < best_ms) {
+                best_ms = t_min;
+                win = cand[ci];
+            }
+        }
+        if (e != cudaSuccess) result = cuda_fail(e, "rgf_autotune buffers");
+        if (dE) cudaFree(dE);
+        if (dT) cudaFree(dT);
+        rgf_free_ribbon(r);
+        win.K_max = rgf::col_KL(Ns[b]);
+        table.push_back(win);
+        best[idx[b]] = win;
+    }
+    g_prof.on = prof_was;
+    g_prof.recorded = false;
+    if (result != RGF_OK) return result;
+    return rgf_set_tuning(precision, table.data(), (int)table.size());
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Prepared batches: the forward path of a fixed list of chains as one CUDA
+// graph.
+// ---------------------------------------------------------------------------
+struct rgf_batch {
+    int device = 0;
+    bool profiled = false;   // the graph records the profile events
+    Plan plan;
+    DevLayout layout;
+    unsigned char* mem = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+void rgf_batch_free(rgf_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->mem) cudaFree(b->mem);
+    delete b;
+}
+
+rgf_status rgf_batch_create(const rgf_ribbon* const* rib, const double* E_dev, int nchains,
+                            double eta_device, double eta_lead, int precision, double* T_dev,
+                            int32_t* status_dev, rgf_batch** out) {
+    if (!out) return fail(RGF_EINVAL, "out is NULL");
+    *out = nullptr;
+    rgf_status s = check_call(rib, E_dev, T_dev, nchains, precision, eta_device, eta_lead);
+    if (s != RGF_OK) return s;
+    if (nchains == 0) return fail(RGF_EINVAL, "a batch needs at least one chain");
+    rgf_batch* b = new (std::nothrow) rgf_batch();
+    if (!b) return fail(RGF_ENOMEM, "host allocation failed");
+    cudaGetDevice(&b->device);
+    s = make_plan(rib, nchains, precision, b->plan);
+    if (s != RGF_OK) {
+        rgf_batch_free(b);
+        return s;
+    }
+    b->layout = layout_of(b->plan);
+    const std::vector<unsigned char> hdr = header_of(b->plan, b->layout);
+    cudaError_t e = cudaMalloc(&b->mem, b->layout.total);
+    if (e != cudaSuccess) {
+        rgf_batch_free(b);
+        return e == cudaErrorMemoryAllocation ? fail(RGF_ENOMEM, "batch workspace allocation failed")
+                                              : cuda_fail(e, "cudaMalloc(batch)");
+    }
+    e = cudaMemcpy(b->mem, hdr.data(), hdr.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = configure_groups(b->plan);
+    if (e != cudaSuccess) {
+        rgf_batch_free(b);
+        return cuda_fail(e, "batch set-up");
+    }
+    // capture the launch sequence on a private stream
+    StreamGuard cs;
+    e = cudaStreamCreateWithFlags(&cs.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs.st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        rgf_batch_free(b);
+        return cuda_fail(e, "stream capture");
+    }
+    b->profiled = g_prof.on;
+    s = enqueue_forward(b->plan, b->layout, b->mem, E_dev, eta_device, eta_lead, cs.st, T_dev,
+                        status_dev, RGF_SCHED_PERSISTENT, b->profiled ? 2 : 0);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs.st, &g);
+    b->graph = g;
+    if (s != RGF_OK) {
+        rgf_batch_free(b);
+        return s;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        rgf_batch_free(b);
+        return cuda_fail(e, "graph capture");
+    }
+    *out = b;
+    return RGF_OK;
+}
+
+rgf_status rgf_batch_launch(rgf_batch* b, void* stream) {
+    if (!b || !b->exec) return fail(RGF_EINVAL, "batch is NULL");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != b->device) return fail(RGF_EINVAL, "batch was created on another device");
+    RGF_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "cudaGraphLaunch");
+    if (b->profiled && g_prof.on) g_prof.recorded = true;
+    return RGF_OK;
 }
 
 }  // extern "C"

@@ -37,7 +37,22 @@ struct ChainDev {
     int lead;               // index of its lead problem
     size_t ws_off;          // offset (16-byte elements) of its sweep workspace
     size_t grad_off;        // offset (doubles) of its dT/d eps block (gradient only)
+    // Schedule of its forward sweep (chosen per column size by the host's
+    // tuning table; the gradient sweep ignores it):
+    int8_t tc;              // 1: dense products on the tensor cores (RGF_MIXED_TC
+                            // launches only), 0: on the FP32 / FP64 pipes
+    int8_t panel;           // Gauss-Jordan panel width; 0 = the widest that fits
+    int8_t pairs;           // 1: t I-bonded column pairs share one inverse
+    int8_t sched_pad;
 };
+
+// The default schedule of a chain: everything on, the widest panel.
+__host__ __device__ inline void default_sched(ChainDev& ch) {
+    ch.tc = 1;
+    ch.panel = 0;
+    ch.pairs = 1;
+    ch.sched_pad = 0;
+}
 
 // Number of 16-byte elements of the decimation workspace of one lead problem.
 __host__ __device__ inline size_t lead_ws_elems(int N) {
@@ -94,6 +109,22 @@ cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order
                          int Kmax, double eta_device, const void* leadout, const int* lead_status,
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st);
+
+// The same three steps as one persistent kernel (rgf_sweep.cu): one block per
+// SM (at most 2 * nchains), each taking the next half from a work queue in the
+// order of `order` (item 2i + h = half h of chain order[i]), preparing its end
+// column, running its recursion and, if it finishes second of its chain's two
+// halves, joining them and writing T and status.  queue: batch_queue_ints(n)
+// zeroed ints (the caller zeroes them before every launch); nsm: the number of
+// persistent blocks.
+inline size_t batch_queue_ints(int nchains) { return 1 + (size_t)nchains; }
+cudaError_t launch_batch(int precision, const ChainDev* chains, const int* order, int nchains,
+                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                         const LeadDev* leads, void* ws, double* T, int32_t* status, int* queue,
+                         int nsm, cudaStream_t st);
+// Sets the kernels' shared-memory limits for a largest column size Kmax (done by
+// every launcher; also callable ahead of a stream capture).
+cudaError_t configure_sweep(int precision, int Kmax);
 
 // Two-sided sweep (rgf_grad.cu): workspace (16-byte elements) of one chain
 // with segments of seg_cols columns, and the launcher (seg_cols: [nchains] on

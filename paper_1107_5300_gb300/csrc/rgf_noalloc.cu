@@ -85,6 +85,7 @@ __global__ void noalloc_setup(rgf::ChainDev* chains, rgf::LeadDev* leads, int* o
         ch.lead = i;
         ch.ws_off = (size_t)i * rgf::sweep_ws_elems(N);
         ch.grad_off = 0;
+        rgf::default_sched(ch);
         rgf::LeadDev& ld = leads[i];
         ld.N = N;
         ld.t = t;

@@ -48,6 +48,9 @@ __host__ __device__ inline size_t tc_area_offset(int Kmax, int bm) {
 __host__ __device__ inline size_t sweep_total_bytes(int Kmax, int bm, bool tc) {
     return tc ? tc_area_offset(Kmax, bm) + tc::smem_bytes() : sweep_base_bytes(Kmax, bm, false);
 }
+// The binary64 staging tiles (the only part of a binary64 layout beyond the
+// tensor-core layout's own buffers) fit inside the digit tiles of A.
+static_assert(2 * 8 * 64 * 16 + 1024 <= tc::OFF_B, "binary64 layout inside the tensor-core tiles");
 
 // Panel width of the blocked Gauss-Jordan for a largest column size Kmax:
 // the widest of 16, 8, 4, 2 whose layout fits the 227 KB of shared memory a
@@ -58,12 +61,17 @@ __host__ __device__ inline int gj_panel_width(int Kmax, bool tc = false) {
     return b;
 }
 
+// The layout for panel width bm (0: gj_panel_width(Kmax, tc)).  A binary64
+// layout (tc false) carved with the panel width of a tensor-core launch ends
+// inside that launch's digit tiles (its GEMM staging tiles are the only part
+// past the sweep's own buffers), so a persistent block can alternate between
+// the two without touching its mbarriers or TMEM address.
 template <class R>
-__device__ SweepSmem<R> carve(unsigned char* base, int Kmax, bool tc = false) {
+__device__ SweepSmem<R> carve(unsigned char* base, int Kmax, bool tc = false, int bm = 0) {
     SweepSmem<R> s;
     size_t o = 0;
     auto take = [&](size_t bytes) { unsigned char* p = base + o; o += align16(bytes); return p; };
-    const int bm = gj_panel_width(Kmax, tc);
+    if (bm <= 0) bm = gj_panel_width(Kmax, tc);
     s.gj.tcs = nullptr;
     s.tcs = nullptr;
     s.gj.bmax = bm;

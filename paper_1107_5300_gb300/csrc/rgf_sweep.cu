@@ -118,25 +118,32 @@ __device__ inline double max_abs2(const zd* A, int K, int ld, double* red) {
     return block_max(m, red);
 }
 
-}  // namespace
+// Everything the sweep kernels read besides their own shared memory.
+struct SweepArgs {
+    const ChainDev* chains;
+    const int* order;
+    int nchains, Kmax;
+    double eta_d;
+    const zd* leadout;
+    const int* lead_status;
+    const LeadDev* leads;
+    void* ws;
+    double* T;
+    int32_t* status;
+};
 
-// The lead-attached first column of each half, in binary64: h = 0 the left
-// lead's column 0 (KL even-row left atoms), h = 1 the right lead's column
+// The lead-attached first column of half h of chain ci, in binary64: h = 0 the
+// left lead's column 0 (KL even-row left atoms), h = 1 the right lead's column
 // n-1 (KR odd-row right atoms).  Writes g (site basis) and P (rows in the
 // lead's mode basis) into the half's G and P in the working precision R, and
-// the Gauss-Jordan flags into the half's flag word.
+// the Gauss-Jordan flags into the half's flag word.  bm: the launch's panel
+// width.  Every thread; ends with a barrier.
 template <class R>
-__global__ void __launch_bounds__(NT, 1)
-prep_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int Kmax,
-            double eta_d, const zd* __restrict__ leadout, const int* __restrict__ lead_status,
-            const LeadDev* __restrict__ leads, void* __restrict__ ws) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    SweepSmem<double> s = carve<double>(smem_raw, Kmax, false);
-    const int ci = order[blockIdx.x >> 1], h = blockIdx.x & 1;
-    const ChainDev ch = chains[ci];
-    if (lead_state(lead_status, ch.lead) != ST_OK) return;     // reported by the merge
-    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d, h);
-    const Half<R> hw = half_of<R>(ws, ch, h);
+__device__ __noinline__ void prep_body(const SweepArgs a, int ci, int h, int bm) {
+    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, false, bm);
+    const ChainDev& ch = a.chains[ci];
+    const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, h);
+    const Half<R> hw = half_of<R>(a.ws, ch, h);
     zd* X = reinterpret_cast<zd*>(hw.X);
     zd* G = reinterpret_cast<zd*>(hw.G);
     zd* P = reinterpret_cast<zd*>(hw.P);
@@ -185,27 +192,30 @@ prep_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     to_working<R>(hw.G, K, K, KL);
     to_working<R>(hw.P, K, K, KL);
     if (threadIdx.x == 0) *hw.flag = flag;
+    __syncthreads();
 }
 
-// The recursion of one half (h = blockIdx.x & 1) from its second column to
-// the cut: columns 1 .. m-1 (left) or n-2 .. m (right), in pairs of t I-bonded
-// columns wherever pair_ok allows (pair_column in rgf_steps.cuh), else one
-// column at a time.
+// The recursion of half h of chain ci from its second column to the cut:
+// columns 1 .. m-1 (left) or n-2 .. m (right), in pairs of t I-bonded columns
+// wherever the chain's schedule and pair_ok allow (pair_column in
+// rgf_steps.cuh), else one column at a time.  bm: the launch's panel width
+// (the chain's schedule may narrow it); tst: the block's tensor-core state
+// (TC).  ORs the Gauss-Jordan
+// and tensor-core flags into the half's flag word.  Every thread; ends with a
+// barrier.
 template <class R, bool TC>
-__global__ void __launch_bounds__(NT, 1)
-half_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int Kmax,
-            double eta_d, const zd* __restrict__ leadout, const int* __restrict__ lead_status,
-            const LeadDev* __restrict__ leads, void* __restrict__ ws) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    SweepSmem<R> s = carve<R>(smem_raw, Kmax, TC);
-    const int ci = order[blockIdx.x >> 1], h = blockIdx.x & 1;
-    const ChainDev ch = chains[ci];
-    if (lead_state(lead_status, ch.lead) != ST_OK) return;
-    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d, h);
-    const Half<R> hw = half_of<R>(ws, ch, h);
+__device__ __forceinline__ void half_body(const SweepArgs& a, int ci, int h, int bm, tc::State* tst) {
+    SweepSmem<R> s = carve<R>(rgf_dyn_smem, a.Kmax, TC, bm);
+    const ChainDev& ch = a.chains[ci];
+    const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, h);
+    const Half<R> hw = half_of<R>(a.ws, ch, h);
     const int m = left_cols(c.ncol), steps = h ? c.ncol - m : m;
-    tc::State tst;
-    if constexpr (TC) tc_attach<R>(Kmax, s, tst);
+    if (ch.panel > 0 && ch.panel < bm) s.gj.bmax = ch.panel;
+    const bool pairs_on = ch.pairs != 0;
+    if constexpr (TC) {
+        s.gj.tcs = tst;
+        s.tcs = tst;
+    }
     int flag = 0;
     for (int j = 1; j < steps;) {
         const int k = h ? c.ncol - 1 - j : j;
@@ -213,7 +223,7 @@ half_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
         // (c0-c1 or c2-c3 of one cell); the second column of the first pair of
         // each half is the one after the prepared end column
         const int kb = h ? k - 1 : k + 1;
-        const bool pairable = j + 1 < steps && (h ? (k & 1) == 1 : (k & 1) == 0);
+        const bool pairable = pairs_on && j + 1 < steps && (h ? (k & 1) == 1 : (k & 1) == 0);
         load_col(c, k, s.kc, s.eps);
         load_col(c, prev_col(c, k), s.kp, nullptr);
         if (pairable) load_col(c, kb, s.kn, nullptr);
@@ -227,32 +237,33 @@ half_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
         j += pair ? 2 : 1;
     }
     if constexpr (TC) {
-        if (*(volatile int*)tst.ar.err()) flag |= 4;
-        tc::teardown(tst.ar);
+        if (*(volatile int*)tst->ar.err()) flag |= 4;
     }
+    __syncthreads();
     if (threadIdx.x == 0) *hw.flag |= flag;
+    __syncthreads();
 }
 
-// The Dyson step across the bond between columns m-1 and m, in binary64, and
-// the trace.  Scratch: the two halves' X and, once read, their G and P.
+// The Dyson step across the bond between columns m-1 and m of chain ci, in
+// binary64, and the trace; writes T and the status word.  Scratch: the two
+// halves' X and, once read, their G and P.  bm: the launch's panel width.
+// Every thread; ends with a barrier.
 template <class R>
-__global__ void __launch_bounds__(NT, 1)
-merge_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, int Kmax,
-             double eta_d, const zd* __restrict__ leadout, const int* __restrict__ lead_status,
-             const LeadDev* __restrict__ leads, void* __restrict__ ws, double* __restrict__ Tout,
-             int32_t* __restrict__ status) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    SweepSmem<double> s = carve<double>(smem_raw, Kmax, false);
+__device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
+    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, false, bm);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ci = order[blockIdx.x];
-    const ChainDev ch = chains[ci];
-    const int lst = lead_state(lead_status, ch.lead);
+    const ChainDev& ch = a.chains[ci];
+    const int lst = lead_state(a.lead_status, ch.lead);
     if (lst != ST_OK) {
-        if (threadIdx.x == 0) { Tout[ci] = NAN; if (status) status[ci] = lst; }
+        if (threadIdx.x == 0) {
+            a.T[ci] = NAN;
+            if (a.status) a.status[ci] = lst;
+        }
+        __syncthreads();
         return;
     }
-    const ChainCtx c = make_ctx(ch, leads[ch.lead], leadout, eta_d, 0);
-    const Half<R> L = half_of<R>(ws, ch, 0), Rt = half_of<R>(ws, ch, 1);
+    const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, 0);
+    const Half<R> L = half_of<R>(a.ws, ch, 0), Rt = half_of<R>(a.ws, ch, 1);
     const int KL = c.KL, KR = c.KR, m = left_cols(c.ncol);
     const int K = col_size(c, m), Kp = col_size(c, m - 1), ct = m & 3;
     int flag = *L.flag | *Rt.flag;
@@ -327,9 +338,81 @@ merge_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order,
     const double T = block_sum(acc, s.red);
     if (threadIdx.x == 0) {
         const int st = chain_status(c, flag, T);
-        Tout[ci] = (st == ST_OK) ? T : NAN;
-        if (status) status[ci] = st;
+        a.T[ci] = (st == ST_OK) ? T : NAN;
+        if (a.status) a.status[ci] = st;
     }
+    __syncthreads();
+}
+
+}  // namespace
+
+// Three-launch schedule: each kernel runs one step for every half (or chain),
+// blocks in the order of `order`.
+template <class R>
+__global__ void __launch_bounds__(NT, 1) prep_kernel(SweepArgs a, int bm) {
+    const int ci = a.order[blockIdx.x >> 1], h = blockIdx.x & 1;
+    if (lead_state(a.lead_status, a.chains[ci].lead) != ST_OK) return;     // reported by the merge
+    prep_body<R>(a, ci, h, bm);
+}
+
+template <class R, bool TC>
+__global__ void __launch_bounds__(NT, 1) half_kernel(SweepArgs a, int bm) {
+    const int ci = a.order[blockIdx.x >> 1], h = blockIdx.x & 1;
+    if (lead_state(a.lead_status, a.chains[ci].lead) != ST_OK) return;
+    tc::State tst;
+    if constexpr (TC) {
+        SweepSmem<R> s = carve<R>(rgf_dyn_smem, a.Kmax, TC, bm);
+        tc_attach<R>(a.Kmax, s, tst);
+    }
+    half_body<R, TC>(a, ci, h, bm, &tst);
+    if constexpr (TC) tc::teardown(tst.ar);
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT, 1) merge_kernel(SweepArgs a, int bm) {
+    merge_body<R>(a, a.order[blockIdx.x], bm);
+}
+
+// Persistent schedule: gridDim.x blocks (at most one per SM) take halves from
+// the work queue (queue[0] = next item; item 2i + h = half h of chain
+// order[i], so the halves go out longest chain first) until it is empty.  A
+// block prepares its half's end column, runs its recursion, and counts the
+// half done on its chain (queue[1 + ci]); the block that brings the count to
+// two -- its partner half is complete by then -- joins the halves and writes T
+// and the status word.  Nothing waits: a block never spins on another block,
+// the queue and the counters only hand out work.  The release of a finished
+// half (its workspace, by every thread) to the joining block is the block
+// barrier, a device-scope fence and the counter's atomic on one side, the
+// atomic and a fence on the other.  With TC the block holds TMEM for the
+// whole launch.
+template <class R, bool TC>
+__global__ void __launch_bounds__(NT, 1) batch_kernel(SweepArgs a, int bm, int* queue) {
+    __shared__ int s_item, s_join;
+    tc::State tst;
+    if constexpr (TC) {
+        SweepSmem<R> s = carve<R>(rgf_dyn_smem, a.Kmax, TC, bm);
+        tc_attach<R>(a.Kmax, s, tst);
+    }
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&queue[0], 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= 2 * a.nchains) break;
+        const int ci = a.order[item >> 1], h = item & 1;
+        if (lead_state(a.lead_status, a.chains[ci].lead) == ST_OK) {
+            prep_body<R>(a, ci, h, bm);
+            half_body<R, TC>(a, ci, h, bm, &tst);
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_join = atomicAdd(&queue[1 + ci], 1);
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_join == 1) merge_body<R>(a, ci, bm);
+        __syncthreads();                 // s_item and s_join are rewritten next
+    }
+    if constexpr (TC) tc::teardown(tst.ar);
 }
 
 namespace {
@@ -339,18 +422,59 @@ cudaError_t set_smem(K kern, size_t smem) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// Panel width of a launch of `precision` (2 = RGF_MIXED_TC) and the shared
+// memory of its binary64 steps and of its recursion.
+int launch_panel(int precision, int Kmax) { return gj_panel_width(Kmax, precision == 2); }
+size_t f64_smem(int precision, int Kmax) {
+    return sweep_total_bytes(Kmax, launch_panel(precision, Kmax), false);
+}
+size_t rec_smem(int precision, int Kmax) {
+    const size_t b = sweep_total_bytes(Kmax, launch_panel(precision, Kmax), precision == 2);
+    // a tensor-core block holds all 512 TMEM columns: ask for more than half
+    // of an SM's shared memory so that no second block shares its SM (the
+    // register file already allows only one)
+    return precision == 2 && b < 120 * 1024 ? 120 * 1024 : b;
+}
+
+SweepArgs make_args(const ChainDev* chains, const int* order, int nchains, int Kmax,
+                    double eta_device, const void* leadout, const int* lead_status,
+                    const LeadDev* leads, void* ws, double* T, int32_t* status) {
+    return SweepArgs{chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status,
+                     leads, ws, T, status};
+}
+
 }  // namespace
+
+cudaError_t configure_sweep(int precision, int Kmax) {
+    const size_t f64 = f64_smem(precision, Kmax), rec = rec_smem(precision, Kmax);
+    const size_t both = rec > f64 ? rec : f64;
+    cudaError_t e;
+    if (precision == 0) {
+        if ((e = set_smem(prep_kernel<double>, f64)) != cudaSuccess) return e;
+        if ((e = set_smem(merge_kernel<double>, f64)) != cudaSuccess) return e;
+        if ((e = set_smem(half_kernel<double, false>, rec)) != cudaSuccess) return e;
+        return set_smem(batch_kernel<double, false>, both);
+    }
+    if ((e = set_smem(prep_kernel<df32>, f64)) != cudaSuccess) return e;
+    if ((e = set_smem(merge_kernel<df32>, f64)) != cudaSuccess) return e;
+    if (precision == 2) {
+        if ((e = set_smem(half_kernel<df32, true>, rec)) != cudaSuccess) return e;
+        return set_smem(batch_kernel<df32, true>, both);
+    }
+    if ((e = set_smem(half_kernel<df32, false>, rec)) != cudaSuccess) return e;
+    return set_smem(batch_kernel<df32, false>, both);
+}
 
 cudaError_t launch_prep(int precision, const ChainDev* chains, const int* order, int nchains,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
                         const LeadDev* leads, void* ws, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    const size_t smem = sweep_smem_bytes(Kmax, false);
-    auto kern = precision == 0 ? prep_kernel<double> : prep_kernel<df32>;
-    cudaError_t e = set_smem(kern, smem);
+    cudaError_t e = configure_sweep(precision, Kmax);
     if (e != cudaSuccess) return e;
-    kern<<<2 * nchains, NT, smem, st>>>(chains, order, Kmax, eta_device, (const zd*)leadout,
-                                        lead_status, leads, ws);
+    const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
+                                  leads, ws, nullptr, nullptr);
+    auto kern = precision == 0 ? prep_kernel<double> : prep_kernel<df32>;
+    kern<<<2 * nchains, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
     return cudaGetLastError();
 }
 
@@ -358,14 +482,13 @@ cudaError_t launch_half(int precision, const ChainDev* chains, const int* order,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
                         const LeadDev* leads, void* ws, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    const bool tc = precision == 2;
-    const size_t smem = sweep_smem_bytes(Kmax, tc);
-    auto kern = precision == 0 ? half_kernel<double, false>
-                               : (tc ? half_kernel<df32, true> : half_kernel<df32, false>);
-    cudaError_t e = set_smem(kern, smem);
+    cudaError_t e = configure_sweep(precision, Kmax);
     if (e != cudaSuccess) return e;
-    kern<<<2 * nchains, NT, smem, st>>>(chains, order, Kmax, eta_device, (const zd*)leadout,
-                                        lead_status, leads, ws);
+    const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
+                                  leads, ws, nullptr, nullptr);
+    auto kern = precision == 0 ? half_kernel<double, false>
+                               : (precision == 2 ? half_kernel<df32, true> : half_kernel<df32, false>);
+    kern<<<2 * nchains, NT, rec_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
     return cudaGetLastError();
 }
 
@@ -374,12 +497,29 @@ cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    const size_t smem = sweep_smem_bytes(Kmax, false);
-    auto kern = precision == 0 ? merge_kernel<double> : merge_kernel<df32>;
-    cudaError_t e = set_smem(kern, smem);
+    cudaError_t e = configure_sweep(precision, Kmax);
     if (e != cudaSuccess) return e;
-    kern<<<nchains, NT, smem, st>>>(chains, order, Kmax, eta_device, (const zd*)leadout,
-                                    lead_status, leads, ws, T, status);
+    const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
+                                  leads, ws, T, status);
+    auto kern = precision == 0 ? merge_kernel<double> : merge_kernel<df32>;
+    kern<<<nchains, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(int precision, const ChainDev* chains, const int* order, int nchains,
+                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                         const LeadDev* leads, void* ws, double* T, int32_t* status, int* queue,
+                         int nsm, cudaStream_t st) {
+    if (nchains <= 0) return cudaSuccess;
+    cudaError_t e = configure_sweep(precision, Kmax);
+    if (e != cudaSuccess) return e;
+    const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
+                                  leads, ws, T, status);
+    const size_t f64 = f64_smem(precision, Kmax), rec = rec_smem(precision, Kmax);
+    const int grid = nsm < 2 * nchains ? (nsm > 0 ? nsm : 1) : 2 * nchains;
+    auto kern = precision == 0 ? batch_kernel<double, false>
+                               : (precision == 2 ? batch_kernel<df32, true> : batch_kernel<df32, false>);
+    kern<<<grid, NT, rec > f64 ? rec : f64, st>>>(a, launch_panel(precision, Kmax), queue);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,20 @@ EXPORTS = ["rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "r
            "rgf_conductance_grad", "rgf_conductance_grad_dev", "rgf_ldos", "rgf_conductance_noalloc", "rgf_zgemm_tc",
            "rgf_zgemm_tc_selftest_timeout", "rgf_profile_enable", "rgf_profile_read",
            "rgf_profile_read_phases", "rgf_set_lead_controls", "rgf_status_str", "rgf_last_error",
-           "rgf_version"]
+           "rgf_version", "rgf_set_schedule", "rgf_get_schedule", "rgf_batch_create",
+           "rgf_batch_launch", "rgf_batch_free", "rgf_set_tuning", "rgf_get_tuning",
+           "rgf_tune_lookup", "rgf_autotune"]
+RGF_SCHED_PERSISTENT, RGF_SCHED_PHASED = 0, 1
+RGF_ENGINE_PIPES, RGF_ENGINE_TENSOR = 0, 1
+RGF_TUNE_MAX_ENTRIES, RGF_TUNE_MAX_CANDIDATES = 64, 12
+
+
+class TuneEntry(C.Structure):
+    """rgf_tune_entry: the schedule of the chains with ceil(N/2) <= K_max."""
+    _fields_ = [("K_max", C.c_int), ("engine", C.c_int), ("panel", C.c_int), ("pairs", C.c_int)]
+
+    def as_dict(self):
+        return {"K_max": self.K_max, "engine": self.engine, "panel": self.panel, "pairs": self.pairs}
 
 
 class _Desc(C.Structure):
@@ -77,6 +90,25 @@ lib.rgf_profile_read_phases.argtypes = [_dp]
 lib.rgf_profile_read_phases.restype = C.c_int
 lib.rgf_set_lead_controls.argtypes = [C.c_int, C.c_double]
 lib.rgf_set_lead_controls.restype = C.c_int
+lib.rgf_set_schedule.argtypes = [C.c_int]
+lib.rgf_set_schedule.restype = C.c_int
+lib.rgf_get_schedule.argtypes = []
+lib.rgf_get_schedule.restype = C.c_int
+lib.rgf_batch_create.argtypes = [C.POINTER(_vp), _vp, C.c_int, C.c_double, C.c_double, C.c_int,
+                                 _vp, _vp, C.POINTER(_vp)]
+lib.rgf_batch_create.restype = C.c_int
+lib.rgf_batch_launch.argtypes = [_vp, _vp]
+lib.rgf_batch_launch.restype = C.c_int
+lib.rgf_batch_free.argtypes = [_vp]
+lib.rgf_batch_free.restype = None
+lib.rgf_set_tuning.argtypes = [C.c_int, C.POINTER(TuneEntry), C.c_int]
+lib.rgf_set_tuning.restype = C.c_int
+lib.rgf_get_tuning.argtypes = [C.c_int, C.POINTER(TuneEntry), C.c_int, _ip]
+lib.rgf_get_tuning.restype = C.c_int
+lib.rgf_tune_lookup.argtypes = [C.c_int, C.c_int, C.POINTER(TuneEntry)]
+lib.rgf_tune_lookup.restype = C.c_int
+lib.rgf_autotune.argtypes = [C.c_int, _ip, C.c_int, C.c_int, C.c_int, C.POINTER(TuneEntry), _dp, _ip]
+lib.rgf_autotune.restype = C.c_int
 lib.rgf_status_str.restype = C.c_char_p
 lib.rgf_status_str.argtypes = [C.c_int]
 lib.rgf_last_error.restype = C.c_char_p
@@ -315,3 +347,96 @@ def zgemm_tc(A_ptr, B_ptr, C_ptr, m, n, k, lda=None, ldb=None, ldc=None, stream=
     if check:
         _check(st)
     return st
+
+
+def set_schedule(schedule):
+    """RGF_SCHED_PERSISTENT (default) or RGF_SCHED_PHASED for the forward sweep (process-wide)."""
+    _check(lib.rgf_set_schedule(int(schedule)))
+
+
+def get_schedule():
+    return int(lib.rgf_get_schedule())
+
+
+def _table(entries):
+    arr = (TuneEntry * max(len(entries), 1))()
+    for i, e in enumerate(entries):
+        d = e.as_dict() if isinstance(e, TuneEntry) else e
+        arr[i] = TuneEntry(int(d["K_max"]), int(d["engine"]), int(d["panel"]), int(d["pairs"]))
+    return arr
+
+
+def set_tuning(precision, entries):
+    """Installs a tuning table (list of dicts with K_max, engine, panel, pairs; [] removes it)."""
+    arr = _table(entries)
+    _check(lib.rgf_set_tuning(int(precision), arr, len(entries)))
+
+
+def get_tuning(precision):
+    arr = (TuneEntry * RGF_TUNE_MAX_ENTRIES)()
+    n = C.c_int(0)
+    _check(lib.rgf_get_tuning(int(precision), arr, RGF_TUNE_MAX_ENTRIES, C.byref(n)))
+    return [arr[i].as_dict() for i in range(n.value)]
+
+
+def tune_lookup(precision, N):
+    """The schedule a ribbon of width N gets from the installed table."""
+    e = TuneEntry()
+    _check(lib.rgf_tune_lookup(int(precision), int(N), C.byref(e)))
+    return e.as_dict()
+
+
+def autotune(precision, widths, cells=4, reps=2):
+    """Times every candidate schedule on one chain per width, installs the
+    fastest per column size and returns (table, ms [len(widths), ncand])."""
+    Ns = np.ascontiguousarray(widths, dtype=np.int32)
+    best = (TuneEntry * len(Ns))()
+    ms = np.full((len(Ns), RGF_TUNE_MAX_CANDIDATES), np.nan)
+    nc = C.c_int(0)
+    _check(lib.rgf_autotune(int(precision), Ns.ctypes.data_as(_ip), len(Ns), int(cells), int(reps),
+                            best, _ptr(ms, C.c_double), C.byref(nc)))
+    ms = ms.reshape(-1)[: len(Ns) * nc.value].reshape(len(Ns), nc.value)
+    return [best[i].as_dict() for i in range(len(Ns))], ms
+
+
+def save_tuning(path, precisions=(RGF_FP64, RGF_MIXED, RGF_MIXED_TC)):
+    """Writes the installed tables to a JSON file."""
+    import json
+    Path(path).write_text(json.dumps({str(p): get_tuning(p) for p in precisions}, indent=1))
+
+
+def load_tuning(path):
+    """Installs the tables of a JSON file written by save_tuning."""
+    import json
+    for p, entries in json.loads(Path(path).read_text()).items():
+        set_tuning(int(p), entries)
+
+
+class Batch:
+    """A prepared batch (rgf_batch_create): the forward path of a fixed list of
+    chains as one CUDA graph.  E_ptr, T_ptr, status_ptr: device pointers the
+    graph keeps; launch() re-reads the energies and the ribbons each time."""
+
+    def __init__(self, ribbons, E_ptr, n, T_ptr, status_ptr=0, eta_device=1e-8, eta_lead=1e-8,
+                 precision=RGF_FP64):
+        self._ribbons = list(ribbons)          # kept alive with the graph
+        hs = _handles(self._ribbons)
+        h = _vp()
+        _check(lib.rgf_batch_create(hs, _vp(E_ptr), int(n), float(eta_device), float(eta_lead),
+                                    int(precision), _vp(T_ptr),
+                                    _vp(status_ptr) if status_ptr else None, C.byref(h)))
+        self._h = h
+
+    def launch(self, stream=0):
+        _check(lib.rgf_batch_launch(self._h, _vp(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.rgf_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
