@@ -80,12 +80,12 @@ def parse():
                     help="batched_uneven_chains: number of chains (default 2048)")
     ap.add_argument("--grad", action="store_true",
                     help="time rgf_conductance_grad on the workload (its gradient energies)")
-    ap.add_argument("--schedule", default="persistent", choices=["persistent", "phased"],
-                    help="persistent: the batch kernel with its work queue (default); phased: "
-                         "three launches per step")
+    ap.add_argument("--schedule", default="phased", choices=["persistent", "phased"],
+                    help="phased: three launches per step (default); persistent: the batch kernel "
+                         "with its device work queue")
     ap.add_argument("--no-graph", action="store_true",
-                    help="persistent schedule through rgf_conductance_dev instead of a prepared "
-                         "CUDA-graph batch")
+                    help="each step through rgf_conductance_dev instead of a prepared CUDA-graph "
+                         "batch")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default schedule instead of the autotuner's choice for the width")
     ap.add_argument("--check-chains", type=int, default=0,
@@ -287,7 +287,7 @@ def run_uneven(args):
         eng = {rgf.tune_lookup(prec, int(N))["engine"] for N in Ns}
         groups = len(eng)
     rgf.profile_enable(True)
-    use_graph = args.schedule == "persistent" and not args.no_graph
+    use_graph = not args.no_graph
     if use_graph:
         batch = rgf.Batch(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8, prec)
 
@@ -491,7 +491,7 @@ def main():
                  "candidates": "engine (tensor, pipes) x panel (16, 8, 4) x pairs (1, 0)",
                  "tuning_s": round(time.perf_counter() - t0, 2)}
     rgf.profile_enable(True)
-    use_graph = args.schedule == "persistent" and not args.no_graph
+    use_graph = not args.no_graph
     if use_graph:
         batch = rgf.Batch(ribs, Ed.data_ptr(), n, Td.data_ptr(), Sd.data_ptr(), 1e-8, 1e-8, prec)
 

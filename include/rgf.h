@@ -175,17 +175,21 @@ rgf_status rgf_conductance_dev(const rgf_ribbon* const* rib, const double* E_dev
 
 /*
  * Schedule of the forward sweep of rgf_conductance[_dev] (no counterpart in
- * the paper; process-wide, default RGF_SCHED_PERSISTENT).  Both run the same
+ * the paper; process-wide, default RGF_SCHED_PHASED).  Both run the same
  * arithmetic in separately compiled kernels, so their T agree to rounding (the
  * compiler may fuse a product and a sum into one FMA in one of them only);
  * each is deterministic, whatever order the queue hands the work out in.
+ *   RGF_SCHED_PHASED: three launches (end-column preparation, half sweeps,
+ *     joins), blocks longest chain first; the hardware block scheduler hands
+ *     each freed SM the next half.
  *   RGF_SCHED_PERSISTENT: after the lead decimation, one persistent kernel per
  *     launch group (one block per SM) takes the halves of the chains from a
  *     device work queue, longest chain first; the block that finishes the
  *     second half of a chain joins the two and writes T.  No block waits for
- *     another, so there is no queue wait that could time out.
- *   RGF_SCHED_PHASED: three launches (end-column preparation, half sweeps,
- *     joins), blocks in the same order.
+ *     another, so there is no queue wait that could time out.  It overlaps the
+ *     preparations and joins with other chains' sweeps, but its recursion,
+ *     compiled inside the queue loop beside the binary64 steps, runs about 7%
+ *     slower on GB300 than the phased kernel's, hence the default.
  * A launch group is the set of chains on one engine: with RGF_MIXED_TC, the
  * chains that the tuning table (rgf_set_tuning) sends to the FP32 pipes run
  * after the tensor-core group, as RGF_MIXED.  Errors: RGF_EINVAL.
@@ -196,8 +200,9 @@ int rgf_get_schedule(void);
 
 /*
  * A prepared batch: the conductance of a fixed list of chains as one CUDA
- * graph (energies into the descriptors, lead decimation, work-queue reset,
- * persistent sweep), built once and launched any number of times.
+ * graph (energies into the descriptors, lead decimation, then the sweep in the
+ * schedule in force at creation: work-queue reset and persistent kernel, or
+ * the three launches), built once and launched any number of times.
  * rgf_batch_create plans the chains (schedule from the tuning table in force),
  * allocates and uploads the batch's descriptors and workspace (cudaMalloc;
  * about the device memory of one rgf_conductance_dev call), and captures the
@@ -211,7 +216,7 @@ int rgf_get_schedule(void);
  * rgf_profile_read_phases reads them after a launch.  rgf_batch_launch
  * enqueues the graph on `stream` and returns; launches of one batch share its
  * workspace and must not overlap (one stream, or events between streams).
- * Results equal those of rgf_conductance_dev with RGF_SCHED_PERSISTENT bit for
+ * Results equal those of rgf_conductance_dev under the same schedule bit for
  * bit.  Errors:
  * RGF_EINVAL (as rgf_conductance_dev; nchains must be >= 1), RGF_ENOMEM,
  * RGF_ECUDA (the capture or the launch failed).

@@ -115,7 +115,7 @@ struct DevBuf {
 // (thread-local).
 std::mutex g_tune_mu;
 std::vector<rgf_tune_entry> g_tune[3];
-int g_schedule = RGF_SCHED_PERSISTENT;
+int g_schedule = RGF_SCHED_PHASED;
 thread_local const rgf_tune_entry* g_force = nullptr;
 thread_local int g_force_schedule = -1;
 
@@ -988,8 +988,13 @@ rgf_status rgf_batch_create(const rgf_ribbon* const* rib, const double* E_dev, i
         return cuda_fail(e, "stream capture");
     }
     b->profiled = g_prof.on;
+    int sched;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        sched = g_schedule;
+    }
     s = enqueue_forward(b->plan, b->layout, b->mem, E_dev, eta_device, eta_lead, cs.st, T_dev,
-                        status_dev, RGF_SCHED_PERSISTENT, b->profiled ? 2 : 0);
+                        status_dev, sched, b->profiled ? 2 : 0);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cs.st, &g);
     b->graph = g;

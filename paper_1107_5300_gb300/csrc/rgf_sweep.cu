@@ -398,18 +398,26 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel(SweepArgs a, int bm, int* 
         __syncthreads();
         const int item = s_item;
         if (item >= 2 * a.nchains) break;
-        const int ci = a.order[item >> 1], h = item & 1;
-        if (lead_state(a.lead_status, a.chains[ci].lead) == ST_OK) {
-            prep_body<R>(a, ci, h, bm);
-            half_body<R, TC>(a, ci, h, bm, &tst);
+        {
+            const int ci = a.order[item >> 1], h = item & 1;
+            if (lead_state(a.lead_status, a.chains[ci].lead) == ST_OK) {
+                prep_body<R>(a, ci, h, bm);
+                half_body<R, TC>(a, ci, h, bm, &tst);
+            }
         }
+        // the chain is looked up again from the item in shared memory, so that
+        // nothing of the loop stays live in registers across the half sweep
         if (threadIdx.x == 0) {
+            const int cj = a.order[*(volatile int*)&s_item >> 1];
             __threadfence();
-            s_join = atomicAdd(&queue[1 + ci], 1);
+            s_join = cj | (atomicAdd(&queue[1 + cj], 1) << 30);
             __threadfence();
         }
         __syncthreads();
-        if (s_join == 1) merge_body<R>(a, ci, bm);
+        {
+            const int j = *(volatile int*)&s_join;
+            if ((j >> 30) == 1) merge_body<R>(a, j & ((1 << 30) - 1), bm);
+        }
         __syncthreads();                 // s_item and s_join are rewritten next
     }
     if constexpr (TC) tc::teardown(tst.ar);

@@ -350,7 +350,7 @@ def zgemm_tc(A_ptr, B_ptr, C_ptr, m, n, k, lda=None, ldb=None, ldc=None, stream=
 
 
 def set_schedule(schedule):
-    """RGF_SCHED_PERSISTENT (default) or RGF_SCHED_PHASED for the forward sweep (process-wide)."""
+    """RGF_SCHED_PHASED (default) or RGF_SCHED_PERSISTENT for the forward sweep (process-wide)."""
     _check(lib.rgf_set_schedule(int(schedule)))
 
 

@@ -14,7 +14,7 @@ T_HOP = -2.7
 @pytest.fixture
 def clean_state(rgflib):
     yield
-    rgflib.set_schedule(rgflib.RGF_SCHED_PERSISTENT)
+    rgflib.set_schedule(rgflib.RGF_SCHED_PHASED)
     for p in (rgflib.RGF_FP64, rgflib.RGF_MIXED, rgflib.RGF_MIXED_TC):
         rgflib.set_tuning(p, [])
 
@@ -53,7 +53,7 @@ def _both_schedules(rgflib, ribs, E, prec):
     for sched in (rgflib.RGF_SCHED_PERSISTENT, rgflib.RGF_SCHED_PHASED):
         rgflib.set_schedule(sched)
         out[sched] = _dev_call(rgflib, ribs, E, prec)
-    rgflib.set_schedule(rgflib.RGF_SCHED_PERSISTENT)
+    rgflib.set_schedule(rgflib.RGF_SCHED_PHASED)
     return out[rgflib.RGF_SCHED_PERSISTENT], out[rgflib.RGF_SCHED_PHASED]
 
 
@@ -71,6 +71,7 @@ def test_persistent_queue_equals_three_launches(rgflib, clean_state, prec):
     ribs, E, _ = _mixed_batch(rgflib, 200, 11)
     E[17] = np.nan
     (Tp, sp), (Tq, sq) = _both_schedules(rgflib, ribs, E, prec)
+    rgflib.set_schedule(rgflib.RGF_SCHED_PERSISTENT)
     Tp2, sp2 = _dev_call(rgflib, ribs, E, prec)            # persistent again
     assert np.array_equal(sp, sq) and np.array_equal(sp, sp2)
     assert sp[17] == rgflib.RGF_EINVAL and np.isnan(Tp[17])
@@ -83,6 +84,7 @@ def test_persistent_queue_equals_three_launches(rgflib, clean_state, prec):
 
 def test_persistent_queue_vs_oracle(rgflib, clean_state):
     ribs, E, host = _mixed_batch(rgflib, 320, 12, Nmax=24, Lmax=4)
+    rgflib.set_schedule(rgflib.RGF_SCHED_PERSISTENT)
     for prec, tol in ((rgflib.RGF_FP64, 1e-9), (rgflib.RGF_MIXED_TC, 1e-7)):
         T, st = rgflib.conductance(ribs, E, 1e-8, 1e-8, prec, check=False)
         for i in range(0, len(ribs), 16):        # a sample the oracle does in seconds
@@ -98,7 +100,10 @@ def test_persistent_queue_vs_oracle(rgflib, clean_state):
 def test_graph_batch_relaunch_follows_new_energies(rgflib, clean_state):
     torch = pytest.importorskip("torch")
     ribs, E, _ = _mixed_batch(rgflib, 40, 13)
-    for prec in (rgflib.RGF_FP64, rgflib.RGF_MIXED_TC):
+    for prec, sched in ((rgflib.RGF_FP64, rgflib.RGF_SCHED_PHASED),
+                        (rgflib.RGF_MIXED_TC, rgflib.RGF_SCHED_PHASED),
+                        (rgflib.RGF_MIXED_TC, rgflib.RGF_SCHED_PERSISTENT)):
+        rgflib.set_schedule(sched)                 # captured at creation, used by both calls
         dE = torch.tensor(E, dtype=torch.float64, device="cuda")
         dT = torch.full((len(E),), -1.0, dtype=torch.float64, device="cuda")
         dS = torch.full((len(E),), -1, dtype=torch.int32, device="cuda")

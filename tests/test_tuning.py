@@ -6,18 +6,18 @@ import pytest
 @pytest.fixture
 def lib(rgflib):
     yield rgflib
-    rgflib.set_schedule(rgflib.RGF_SCHED_PERSISTENT)
+    rgflib.set_schedule(rgflib.RGF_SCHED_PHASED)
     for p in (rgflib.RGF_FP64, rgflib.RGF_MIXED, rgflib.RGF_MIXED_TC):
         rgflib.set_tuning(p, [])
 
 
 def test_schedule_switch(lib):
-    assert lib.get_schedule() == lib.RGF_SCHED_PERSISTENT
-    lib.set_schedule(lib.RGF_SCHED_PHASED)
     assert lib.get_schedule() == lib.RGF_SCHED_PHASED
+    lib.set_schedule(lib.RGF_SCHED_PERSISTENT)
+    assert lib.get_schedule() == lib.RGF_SCHED_PERSISTENT
     with pytest.raises(lib.RGFError):
         lib.set_schedule(7)
-    assert lib.get_schedule() == lib.RGF_SCHED_PHASED
+    assert lib.get_schedule() == lib.RGF_SCHED_PERSISTENT
 
 
 def test_default_entry_without_a_table(lib):
