@@ -160,10 +160,12 @@ def test_engine_groups_split_one_call(rgflib, clean_state):
     narrow = [i for i, r in enumerate(ribs) if (r.N + 1) // 2 <= 12]
     wide = [i for i, r in enumerate(ribs) if (r.N + 1) // 2 > 12]
     assert narrow and wide
-    for idx in (narrow, wide):
-        T1, s1 = rgflib.conductance([ribs[i] for i in idx], E[idx], 1e-8, 1e-8, rgflib.RGF_MIXED_TC,
-                                    check=False)
-        assert np.array_equal(T1, Tp[idx])
+    for sched, Tref in ((rgflib.RGF_SCHED_PHASED, Tq), (rgflib.RGF_SCHED_PERSISTENT, Tp)):
+        rgflib.set_schedule(sched)
+        for idx in (narrow, wide):
+            T1, s1 = rgflib.conductance([ribs[i] for i in idx], E[idx], 1e-8, 1e-8,
+                                        rgflib.RGF_MIXED_TC, check=False)
+            assert np.array_equal(T1, Tref[idx])
 
 
 def test_autotune_installs_a_table_that_stays_correct(rgflib, clean_state):
