@@ -601,7 +601,11 @@ def main():
     smax = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * smax * 1e6 * 8.0 / 54.0 / 1e12
     if prec == rgf.RGF_FP64:
-        bound, peak, peak_src = "alu", 1.25, "nominal GB300 FP64 rate (no measured figure)"
+        # binary64 runs on the FP64 pipe: its bound is the executed binary64
+        # flop rate (pair steps), not the unit-cell count
+        achieved = pair_step_flops_per_cell(N) * steps_ok / half_s / 1e12
+        bound, peak, peak_src = "alu", 1.25, ("nominal GB300 FP64 rate (no measured figure); achieved "
+                                              "at the executed pair-step count")
     else:
         bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         peak_src = f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peaks_src})"
