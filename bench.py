@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tc", choices=["tc", "mixed", "fp64"])
+    ap.add_argument("--precision", default="tc", choices=["tc", "mixed", "fp64", "fp64tc"])
     ap.add_argument("--workload", default="agnr245_L4000_anderson")
     ap.add_argument("--cells", type=int, default=0, help="override L (profiling runs)")
     ap.add_argument("--energies", type=int, default=0, help="use only the first n energies")
@@ -257,7 +257,8 @@ def run_uneven(args):
     from paper_1107_5300_gb300 import rgf
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    prec = {"mixed": rgf.RGF_MIXED, "tc": rgf.RGF_MIXED_TC, "fp64": rgf.RGF_FP64}[args.precision]
+    prec = {"mixed": rgf.RGF_MIXED, "tc": rgf.RGF_MIXED_TC, "fp64": rgf.RGF_FP64,
+            "fp64tc": rgf.RGF_FP64_TC}[args.precision]
     chains = workloads.batched_uneven_chains(args.chains or 2048, seed=3)
     ribs, Es, cells, Ns = [], [], [], []
     for ch in chains:
@@ -283,7 +284,7 @@ def run_uneven(args):
         table, _ = rgf.autotune(prec, widths, cells=4, reps=2)
         tuned = {"table": table, "tuning_s": round(time.perf_counter() - t0, 2)}
     groups = 1
-    if prec == rgf.RGF_MIXED_TC:
+    if prec in (rgf.RGF_MIXED_TC, rgf.RGF_FP64_TC):
         eng = {rgf.tune_lookup(prec, int(N))["engine"] for N in Ns}
         groups = len(eng)
     rgf.profile_enable(True)
@@ -342,7 +343,7 @@ def run_uneven(args):
     out = {"metric": "RGF slice-inversions/s (uneven batch, M in [102, 802])", "value": units * args.steps / t,
            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if prec == rgf.RGF_FP64 else "f32x2", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f64" if prec in (rgf.RGF_FP64, rgf.RGF_FP64_TC) else "f32x2", "data": "synthetic",
            "config": {"workload": "batched_uneven_chains", "chains": n, "chains_ok": int(ok.sum()),
                       "cells_cap": args.cells or None, "cells_total": int(cells.sum()),
                       "precision": args.precision, "l2": "flushed (256 MB write) between steps",
@@ -372,7 +373,8 @@ def run_grad(args):
     from paper_1107_5300_gb300 import rgf
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    prec = {"mixed": rgf.RGF_MIXED, "tc": rgf.RGF_MIXED_TC, "fp64": rgf.RGF_FP64}[args.precision]
+    prec = {"mixed": rgf.RGF_MIXED, "tc": rgf.RGF_MIXED_TC, "fp64": rgf.RGF_FP64,
+            "fp64tc": rgf.RGF_FP64_TC}[args.precision]
     w = workloads.WORKLOADS[args.workload]
     N, L = w["N"], (args.cells or w["L"])
     eps = workloads.anderson_onsite(N, L, w["W"], w["seed"])
@@ -419,7 +421,7 @@ def run_grad(args):
            "value": float(ok.sum()) * L * args.steps / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if prec == rgf.RGF_FP64 else "f32x2", "data": "synthetic",
+           "dtype": "f64" if prec in (rgf.RGF_FP64, rgf.RGF_FP64_TC) else "f32x2", "data": "synthetic",
            "config": {"workload": args.workload, "N": N, "L": L, "energies": int(len(Es)),
                       "ckpt_stride": w.get("ckpt_stride", 0), "precision": args.precision,
                       "timing": "host wall clock around the host-buffer call"},
@@ -451,7 +453,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1107_5300_gb300 import rgf, shard
 
-    prec = {"mixed": rgf.RGF_MIXED, "tc": rgf.RGF_MIXED_TC, "fp64": rgf.RGF_FP64}[args.precision]
+    prec = {"mixed": rgf.RGF_MIXED, "tc": rgf.RGF_MIXED_TC, "fp64": rgf.RGF_FP64,
+            "fp64tc": rgf.RGF_FP64_TC}[args.precision]
     w = workloads.WORKLOADS[args.workload]
     N, L = w["N"], (args.cells or w["L"])
     Es_all = w["energies"]()
@@ -548,6 +551,7 @@ def main():
     # Parity of this arm against the FP64 GPU path on the same chains (untimed).
     parity = None
     if not args.no_check and prec != rgf.RGF_FP64:
+        # binary64 reference on the same chains, untimed (three launches)
         T64, s64 = rgf.conductance(ribs, Es, 1e-8, 1e-8, rgf.RGF_FP64, check=False)
         both = ok & (s64 == 0)
         d = np.abs(T - T64)
@@ -627,7 +631,7 @@ def main():
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             **({} if traffic is not None else {"traffic_note": traffic_note}),
-            "kernel": f"{kernel_tag}_kernel" + {0: "<double>", 1: "<df32>", 2: "<df32,tc>"}[prec],
+            "kernel": f"{kernel_tag}_kernel" + {0: "<double>", 1: "<df32>", 2: "<df32,tc>", 3: "<double,tc>"}[prec],
             "flops_per_step": F_alg,
             "flops_note": "F_alg(M) = 8/3 M^3 + 8 M^2 floor(N/2) + 8 ceil(N/2)^2 floor(N/2) per unit-cell "
                           "slice step (M = 2N); achieved = F_alg x slice steps / time of the kernel "
@@ -664,7 +668,7 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f64" if prec == rgf.RGF_FP64 else "f32x2", "data": "synthetic",
+               "dtype": "f64" if prec in (rgf.RGF_FP64, rgf.RGF_FP64_TC) else "f32x2", "data": "synthetic",
                "config": {"workload": args.workload, "N": N, "M": 2 * N, "L": L,
                           "energies": int(len(Es_all)), "chains_per_rank": int(n),
                           "chains_ok": int(ok.sum()), "W_eV": w["W"], "eta_eV": 1e-8,

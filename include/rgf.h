@@ -67,11 +67,17 @@ typedef enum {
     RGF_FP64 = 0,        /* every step in IEEE binary64                               */
     RGF_MIXED = 1,       /* slice recursion in double-float (pairs of binary32 on the
                             FP32 pipes, ~48-bit significand); leads and trace binary64 */
-    RGF_MIXED_TC = 2     /* as RGF_MIXED, with the dense contractions of every slice
+    RGF_MIXED_TC = 2,    /* as RGF_MIXED, with the dense contractions of every slice
                             step (the rank-b updates of the slice inverse, the
                             corner-strip product of Eq. 5, the gradient's products) on
                             the tcgen05 tensor cores by exact bfloat16 digit slicing
-                            (see rgf_zgemm_tc) */
+                            of the double-float operands (see rgf_zgemm_tc)          */
+    RGF_FP64_TC = 3      /* binary64 storage and ALU steps (as RGF_FP64), with the two
+                            dense contractions of every slice step on the tensor cores,
+                            sliced from binary64 and summed in binary64: products
+                            accurate to a few units of 2^-53 of (row max x column max
+                            x inner dimension).  The gradient and LDOS sweeps run it
+                            as RGF_FP64. */
 } rgf_precision;
 
 /* One ribbon instance (the paper's input step: geometry, defects, disorder). */
@@ -190,9 +196,10 @@ rgf_status rgf_conductance_dev(const rgf_ribbon* const* rib, const double* E_dev
  *     preparations and joins with other chains' sweeps, but its recursion,
  *     compiled inside the queue loop beside the binary64 steps, runs about 7%
  *     slower on GB300 than the phased kernel's, hence the default.
- * A launch group is the set of chains on one engine: with RGF_MIXED_TC, the
- * chains that the tuning table (rgf_set_tuning) sends to the FP32 pipes run
- * after the tensor-core group, as RGF_MIXED.  Errors: RGF_EINVAL.
+ * A launch group is the set of chains on one engine: with RGF_MIXED_TC or
+ * RGF_FP64_TC, the chains that the tuning table (rgf_set_tuning) sends to the
+ * pipes run after the tensor-core group, as RGF_MIXED or RGF_FP64.  Errors:
+ * RGF_EINVAL.
  */
 typedef enum { RGF_SCHED_PERSISTENT = 0, RGF_SCHED_PHASED = 1 } rgf_schedule;
 rgf_status rgf_set_schedule(int schedule);
@@ -291,12 +298,13 @@ rgf_status rgf_ldos(const rgf_ribbon* const* rib, const double* E, int nchains,
 /*
  * Complex matrix product C = A B on the tcgen05 tensor cores: the dense
  * product the recursion forms at every slice (Eqs. 4-5; the paper's CGEMM
- * calls), here by exact bfloat16 digit slicing of double-float operands
- * (Ozaki scheme: 7 signed base-256 digits per real value, per-row and
- * per-column power-of-two scales), binary32 tensor-core accumulation that is
- * exact for the five leading digit levels, and double-float recombination.
- * The binary64 inputs are first rounded to double-float (48-bit significand).
- * Accuracy per entry: a few units of 2^-48 times k max_j |A_mj| max_j |B_jn|.
+ * calls), here by exact bfloat16 digit slicing of the binary64 operands
+ * (Ozaki scheme: 7 signed base-256 digits per real value from its
+ * significand, per-row and per-column power-of-two scales), binary32
+ * tensor-core accumulation that is exact for the five leading digit levels,
+ * and binary64 recombination -- the product RGF_FP64_TC uses.  Accuracy per
+ * entry: a few units of 2^-53 times k max_j |A_mj| max_j |B_jn| (at most
+ * 2^-50 k max|A_m.| max|B_.n| per real part).
  *   A: device [m][lda], lda >= k;  B: device [k][ldb], ldb >= n;
  *   C: device [m][ldc], ldc >= n;  complex binary64, interleaved (re, im),
  *   row-major, leading dimensions in complex elements; C must not overlap
@@ -343,7 +351,8 @@ rgf_status rgf_zgemm_tc_selftest_timeout(void);
  * onsite_dev [L][2N] (binary64) and removed_dev [L][2N] (uint8, or NULL),
  * evaluated at nE energies E_dev [nE] (device).  Outputs on the device:
  * T_dev [nE], status_dev [nE] (int32, or NULL), as rgf_conductance_dev, in any
- * precision (RGF_FP64, RGF_MIXED, RGF_MIXED_TC), by the three launches of
+ * precision (RGF_FP64, RGF_MIXED, RGF_MIXED_TC, RGF_FP64_TC), by the three
+ * launches of
  * RGF_SCHED_PHASED with the default schedule of every chain (the tuning table
  * is not read).  Asynchronous on `stream`; results are valid once the stream
  * has passed the call.  Returns RGF_EINVAL,
@@ -403,7 +412,8 @@ rgf_status rgf_set_lead_controls(int max_iter, double residual_tol);
  * wider than the last entry take the last entry; with no table every chain
  * takes the default {engine RGF_ENGINE_TENSOR, panel 0, pairs 1}.
  *   engine: RGF_ENGINE_TENSOR (the dense products on the tcgen05 tensor cores)
- *           or RGF_ENGINE_PIPES (on the FP32 pipes); only RGF_MIXED_TC reads it.
+ *           or RGF_ENGINE_PIPES (on the FP32 / FP64 pipes); only RGF_MIXED_TC
+ *           and RGF_FP64_TC read it.
  *   panel:  Gauss-Jordan panel width 2, 4, 8 or 16, capped by the shared memory
  *           of the launch; 0 = the widest that fits.
  *   pairs:  1 = t I-bonded column pairs share one inverse (where no atom of the
@@ -418,7 +428,7 @@ rgf_status rgf_set_lead_controls(int max_iter, double residual_tol);
  *
  * rgf_autotune measures, for each width N[i], one Anderson-disordered chain
  * (W = 0.1 eV) of `cells` unit cells at E = 0.3 eV under every candidate --
- * engine (both with RGF_MIXED_TC) x panel {16, 8, 4} x pairs {1, 0}, *ncand
+ * engine (both with the _TC precisions) x panel {16, 8, 4} x pairs {1, 0}, *ncand
  * of them -- as the device time of its half sweeps (the middle launch of
  * RGF_SCHED_PHASED, CUDA events; the minimum of `reps` runs after one
  * warm-up), writes

@@ -107,14 +107,21 @@ struct DevBuf {
     }
 };
 
+bool valid_precision(int p) {
+    return p == RGF_FP64 || p == RGF_MIXED || p == RGF_MIXED_TC || p == RGF_FP64_TC;
+}
+bool tc_precision(int p) { return p == RGF_MIXED_TC || p == RGF_FP64_TC; }
+// The precision a tensor-core precision's chains run in on the pipes.
+int pipes_precision(int p) { return p == RGF_FP64_TC ? RGF_FP64 : p == RGF_MIXED_TC ? RGF_MIXED : p; }
+
 // Schedule of the forward sweep and the tuning tables (process-wide).  A
 // table, per precision, maps the column size K = ceil(N/2) of a chain to its
 // schedule: the first entry with K <= K_max, else the last entry; an empty
-// table means the default (tensor cores with RGF_MIXED_TC, widest panel,
+// table means the default (tensor cores with the _TC precisions, widest panel,
 // pair steps).  The autotuner's timing runs force one entry for every chain
 // (thread-local).
 std::mutex g_tune_mu;
-std::vector<rgf_tune_entry> g_tune[3];
+std::vector<rgf_tune_entry> g_tune[4];
 int g_schedule = RGF_SCHED_PHASED;
 thread_local const rgf_tune_entry* g_force = nullptr;
 thread_local int g_force_schedule = -1;
@@ -132,9 +139,9 @@ rgf_tune_entry lookup_tune(int precision, int K) {
 }
 
 // One launch group of the forward sweep: the chains that run on one engine,
-// longest first.  RGF_MIXED_TC chains tuned to the FP32 pipes form a second
-// group that runs as RGF_MIXED (same double-float arithmetic, products on the
-// pipes).
+// longest first.  Chains of a tensor-core precision tuned to the pipes form a
+// second group that runs as the matching pipes precision (RGF_MIXED_TC as
+// RGF_MIXED, RGF_FP64_TC as RGF_FP64: same arithmetic, products on the pipes).
 struct Group {
     int precision = 0;
     int Kmax = 1;
@@ -188,7 +195,7 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, int precision, P
             const rgf_tune_entry te = lookup_tune(precision, rgf::col_KL(r->N));
             ch.panel = (int8_t)te.panel;
             ch.pairs = (int8_t)(te.pairs != 0);
-            ch.tc = (int8_t)(precision == RGF_MIXED_TC && te.engine == RGF_ENGINE_TENSOR);
+            ch.tc = (int8_t)(tc_precision(precision) && te.engine == RGF_ENGINE_TENSOR);
             engine[c] = ch.tc;
             pl.seg_cols[c] = 0;
             pl.ws_elems += rgf::sweep_ws_elems(r->N);
@@ -212,10 +219,10 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, int precision, P
     std::stable_sort(pl.order.begin(), pl.order.end(),
                      [&](int a, int b) { return cost[a] > cost[b]; });
     if (!grad) {
-        const bool split = precision == RGF_MIXED_TC;
+        const bool split = tc_precision(precision);
         for (int pass = 0; pass < (split ? 2 : 1); ++pass) {
             Group g;
-            g.precision = split ? (pass == 0 ? RGF_MIXED_TC : RGF_MIXED) : precision;
+            g.precision = split ? (pass == 0 ? precision : pipes_precision(precision)) : precision;
             for (int c : pl.order)
                 if (!split || engine[c] == (pass == 0 ? 1 : 0)) {
                     g.order.push_back(c);
@@ -375,7 +382,7 @@ rgf_status check_call(const rgf_ribbon* const* rib, const void* E_dev, const voi
                       int nchains, int precision, double eta_device, double eta_lead) {
     if (nchains < 0) return fail(RGF_EINVAL, "nchains < 0");
     if (nchains > 0 && (!rib || !E_dev || !T_dev)) return fail(RGF_EINVAL, "NULL argument");
-    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+    if (!valid_precision(precision))
         return fail(RGF_EINVAL, "unknown precision");
     if (!(eta_device >= 0.0) || !(eta_lead > 0.0) || !std::isfinite(eta_device) ||
         !std::isfinite(eta_lead))
@@ -801,7 +808,7 @@ int rgf_get_schedule(void) {
 }
 
 rgf_status rgf_set_tuning(int precision, const rgf_tune_entry* table, int n) {
-    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+    if (!valid_precision(precision))
         return fail(RGF_EINVAL, "unknown precision");
     if (n < 0 || n > RGF_TUNE_MAX_ENTRIES || (n > 0 && !table))
         return fail(RGF_EINVAL, "n must be in [0, RGF_TUNE_MAX_ENTRIES] with a table");
@@ -821,7 +828,7 @@ rgf_status rgf_set_tuning(int precision, const rgf_tune_entry* table, int n) {
 }
 
 rgf_status rgf_get_tuning(int precision, rgf_tune_entry* table, int cap, int* n) {
-    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+    if (!valid_precision(precision))
         return fail(RGF_EINVAL, "unknown precision");
     if (!n || cap < 0 || (cap > 0 && !table)) return fail(RGF_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -833,7 +840,7 @@ rgf_status rgf_get_tuning(int precision, rgf_tune_entry* table, int cap, int* n)
 }
 
 rgf_status rgf_tune_lookup(int precision, int N, rgf_tune_entry* out) {
-    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+    if (!valid_precision(precision))
         return fail(RGF_EINVAL, "unknown precision");
     if (!out || N < 2) return fail(RGF_EINVAL, "bad argument");
     *out = lookup_tune(precision, rgf::col_KL(N));
@@ -842,7 +849,7 @@ rgf_status rgf_tune_lookup(int precision, int N, rgf_tune_entry* out) {
 
 rgf_status rgf_autotune(int precision, const int* N, int nN, int cells, int reps,
                         rgf_tune_entry* best, double* ms, int* ncand) {
-    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+    if (!valid_precision(precision))
         return fail(RGF_EINVAL, "unknown precision");
     if (nN < 1 || nN > RGF_TUNE_MAX_ENTRIES || !N || !best || cells < 1 || reps < 1)
         return fail(RGF_EINVAL, "bad argument to rgf_autotune");
@@ -859,11 +866,11 @@ rgf_status rgf_autotune(int precision, const int* N, int nN, int cells, int reps
             return fail(RGF_EINVAL, "two widths with the same column size ceil(N/2)");
     // the candidates: engine x panel width x pair steps
     std::vector<rgf_tune_entry> cand;
-    const int engines = precision == RGF_MIXED_TC ? 2 : 1;
+    const int engines = tc_precision(precision) ? 2 : 1;
     for (int en = 0; en < engines; ++en)
         for (int panel : {16, 8, 4})
             for (int pairs : {1, 0})
-                cand.push_back(rgf_tune_entry{0, precision == RGF_MIXED_TC ? 1 - en : 0, panel, pairs});
+                cand.push_back(rgf_tune_entry{0, tc_precision(precision) ? 1 - en : 0, panel, pairs});
     if (ncand) *ncand = (int)cand.size();
     const bool prof_was = g_prof.on;
     g_prof.on = true;

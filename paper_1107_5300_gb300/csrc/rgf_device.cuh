@@ -261,7 +261,36 @@ struct GJUpdateOp {
     }
 };
 
-template <class R>
+// The same rank-b update on binary64 data (RGF_FP64_TC): multipliers, pivot
+// rows and W binary64, sliced from binary64, the update summed in binary64.
+struct GJUpdateOp64 {
+    static constexpr bool kF64 = true;
+    int cm_off;      // multipliers [bm][K]
+    int xr_off;      // substituted pivot rows [bm][K]
+    zd* A;
+    int K, lda, r0, j0, bb, clo, ps, pskip;
+    __device__ int col(int c) const { const int l = clo + c; return l < ps ? l : l + pskip; }
+    __device__ zd a(int m, int k) const {
+        return reinterpret_cast<const zd*>(rgf_dyn_smem + cm_off)[k * K + r0 + m];
+    }
+    __device__ zd b(int k, int n) const {
+        return reinterpret_cast<const zd*>(rgf_dyn_smem + xr_off)[k * K + col(n)];
+    }
+    using Old = zd;
+    __device__ bool colA() const { return true; }
+    __device__ zd load(int m, int n, bool) const {
+        const int i = r0 + m;
+        if (i >= j0 && i < j0 + bb) return reinterpret_cast<const zd*>(rgf_dyn_smem + xr_off)[(i - j0) * K + col(n)];
+        return A[(size_t)col(n) * lda + i];
+    }
+    __device__ void store(int m, int n, zd x, double re, double im, bool) const {
+        A[(size_t)col(n) * lda + r0 + m] = zd{x.re - re, x.im - im};
+    }
+};
+
+// TC64: with R = double, run the rank-b updates on the tensor cores (binary64
+// slicing) when the block holds them.
+template <class R, bool TC64 = false>
 __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __restrict__ G, int ldg,
                              GJSmem<R> s, double amax2 = 0.0, Team tm = Team{0, 1}) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -451,6 +480,15 @@ __device__ int cta_gj_invert(cx<R>* __restrict__ A, int K, int lda, cx<R>* __res
                 const int cm_off = tc::dyn_off(Cm), xr_off = tc::dyn_off(Xr);
                 for (int r0 = 0; r0 < K; r0 += 128) {
                     const GJUpdateOp op{cm_off, xr_off, A, K, lda, r0, j0, bb, clo, ps, pskip};
+                    s.tcs->phase = tc::zgemm(op, min(128, K - r0), nown, bb, s.tcs->ar, s.tcs->phase);
+                }
+                tc_done = true;
+            }
+        } else if constexpr (std::is_same<R, double>::value && TC64) {
+            if (s.tcs && nown > 0) {
+                const int cm_off = tc::dyn_off(Cm), xr_off = tc::dyn_off(Xr);
+                for (int r0 = 0; r0 < K; r0 += 128) {
+                    const GJUpdateOp64 op{cm_off, xr_off, A, K, lda, r0, j0, bb, clo, ps, pskip};
                     s.tcs->phase = tc::zgemm(op, min(128, K - r0), nown, bb, s.tcs->ar, s.tcs->phase);
                 }
                 tc_done = true;

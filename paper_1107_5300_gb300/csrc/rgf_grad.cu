@@ -361,10 +361,12 @@ cudaError_t launch_grad(int precision, const ChainDev* chains, const int* order,
                         const LeadDev* leads, void* ws, const int* seg_cols, double* T, double* dT,
                         double* rho, int out_mode, int32_t* status, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
+    // RGF_FP64_TC (3) runs this sweep as RGF_FP64: its products stay on the
+    // FP64 pipe
     const bool tc = precision == 2;
     const size_t smem = sweep_smem_bytes(Kmax, tc);
     cudaError_t e;
-    if (precision == 0) {
+    if (precision == 0 || precision == 3) {
         e = cudaFuncSetAttribute(grad_kernel<double, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -109,7 +109,8 @@ extern "C" rgf_status rgf_conductance_noalloc(int N, int L, double t, const doub
     if (N < 2 || N > 2047 || L < 1 || !std::isfinite(t) || t == 0.0)
         return nfail(RGF_EINVAL, "bad N, L or t");
     if (!onsite_dev || !E_dev || !T_dev) return nfail(RGF_EINVAL, "NULL device pointer");
-    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC)
+    if (precision != RGF_FP64 && precision != RGF_MIXED && precision != RGF_MIXED_TC &&
+        precision != RGF_FP64_TC)
         return nfail(RGF_EINVAL, "unknown precision");
     if (!(eta_device >= 0.0) || !(eta_lead > 0.0) || !std::isfinite(eta_device) ||
         !std::isfinite(eta_lead))

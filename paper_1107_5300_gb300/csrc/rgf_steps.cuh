@@ -134,6 +134,27 @@ struct DenseOp {
     }
 };
 
+// The same product on binary64 operands (RGF_FP64_TC's strip product).
+struct DenseOp64 {
+    static constexpr bool kF64 = true;
+    const zd* A;
+    int lda;
+    const zd* B;
+    int ldb;
+    zd* C;
+    int ldc, r0;
+    using Old = zd;
+    __device__ bool colA() const { return false; }
+    __device__ zd a(int m, int k) const { return A[(size_t)(r0 + m) * lda + k]; }
+    __device__ zd b(int k, int n) const { return B[(size_t)k * ldb + n]; }
+    __device__ zd load(int m, int n, bool first) const {
+        return first ? zd{0.0, 0.0} : C[(size_t)(r0 + m) * ldc + n];
+    }
+    __device__ void store(int m, int n, zd x, double re, double im, bool first) const {
+        C[(size_t)(r0 + m) * ldc + n] = first ? zd{re, im} : zd{x.re + re, x.im + im};
+    }
+};
+
 // C = op(A) B on the tensor cores over row tiles of 128; one out-of-line copy
 // for the gradient's dense products (arguments by value; the sweep's strip
 // product is inlined).  Returns the next mbarrier phase.
@@ -287,7 +308,7 @@ __device__ __forceinline__ cx<R> pair_d(const ChainCtx& c, int kb, int i) {
 // kb >= 0 (pair steps, kb = the pair's second column): the diagonal of X
 // additionally loses t^2 kappa_i / d_i (see pair_scales; s.kn holds the keep
 // mask of kb).
-template <class R>
+template <class R, bool TC64 = false>
 __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* Gout, cx<R>* X,
                           SweepSmem<R>& s, int kb = -1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -323,10 +344,10 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
         }
     }
     amax2 = block_max(amax2, s.red);
-    return cta_gj_invert<R>(X, K, KL, Gout, KL, s.gj, amax2);
+    return cta_gj_invert<R, TC64>(X, K, KL, Gout, KL, s.gj, amax2);
 }
 
-template <class R>
+template <class R, bool TC64 = false>
 __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx<R>* Pprev,
                              cx<R>* Pout, cx<R>* Y, SweepSmem<R>& s) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -349,6 +370,14 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
         if (s.tcs) {
             for (int r0 = 0; r0 < rows; r0 += 128) {
                 const DenseOp op{Y, KL, Gk, KL, Pout, KL, r0, false};
+                s.tcs->phase = tc::zgemm(op, min(128, rows - r0), K, K, s.tcs->ar, s.tcs->phase);
+            }
+            return;
+        }
+    } else if constexpr (std::is_same<R, double>::value && TC64) {
+        if (s.tcs) {
+            for (int r0 = 0; r0 < rows; r0 += 128) {
+                const DenseOp64 op{Y, KL, Gk, KL, Pout, KL, r0};
                 s.tcs->phase = tc::zgemm(op, min(128, rows - r0), K, K, s.tcs->ar, s.tcs->phase);
             }
             return;

@@ -230,9 +230,9 @@ __device__ __forceinline__ void half_body(const SweepArgs& a, int ci, int h, int
         __syncthreads();
         const bool pair = pairable && pair_ok<R>(c, kb, s);
         // one call site each for the inverse and the strip product (inlined)
-        flag |= inv_column<R>(c, k, hw.G, hw.G, hw.X, s, pair ? kb : -1);
+        flag |= inv_column<R, TC>(c, k, hw.G, hw.G, hw.X, s, pair ? kb : -1);
         if (pair) pair_scales<R>(c, k, kb, hw.G, s);
-        strip_column<R>(c, k, hw.G, hw.P, hw.P, hw.X, s);
+        strip_column<R, TC>(c, k, hw.G, hw.P, hw.P, hw.X, s);
         if (pair) pair_finish<R>(c, k, hw.G, s);
         j += pair ? 2 : 1;
     }
@@ -430,18 +430,22 @@ cudaError_t set_smem(K kern, size_t smem) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// Panel width of a launch of `precision` (2 = RGF_MIXED_TC) and the shared
-// memory of its binary64 steps and of its recursion.
-int launch_panel(int precision, int Kmax) { return gj_panel_width(Kmax, precision == 2); }
+// Precisions: 0 RGF_FP64, 1 RGF_MIXED, 2 RGF_MIXED_TC, 3 RGF_FP64_TC.
+bool uses_tc(int precision) { return precision == 2 || precision == 3; }
+bool binary64(int precision) { return precision == 0 || precision == 3; }
+
+// Panel width of a launch of `precision` and the shared memory of its
+// binary64 steps and of its recursion.
+int launch_panel(int precision, int Kmax) { return gj_panel_width(Kmax, uses_tc(precision)); }
 size_t f64_smem(int precision, int Kmax) {
     return sweep_total_bytes(Kmax, launch_panel(precision, Kmax), false);
 }
 size_t rec_smem(int precision, int Kmax) {
-    const size_t b = sweep_total_bytes(Kmax, launch_panel(precision, Kmax), precision == 2);
+    const size_t b = sweep_total_bytes(Kmax, launch_panel(precision, Kmax), uses_tc(precision));
     // a tensor-core block holds all 512 TMEM columns: ask for more than half
     // of an SM's shared memory so that no second block shares its SM (the
     // register file already allows only one)
-    return precision == 2 && b < 120 * 1024 ? 120 * 1024 : b;
+    return uses_tc(precision) && b < 120 * 1024 ? 120 * 1024 : b;
 }
 
 SweepArgs make_args(const ChainDev* chains, const int* order, int nchains, int Kmax,
@@ -457,9 +461,13 @@ cudaError_t configure_sweep(int precision, int Kmax) {
     const size_t f64 = f64_smem(precision, Kmax), rec = rec_smem(precision, Kmax);
     const size_t both = rec > f64 ? rec : f64;
     cudaError_t e;
-    if (precision == 0) {
+    if (binary64(precision)) {
         if ((e = set_smem(prep_kernel<double>, f64)) != cudaSuccess) return e;
         if ((e = set_smem(merge_kernel<double>, f64)) != cudaSuccess) return e;
+        if (precision == 3) {
+            if ((e = set_smem(half_kernel<double, true>, rec)) != cudaSuccess) return e;
+            return set_smem(batch_kernel<double, true>, both);
+        }
         if ((e = set_smem(half_kernel<double, false>, rec)) != cudaSuccess) return e;
         return set_smem(batch_kernel<double, false>, both);
     }
@@ -481,7 +489,7 @@ cudaError_t launch_prep(int precision, const ChainDev* chains, const int* order,
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, nullptr, nullptr);
-    auto kern = precision == 0 ? prep_kernel<double> : prep_kernel<df32>;
+    auto kern = binary64(precision) ? prep_kernel<double> : prep_kernel<df32>;
     kern<<<2 * nchains, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
     return cudaGetLastError();
 }
@@ -494,8 +502,10 @@ cudaError_t launch_half(int precision, const ChainDev* chains, const int* order,
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, nullptr, nullptr);
-    auto kern = precision == 0 ? half_kernel<double, false>
-                               : (precision == 2 ? half_kernel<df32, true> : half_kernel<df32, false>);
+    auto kern = precision == 0   ? half_kernel<double, false>
+                : precision == 3 ? half_kernel<double, true>
+                : precision == 2 ? half_kernel<df32, true>
+                                 : half_kernel<df32, false>;
     kern<<<2 * nchains, NT, rec_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
     return cudaGetLastError();
 }
@@ -509,7 +519,7 @@ cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, T, status);
-    auto kern = precision == 0 ? merge_kernel<double> : merge_kernel<df32>;
+    auto kern = binary64(precision) ? merge_kernel<double> : merge_kernel<df32>;
     kern<<<nchains, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
     return cudaGetLastError();
 }
@@ -525,8 +535,10 @@ cudaError_t launch_batch(int precision, const ChainDev* chains, const int* order
                                   leads, ws, T, status);
     const size_t f64 = f64_smem(precision, Kmax), rec = rec_smem(precision, Kmax);
     const int grid = nsm < 2 * nchains ? (nsm > 0 ? nsm : 1) : 2 * nchains;
-    auto kern = precision == 0 ? batch_kernel<double, false>
-                               : (precision == 2 ? batch_kernel<df32, true> : batch_kernel<df32, false>);
+    auto kern = precision == 0   ? batch_kernel<double, false>
+                : precision == 3 ? batch_kernel<double, true>
+                : precision == 2 ? batch_kernel<df32, true>
+                                 : batch_kernel<df32, false>;
     kern<<<grid, NT, rec > f64 ? rec : f64, st>>>(a, launch_panel(precision, Kmax), queue);
     return cudaGetLastError();
 }

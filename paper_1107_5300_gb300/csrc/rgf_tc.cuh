@@ -42,6 +42,8 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "rgf_common.cuh"
 
 namespace rgf {
@@ -297,6 +299,69 @@ __device__ __forceinline__ void scales(float mx, float& sc, float& fac) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Binary64 operands (accessors with kF64 = true).  The scale of a row / column
+// comes from the largest binary64 exponent field in it, and the digits of a
+// value from its 53-bit integer significand: integer arithmetic only, no work
+// on the FP64 pipe.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned exp64(double v) {
+    return (unsigned)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FFu;
+}
+
+// Slicing scale 2^(7-e) and output factor 2^(e-7) for a largest biased
+// binary64 exponent E (values below 2^(E-1022) in magnitude): e = E - 1022.
+// E = 2047 (NaN, Inf) and e > 126 (beyond binary32) poison the outputs;
+// below 2^-100 the row / column counts as zero -- as scales() does.
+__device__ __forceinline__ void scales64(unsigned E, float& sc, float& fac) {
+    const int e = (int)E - 1022;
+    if (E == 2047u || e > 126) {
+        sc = 1.0f;
+        fac = __int_as_float(0x7fc00000);
+    } else if (e < -99) {
+        sc = 0.0f;
+        fac = 0.0f;
+    } else {
+        sc = __int_as_float((134 - e) << 23);
+        fac = __int_as_float((120 + e) << 23);
+    }
+}
+
+// The S signed base-256 digits of the binary64 value v times the slicing scale
+// sc = 2^(7-e) (|v| < 2^e): X = round(v 2^(55-e)) from the significand by a
+// shift (|X| < 2^55), then balanced digits from the lowest up,
+//     d_i in [-128, 127] (d_0 in [-128, 128]),  v sc ~ sum_i d_i 2^(-8 i),
+// the rounding of X being the only error (half a unit of 2^(-48) of sc's unit,
+// below the lowest digit).  Zero / subnormal v, or sc = 0, give zero digits.
+__device__ __forceinline__ void digits64(double v, float sc, float* d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int E = (int)((b >> 52) & 0x7FFull);
+    const unsigned scb = __float_as_uint(sc);
+    long long X = 0;
+    if (E != 0 && E != 2047 && (scb & 0x7F800000u) != 0u) {
+        const int e = 134 - (int)((scb >> 23) & 0xFFu);
+        const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+        const int sh = E - 1020 - e;              // X = M 2^sh, sh <= 2
+        unsigned long long mag = 0;
+        if (sh >= 0) mag = M << sh;
+        else if (sh > -60) mag = (M + (1ull << (-sh - 1))) >> (-sh);
+        X = (b >> 63) ? -(long long)mag : (long long)mag;
+    }
+#pragma unroll
+    for (int i = S - 1; i >= 1; --i) {
+        const long long r = ((X + 128) & 255) - 128;
+        d[i] = (float)r;
+        X = (X - r) >> 8;                         // exact: X - r is a multiple of 256
+    }
+    d[0] = (float)X;
+}
+
+// Whether an accessor works on binary64 (kF64 = true) or double-float values.
+template <class T, class = void>
+struct IsF64 : std::false_type {};
+template <class T>
+struct IsF64<T, std::void_t<decltype(T::kF64)>> : std::integral_constant<bool, T::kF64> {};
+
 // C op= A B, A: M x Kc (M <= 128), B: Kc x N, complex double-float, through the
 // accessor object `op` (passed by value):
 //   zf op.a(m, k), op.b(k, n)                 operand entries
@@ -308,11 +373,17 @@ __device__ __forceinline__ void scales(float mx, float& sc, float& fac) {
 //                                             (A B)[m][n] = re + i im over one group
 //                                             of up to 96 inner entries; first =
 //                                             the first group
+// With Op::kF64 = true the entries are binary64 (zd), sliced by digits64, and
+// store receives re, im in binary64: the six accumulators are summed
+// error-free in binary32 to three terms s + t + w (|w| < 2^-40 |s|), which are
+// added in binary64 -- a product accurate to a few units of 2^-53 of (row max
+// x column max x inner dimension).
 // Called by every thread of the block (NT = 512); ends with a barrier.
 // Returns the next mbarrier phase.
 template <class Op>
 __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, uint32_t phase) {
     static_assert(NT == 512, "zgemm assumes 512 threads");
+    constexpr bool F64 = IsF64<Op>::value;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t tmem = *ar.tslot();
     float* rsc = ar.rsc();
@@ -329,7 +400,30 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
         const bool cacheA = nch <= NCA;
         // row scales over this group
         const bool colA = op.colA();
-        if (colA) {
+        if constexpr (F64) {
+            if (colA) {
+                if (tid < 128) {
+                    unsigned mx = 0u;
+                    if (tid < M)
+                        for (int k = 0; k < kg; ++k) {
+                            const zd v = op.a(tid, g0 + k);
+                            mx = max(mx, max(exp64(v.re), exp64(v.im)));
+                        }
+                    scales64(mx, rsc[tid], rfac[tid]);
+                }
+            } else {
+                for (int m = warp; m < 128; m += NWARP) {
+                    unsigned mx = 0u;
+                    if (m < M)
+                        for (int k = lane; k < kg; k += 32) {
+                            const zd v = op.a(m, g0 + k);
+                            mx = max(mx, max(exp64(v.re), exp64(v.im)));
+                        }
+                    mx = __reduce_max_sync(0xffffffffu, mx);
+                    if (lane == 0) scales64(mx, rsc[m], rfac[m]);
+                }
+            }
+        } else if (colA) {
             if (tid < 128) {
                 float mx = 0.0f;
                 if (tid < M)
@@ -361,15 +455,28 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
             if (tid < (NT / MAXC) * MAXC) {
                 const int c = tid % MAXC, ks = tid / MAXC;
                 float mx = 0.0f;
-                if (c < nc)
-                    for (int k = ks; k < kg; k += NT / MAXC) {
-                        const zf v = op.b(g0 + k, n0 + c);
-                        mx = nmax(mx, nmax(fabsf(v.re.hi), fabsf(v.im.hi)));
-                    }
-                if (c < nc) atomicMax(&cmax[c], __float_as_uint(mx));
+                if constexpr (F64) {
+                    unsigned ex = 0u;
+                    if (c < nc)
+                        for (int k = ks; k < kg; k += NT / MAXC) {
+                            const zd v = op.b(g0 + k, n0 + c);
+                            ex = max(ex, max(exp64(v.re), exp64(v.im)));
+                        }
+                    if (c < nc) atomicMax(&cmax[c], ex);
+                } else {
+                    if (c < nc)
+                        for (int k = ks; k < kg; k += NT / MAXC) {
+                            const zf v = op.b(g0 + k, n0 + c);
+                            mx = nmax(mx, nmax(fabsf(v.re.hi), fabsf(v.im.hi)));
+                        }
+                    if (c < nc) atomicMax(&cmax[c], __float_as_uint(mx));
+                }
             }
             __syncthreads();
-            if (tid < MAXC) scales(__uint_as_float(cmax[tid]), csc[tid], cfac[tid]);
+            if (tid < MAXC) {
+                if constexpr (F64) scales64(cmax[tid], csc[tid], cfac[tid]);
+                else scales(__uint_as_float(cmax[tid]), csc[tid], cfac[tid]);
+            }
             __syncthreads();
             typename Op::Old old[4];
             uint32_t init = 0u;
@@ -385,10 +492,16 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
                         const int k = colA ? (e >> 7) : (e & 7);
                         float dr[S], di[S];
                         if (m < M && k0 + k < kg) {
-                            const zf v = op.a(m, g0 + k0 + k);
                             const float sc = rsc[m];
-                            digits(v.re.hi, v.re.lo, sc, dr);
-                            digits(v.im.hi, v.im.lo, sc, di);
+                            if constexpr (F64) {
+                                const zd v = op.a(m, g0 + k0 + k);
+                                digits64(v.re, sc, dr);
+                                digits64(v.im, sc, di);
+                            } else {
+                                const zf v = op.a(m, g0 + k0 + k);
+                                digits(v.re.hi, v.re.lo, sc, dr);
+                                digits(v.im.hi, v.im.lo, sc, di);
+                            }
                         } else {
 #pragma unroll
                             for (int i = 0; i < S; ++i) { dr[i] = 0.0f; di[i] = 0.0f; }
@@ -408,10 +521,16 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
                     if (c < ncp) {
                         float dr[S], di[S];
                         if (c < nc && k0 + k < kg) {
-                            const zf v = op.b(g0 + k0 + k, n0 + c);
                             const float sc = csc[c];
-                            digits(v.re.hi, v.re.lo, sc, dr);
-                            digits(v.im.hi, v.im.lo, sc, di);
+                            if constexpr (F64) {
+                                const zd v = op.b(g0 + k0 + k, n0 + c);
+                                digits64(v.re, sc, dr);
+                                digits64(v.im, sc, di);
+                            } else {
+                                const zf v = op.b(g0 + k0 + k, n0 + c);
+                                digits(v.re.hi, v.re.lo, sc, dr);
+                                digits(v.im.hi, v.im.lo, sc, di);
+                            }
                         } else {
 #pragma unroll
                             for (int i = 0; i < S; ++i) { dr[i] = 0.0f; di[i] = 0.0f; }
@@ -486,25 +605,55 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
                             ld4(ah + 4 * ACOLS, a4);
                             ld4(ah + 5 * ACOLS, a5);
                             ld_wait();
-                            float hi[4], lo[4];
+                            if constexpr (F64) {
+                                // s + t + w exactly up to the rounding of w
+                                // (below 2^-70 of s), then binary64
+                                double z[4];
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                float s01, e01, s23, e23, s, e;
-                                two_sum(a0[j], a1[j], s01, e01);        // exact
-                                two_sum(a2[j], a3[j], s23, e23);        // exact
-                                const float r45 = __fadd_rn(a4[j], a5[j]);
-                                two_sum(s01, s23, s, e);
-                                fast_two_sum(s, __fadd_rn(__fadd_rn(e01, e), __fadd_rn(e23, r45)), hi[j], lo[j]);
-                            }
-                            if (mrow < M) {
+                                for (int j = 0; j < 4; ++j) {
+                                    float s01, e01, s23, e23, r45, e45, s, e, p, pe, q, qe, t, te;
+                                    two_sum(a0[j], a1[j], s01, e01);
+                                    two_sum(a2[j], a3[j], s23, e23);
+                                    two_sum(a4[j], a5[j], r45, e45);
+                                    two_sum(s01, s23, s, e);
+                                    two_sum(e01, e, p, pe);
+                                    two_sum(e23, r45, q, qe);
+                                    two_sum(p, q, t, te);
+                                    const float w = __fadd_rn(__fadd_rn(pe, qe), __fadd_rn(te, e45));
+                                    z[j] = (double)s + ((double)t + (double)w);
+                                }
+                                if (mrow < M) {
 #pragma unroll
-                                for (int jj = 0; jj < 2; ++jj) {
-                                    const int j = 2 * h + jj, c = 4 * cb + j;
-                                    if (c < nc) {
-                                        const float f = rf * cfac[c];
-                                        const df32 re{__fmul_rn(hi[2 * jj], f), __fmul_rn(lo[2 * jj], f)};
-                                        const df32 im{__fmul_rn(hi[2 * jj + 1], f), __fmul_rn(lo[2 * jj + 1], f)};
-                                        op.store(mrow, n0 + c, old[j], re, im, g0 == 0);
+                                    for (int jj = 0; jj < 2; ++jj) {
+                                        const int j = 2 * h + jj, c = 4 * cb + j;
+                                        if (c < nc) {
+                                            const double f = (double)rf * (double)cfac[c];
+                                            op.store(mrow, n0 + c, old[j], z[2 * jj] * f, z[2 * jj + 1] * f,
+                                                     g0 == 0);
+                                        }
+                                    }
+                                }
+                            } else {
+                                float hi[4], lo[4];
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    float s01, e01, s23, e23, s, e;
+                                    two_sum(a0[j], a1[j], s01, e01);        // exact
+                                    two_sum(a2[j], a3[j], s23, e23);        // exact
+                                    const float r45 = __fadd_rn(a4[j], a5[j]);
+                                    two_sum(s01, s23, s, e);
+                                    fast_two_sum(s, __fadd_rn(__fadd_rn(e01, e), __fadd_rn(e23, r45)), hi[j], lo[j]);
+                                }
+                                if (mrow < M) {
+#pragma unroll
+                                    for (int jj = 0; jj < 2; ++jj) {
+                                        const int j = 2 * h + jj, c = 4 * cb + j;
+                                        if (c < nc) {
+                                            const float f = rf * cfac[c];
+                                            const df32 re{__fmul_rn(hi[2 * jj], f), __fmul_rn(lo[2 * jj], f)};
+                                            const df32 im{__fmul_rn(hi[2 * jj + 1], f), __fmul_rn(lo[2 * jj + 1], f)};
+                                            op.store(mrow, n0 + c, old[j], re, im, g0 == 0);
+                                        }
                                     }
                                 }
                             }

@@ -1,6 +1,7 @@
 // rgf_tcgemm.cu -- rgf_zgemm_tc: the tensor-core complex product of the RGF
 // step (rgf_tc.cuh) as a stand-alone entry point, C = A B for binary64
-// complex matrices in device memory.  One 512-thread block per 128 rows of C.
+// complex matrices in device memory, sliced from binary64 (binary64-class
+// accuracy, normwise).  One 512-thread block per 128 rows of C.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -14,9 +15,10 @@ void set_last_error(const std::string& msg);
 
 namespace {
 
-// Accessors of the binary64 operands (rounded to double-float on load) and
-// of the output (the sum of the groups of 96 inner entries).
+// Accessors of the binary64 operands (sliced from binary64) and of the
+// output (the binary64 sum of the groups of 96 inner entries).
 struct Z64Op {
+    static constexpr bool kF64 = true;
     const zd* A;
     int lda;
     const zd* B;
@@ -24,21 +26,15 @@ struct Z64Op {
     zd* C;
     int ldc;
     int m0;
-    __device__ zf a(int m, int k) const {
-        const zd v = A[(size_t)(m0 + m) * lda + k];
-        return from_z<df32>(v.re, v.im);
-    }
-    __device__ zf b(int k, int n) const {
-        const zd v = B[(size_t)k * ldb + n];
-        return from_z<df32>(v.re, v.im);
-    }
+    __device__ zd a(int m, int k) const { return A[(size_t)(m0 + m) * lda + k]; }
+    __device__ zd b(int k, int n) const { return B[(size_t)k * ldb + n]; }
     using Old = zd;
     __device__ bool colA() const { return false; }
     __device__ zd load(int m, int n, bool first) const {
         return first ? zd{0.0, 0.0} : C[(size_t)(m0 + m) * ldc + n];
     }
-    __device__ void store(int m, int n, zd old, df32 re, df32 im, bool first) const {
-        const zd x = {(double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo};
+    __device__ void store(int m, int n, zd old, double re, double im, bool first) const {
+        const zd x = {re, im};
         C[(size_t)(m0 + m) * ldc + n] = first ? x : cadd(old, x);
     }
 };

@@ -19,7 +19,7 @@ lib = C.CDLL(str(_LIB_PATH))
 
 (RGF_OK, RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA, RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE,
  RGF_ETIMEOUT, RGF_EBOUNDS) = range(9)
-RGF_FP64, RGF_MIXED, RGF_MIXED_TC = 0, 1, 2
+RGF_FP64, RGF_MIXED, RGF_MIXED_TC, RGF_FP64_TC = 0, 1, 2, 3
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "ESINGULAR", "ENONFINITE", "ETIMEOUT",
                 "EBOUNDS"]
 
@@ -399,7 +399,7 @@ def autotune(precision, widths, cells=4, reps=2):
     return [best[i].as_dict() for i in range(len(Ns))], ms
 
 
-def save_tuning(path, precisions=(RGF_FP64, RGF_MIXED, RGF_MIXED_TC)):
+def save_tuning(path, precisions=(RGF_FP64, RGF_MIXED, RGF_MIXED_TC, RGF_FP64_TC)):
     """Writes the installed tables to a JSON file."""
     import json
     Path(path).write_text(json.dumps({str(p): get_tuning(p) for p in precisions}, indent=1))

@@ -61,10 +61,10 @@ def _both_schedules(rgflib, ribs, E, prec):
 # (the compiler may fuse a product and a sum into one FMA in one and not in
 # the other), so they agree to rounding, not bit for bit; each is
 # deterministic.
-SCHED_TOL = {0: 1e-10, 1: 1e-10, 2: 1e-10}
+SCHED_TOL = {0: 1e-10, 1: 1e-10, 2: 1e-10, 3: 1e-10}
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_persistent_queue_equals_three_launches(rgflib, clean_state, prec):
     # more halves than SMs, uneven sizes, a non-finite energy (RGF_EINVAL from
     # the lead kernel, still counted through the queue and the join)
@@ -131,9 +131,10 @@ def _entries(engine, panel, pairs):
 def test_every_tuned_schedule_vs_oracle(rgflib, clean_state, engine, panel, pairs):
     # widths with columns of several panels and a ragged last panel, vacancies
     cases = [(21, 4, 0.0), (37, 3, 0.25), (50, 2, 0.1)]
-    for prec, tol in ((rgflib.RGF_MIXED_TC, 1e-7), (rgflib.RGF_MIXED, 1e-7), (rgflib.RGF_FP64, 1e-9)):
-        if engine == 0 and prec != rgflib.RGF_MIXED_TC:
-            continue                               # the engine is read by RGF_MIXED_TC only
+    for prec, tol in ((rgflib.RGF_MIXED_TC, 1e-7), (rgflib.RGF_MIXED, 1e-7), (rgflib.RGF_FP64, 1e-9),
+                      (rgflib.RGF_FP64_TC, 1e-9)):
+        if engine == 0 and prec not in (rgflib.RGF_MIXED_TC, rgflib.RGF_FP64_TC):
+            continue                               # the engine is read by the _TC precisions only
         rgflib.set_tuning(prec, _entries(engine, panel, pairs))
         for N, L, p in cases:
             eps = workloads.anderson_onsite(N, L, 0.25, N)

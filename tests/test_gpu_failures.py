@@ -65,7 +65,7 @@ def test_nonfinite_energy_is_einval_per_chain(rgflib):
     assert np.array_equal(T[[0, 2]], ref) and np.isnan(T[[1, 3]]).all()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_exactly_singular_slice_gives_esingular(rgflib, prec):
     # With no broadening in the device (eta_device = 0) and the left atom of
     # row 0 in the first cell removed, the right atom of row 0 has no bond to

@@ -23,15 +23,20 @@ GOLD = json.loads((Path(__file__).resolve().parent / "golden" / "agnr245_golden.
 W = workloads.WORKLOADS["agnr245_L4000_anderson"]
 
 # |dT| per energy.  binary64: the paper's CPU accuracy (better than 1e-9);
+# binary64 with its products on the tensor cores: 1e-9 on 4 cells, 5e-9 on
+# 4000 (the products are accurate normwise, to about 2^-50 of row max x
+# column max, not entry by entry; measured 1.9e-9 against binary64 over the
+# 69 bench energies);
 # mixed paths: 1e-7 on the 4-cell ribbon, 1e-6 (the target) on 4000 cells.
 # E = 0 exactly: the oracle's own value there (mode-basis end slices) is
 # condition-limited; the bound is the one measured on small disordered
 # ribbons against 40 digits (tests/test_gpu_parity.py).
-TOL = {(0, 4): 1e-9, (1, 4): 1e-7, (2, 4): 1e-7, (0, 4000): 1e-9, (1, 4000): 1e-6, (2, 4000): 1e-6}
+TOL = {(0, 4): 1e-9, (1, 4): 1e-7, (2, 4): 1e-7, (3, 4): 1e-9,
+       (0, 4000): 1e-9, (1, 4000): 1e-6, (2, 4000): 1e-6, (3, 4000): 5e-9}
 TOL_E0 = 1e-6
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_bench_launch_configuration_vs_oracle(rgflib, prec):
     N = W["N"]
     Es = W["energies"]()
@@ -56,7 +61,7 @@ def full_ribbon(rgflib):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_full_size_vs_oracle(rgflib, full_ribbon, prec):
     g, e0 = GOLD["L4000"], GOLD["L4000_E0"]
     Es = np.array(g["E"] + [e0["E"]])
@@ -78,7 +83,7 @@ def bench_fp64(rgflib, full_ribbon):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_mixed_paths_match_binary64_at_full_size(rgflib, full_ribbon, bench_fp64, prec):
     Es, T64, s64 = bench_fp64
     T, st = rgflib.conductance([full_ribbon] * len(Es), Es, 1e-8, 1e-8, prec, check=False)
@@ -86,6 +91,6 @@ def test_mixed_paths_match_binary64_at_full_size(rgflib, full_ribbon, bench_fp64
     d = np.abs(T - T64)
     print(f"L4000 precision={prec} vs binary64: max |dT| = {d.max():.3e}, "
           f"at |E| <= 5 meV {d[np.abs(Es) <= 5e-3].max():.3e}")
-    assert d.max() <= 1e-6, d.max()
+    assert d.max() <= (5e-9 if prec == 3 else 1e-6), d.max()
     nch = np.array([bands.channels_closed_form(W["N"], e) for e in Es])
     assert np.all(T64 >= -1e-9) and np.all(T64 <= nch + 1e-9)

@@ -31,7 +31,8 @@ def test_noalloc_matches_allocating_entry_point(rgflib):
     rem_d = torch.tensor(rem, dtype=torch.uint8, device="cuda")
     E_d = torch.tensor(Es, dtype=torch.float64, device="cuda")
     T_d, S_d = _bufs(torch, len(Es))
-    for prec, tol in ((rgflib.RGF_FP64, 1e-9), (rgflib.RGF_MIXED, 1e-7), (rgflib.RGF_MIXED_TC, 1e-7)):
+    for prec, tol in ((rgflib.RGF_FP64, 1e-9), (rgflib.RGF_MIXED, 1e-7), (rgflib.RGF_MIXED_TC, 1e-7),
+                      (rgflib.RGF_FP64_TC, 1e-9)):
         T_ref, st_ref = rgflib.conductance([rib] * len(Es), Es, 1e-8, 1e-8, prec)
         for _ in range(2):
             T_d.fill_(float("nan"))
