@@ -47,13 +47,13 @@ import workloads  # noqa: E402
 
 
 def kernel_sources_digest(csrc: Path | None = None) -> str:
-    """SHA-256 over the sources the sweep kernels are compiled from (rgf_sweep.cu
-    and every header; file names and bytes, in name order): the DRAM counters
-    of a capture hold only for the sources they were taken on."""
+    """SHA-256 over the sources the sweep kernels are compiled from (rgf_sweep.cu,
+    rgf_batch.cu and every header; file names and bytes, in name order): the
+    DRAM counters of a capture hold only for the sources they were taken on."""
     import hashlib
     csrc = csrc or ROOT / "paper_1107_5300_gb300" / "csrc"
     h = hashlib.sha256()
-    for p in sorted({csrc / "rgf_sweep.cu", *csrc.glob("*.cuh"), *csrc.glob("*.h")}):
+    for p in sorted({csrc / "rgf_sweep.cu", csrc / "rgf_batch.cu", *csrc.glob("*.cuh"), *csrc.glob("*.h")}):
         h.update(p.name.encode() + b"\0" + p.read_bytes())
     return h.hexdigest()
 

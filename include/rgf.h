@@ -76,8 +76,8 @@ typedef enum {
                             dense contractions of every slice step on the tensor cores,
                             sliced from binary64 and summed in binary64: products
                             accurate to a few units of 2^-53 of (row max x column max
-                            x inner dimension).  The gradient and LDOS sweeps run it
-                            as RGF_FP64. */
+                            x inner dimension), in the forward, gradient and LDOS
+                            sweeps alike. */
 } rgf_precision;
 
 /* One ribbon instance (the paper's input step: geometry, defects, disorder). */

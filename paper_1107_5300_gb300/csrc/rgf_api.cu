@@ -6,7 +6,7 @@
 //   1. one lead problem per chain (pristine ribbon of the chain's width at the
 //      chain's energy), decimated on the device (rgf_lead.cu);
 //   2. the column-sliced recursion as two halves per chain, one from each
-//      lead, joined by one Dyson step, and the trace (rgf_sweep.cu: end-column
+//      lead, joined by one Dyson step, and the trace (rgf_half.cuh: end-column
 //      preparation, half sweeps, merge); chains are launched longest first so
 //      that the hardware block scheduler balances uneven chains across SMs;
 //   3. T and the per-chain status words return to the host.

@@ -1,5 +1,5 @@
 // rgf_grad.cu -- dT/d eps for every on-site energy, one thread block per
-// chain, over the column slices of rgf_sweep.cu.
+// chain, over the column slices of rgf_half.cuh.
 //
 // The paper does not differentiate; the derivative follows from Eq. 1 and
 // Eq. 2.  With A = z - H - Sigma and dA/d eps_i = -e_i e_i^T, dG = G e_i e_i^T G,
@@ -115,12 +115,12 @@ __device__ double build_A(const ChainCtx& c, int k, bool left, const cx<R>* glp,
 
 // Column k's matrix (build_A) inverted into Gout; one out-of-line copy for
 // the four call sites.  Returns the Gauss-Jordan flags.
-template <class R>
+template <class R, bool TC64>
 static __device__ __noinline__ int build_invert(const ChainCtx& c, int k, bool left, const cx<R>* glp,
                                                 bool right, const cx<R>* grn, cx<R>* X, cx<R>* Gout,
                                                 SweepSmem<R>& s) {
     const double amax2 = build_A<R>(c, k, left, glp, right, grn, X, s);
-    return cta_gj_invert<R>(X, col_size(c, k), c.KL, Gout, c.KL, s.gj, amax2);
+    return cta_gj_invert<R, TC64>(X, col_size(c, k), c.KL, Gout, c.KL, s.gj, amax2);
 }
 
 // Y = Pl W_k (KL x K): Y[r][l] = t sum over the kept sources a of l in column
@@ -220,12 +220,12 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     for (int k = ncol - 1; k >= 0; --k) {
         load_cols(c, k, s);
         const int K = col_size(c, k);
-        flag |= build_invert<R>(c, k, k == 0, nullptr, true, gr, X, gr, s);
+        flag |= build_invert<R, TC>(c, k, k == 0, nullptr, true, gr, X, gr, s);
         if (k == ncol - 1) {
             copy_blk(Qr, gr, B);
         } else {
             stencil_right<R>(c, k, Qr, Z, s);
-            dense_product<R, false>(K, KR, K, gr, KL, Z, KL, Qr, KL, s);
+            dense_product<R, false, TC>(K, KR, K, gr, KL, Z, KL, Qr, KL, s);
         }
         if (k > 0 && k % Sc == 0) {
             cx<R>* cp = ckpt + (size_t)(k / Sc - 1) * 2 * B;
@@ -261,8 +261,8 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
     }
     __syncthreads();
     if (want_grad) {
-        dense_product<R, false>(KR, KL, KR, GR, KR, Y, KL, U, KL, s);
-        dense_product<R, false>(KR, KL, KL, U, KL, GL, KL, Mb, KL, s);
+        dense_product<R, false, TC>(KR, KL, KR, GR, KR, Y, KL, U, KL, s);
+        dense_product<R, false, TC>(KR, KL, KL, U, KL, GL, KL, Mb, KL, s);
     }
 
     // Left-to-right pass, segment by segment.
@@ -280,12 +280,12 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
             const cx<R>* sn = sk + 2 * B;
             load_cols(c, k, s);
             const int K = col_size(c, k);
-            flag |= build_invert<R>(c, k, k == 0, nullptr, true, sn, X, sk, s);
+            flag |= build_invert<R, TC>(c, k, k == 0, nullptr, true, sn, X, sk, s);
             if (k == ncol - 1) {
                 copy_blk(sk + B, sk, B);
             } else {
                 stencil_right<R>(c, k, sn + B, Z, s);
-                dense_product<R, false>(K, KR, K, sk, KL, Z, KL, sk + B, KL, s);
+                dense_product<R, false, TC>(K, KR, K, sk, KL, Z, KL, sk + B, KL, s);
             }
         }
         for (int k = k0; k < k1; ++k) {
@@ -295,7 +295,7 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
             const bool last = k == ncol - 1;
             load_cols(c, k, s);
             // G_kk
-            flag |= build_invert<R>(c, k, true, gl, true, sn, X, Gkk, s);
+            flag |= build_invert<R, TC>(c, k, true, gl, true, sn, X, Gkk, s);
             const int n = k >> 2;
             if (want_ldos) {
                 // rho_i = -Im (G_kk)_ii / pi; 0 on removed atoms
@@ -308,18 +308,18 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
                 // G_1k = Pl_{k-1} W_k G_kk  (KL x K)
                 const cx<R>* g1 = Gkk;
                 if (k > 0) {
-                    dense_product<R, false>(KL, K, K, Y, KL, Gkk, KL, G1k, KL, s);
+                    dense_product<R, false, TC>(KL, K, K, Y, KL, Gkk, KL, G1k, KL, s);
                     g1 = G1k;
                 }
                 // G_kL = G_kk W_{k+1} Qr_{k+1}  (K x KR)
                 const cx<R>* gL = Gkk;
                 if (!last) {
                     stencil_right<R>(c, k, sn + B, Z, s);
-                    dense_product<R, false>(K, KR, K, Gkk, KL, Z, KL, GkL, KL, s);
+                    dense_product<R, false, TC>(K, KR, K, Gkk, KL, Z, KL, GkL, KL, s);
                     gL = GkL;
                 }
                 // dT/d eps_i = 2 Re sum_b (G_kL M)[i][b] G_1k[b][i]
-                dense_product<R, false>(K, KL, KR, gL, KL, Mb, KL, U, KL, s);
+                dense_product<R, false, TC>(K, KL, KR, gL, KL, Mb, KL, U, KL, s);
                 for (int i = warp; i < K; i += NWARP) {
                     double acc = 0.0;
                     for (int b = lane; b < KL; b += 32) {
@@ -331,9 +331,9 @@ grad_kernel(const ChainDev* __restrict__ chains, const int* __restrict__ order, 
                 }
             }
             // gl_k and Pl_k (the forward recursion)
-            flag |= build_invert<R>(c, k, true, gl, last, nullptr, X, gl, s);
+            flag |= build_invert<R, TC>(c, k, true, gl, last, nullptr, X, gl, s);
             if (k == 0) copy_blk(Pl, gl, B);
-            else dense_product<R, false>(KL, K, K, Y, KL, gl, KL, Pl, KL, s);
+            else dense_product<R, false, TC>(KL, K, K, Y, KL, gl, KL, Pl, KL, s);
         }
     }
     if constexpr (TC) {
@@ -361,12 +361,17 @@ cudaError_t launch_grad(int precision, const ChainDev* chains, const int* order,
                         const LeadDev* leads, void* ws, const int* seg_cols, double* T, double* dT,
                         double* rho, int out_mode, int32_t* status, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    // RGF_FP64_TC (3) runs this sweep as RGF_FP64: its products stay on the
-    // FP64 pipe
-    const bool tc = precision == 2;
+    const bool tc = precision == 2 || precision == 3;
     const size_t smem = sweep_smem_bytes(Kmax, tc);
     cudaError_t e;
-    if (precision == 0 || precision == 3) {
+    if (precision == 3) {
+        e = cudaFuncSetAttribute(grad_kernel<double, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        grad_kernel<double, true><<<nchains, NT, smem, st>>>(
+            chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status, leads,
+            (zd*)ws, seg_cols, T, dT, rho, out_mode, status);
+    } else if (precision == 0) {
         e = cudaFuncSetAttribute(grad_kernel<double, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -64,7 +64,7 @@ __host__ __device__ inline size_t lead_out_elems(int N) {
     return 3 * (KL * KL + KR * KR) + KL;
 }
 // The sweep of one chain runs as two halves, one from each lead (see
-// rgf_sweep.cu).  Workspace of one half: X, G, P (each KL x KL) and one
+// rgf_half.cuh).  Workspace of one half: X, G, P (each KL x KL) and one
 // element holding the half's status flags; a chain holds two halves.
 __host__ __device__ inline size_t half_ws_elems(int N) {
     size_t KL = (size_t)col_KL(N);
@@ -110,7 +110,7 @@ cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st);
 
-// The same three steps as one persistent kernel (rgf_sweep.cu): one block per
+// The same three steps as one persistent kernel (rgf_batch.cu): one block per
 // SM (at most 2 * nchains), each taking the next half from a work queue in the
 // order of `order` (item 2i + h = half h of chain order[i]), preparing its end
 // column, running its recursion and, if it finishes second of its chain's two
@@ -123,8 +123,10 @@ cudaError_t launch_batch(int precision, const ChainDev* chains, const int* order
                          const LeadDev* leads, void* ws, double* T, int32_t* status, int* queue,
                          int nsm, cudaStream_t st);
 // Sets the kernels' shared-memory limits for a largest column size Kmax (done by
-// every launcher; also callable ahead of a stream capture).
+// every launcher; also callable ahead of a stream capture): configure_sweep
+// for all of them, configure_batch for the persistent kernel alone.
 cudaError_t configure_sweep(int precision, int Kmax);
+cudaError_t configure_batch(int precision, int Kmax);
 
 // Two-sided sweep (rgf_grad.cu): workspace (16-byte elements) of one chain
 // with segments of seg_cols columns, and the launcher (seg_cols: [nchains] on

@@ -1,6 +1,6 @@
 // rgf_steps.cuh -- one column step of the forward RGF recursion (Eqs. 4-5) and
-// the helpers shared by the forward sweep (rgf_sweep.cu) and the gradient sweep
-// (rgf_grad.cu).  See rgf_sweep.cu for the column slicing.
+// the helpers shared by the forward sweep (rgf_half.cuh) and the gradient sweep
+// (rgf_grad.cu).  See rgf_half.cuh for the column slicing.
 #pragma once
 
 #include <type_traits>
@@ -134,7 +134,7 @@ struct DenseOp {
     }
 };
 
-// The same product on binary64 operands (RGF_FP64_TC's strip product).
+// The same product on binary64 operands (RGF_FP64_TC).
 struct DenseOp64 {
     static constexpr bool kF64 = true;
     const zd* A;
@@ -143,9 +143,12 @@ struct DenseOp64 {
     int ldb;
     zd* C;
     int ldc, r0;
+    bool ta;
     using Old = zd;
-    __device__ bool colA() const { return false; }
-    __device__ zd a(int m, int k) const { return A[(size_t)(r0 + m) * lda + k]; }
+    __device__ bool colA() const { return ta; }
+    __device__ zd a(int m, int k) const {
+        return ta ? A[(size_t)k * lda + r0 + m] : A[(size_t)(r0 + m) * lda + k];
+    }
     __device__ zd b(int k, int n) const { return B[(size_t)k * ldb + n]; }
     __device__ zd load(int m, int n, bool first) const {
         return first ? zd{0.0, 0.0} : C[(size_t)(r0 + m) * ldc + n];
@@ -168,9 +171,21 @@ static __device__ __noinline__ uint32_t tc_dense(int m, int n, int kd, const zf*
     return phase;
 }
 
+// The binary64 copy (RGF_FP64_TC's gradient products).
+static __device__ __noinline__ uint32_t tc_dense64(int m, int n, int kd, const zd* A, int lda,
+                                                   const zd* B, int ldb, zd* C, int ldc, bool ta,
+                                                   tc::Area ar, uint32_t phase) {
+    for (int r0 = 0; r0 < m; r0 += 128) {
+        const DenseOp64 op{A, lda, B, ldb, C, ldc, r0, ta};
+        phase = tc::zgemm(op, min(128, m - r0), n, kd, ar, phase);
+    }
+    return phase;
+}
+
 // C = op(A) B on the tensor cores when the block holds them (double-float
-// operands), else on the FP32 / FP64 pipes.  Every thread; ends with a barrier.
-template <class R, bool TA>
+// operands; binary64 with TC64), else on the FP32 / FP64 pipes.  Every
+// thread; ends with a barrier.
+template <class R, bool TA, bool TC64 = false>
 __device__ void dense_product(int m, int n, int kd, const cx<R>* A, int lda, const cx<R>* B, int ldb,
                               cx<R>* C, int ldc, SweepSmem<R>& s) {
     if constexpr (std::is_same<R, df32>::value) {
@@ -180,6 +195,15 @@ __device__ void dense_product(int m, int n, int kd, const cx<R>* A, int lda, con
                 return;
             }
             s.tcs->phase = tc_dense(m, n, kd, A, lda, B, ldb, C, ldc, TA, s.tcs->ar, s.tcs->phase);
+            return;
+        }
+    } else if constexpr (std::is_same<R, double>::value && TC64) {
+        if (s.tcs) {
+            if (m <= 0 || n <= 0 || kd <= 0) {
+                __syncthreads();
+                return;
+            }
+            s.tcs->phase = tc_dense64(m, n, kd, A, lda, B, ldb, C, ldc, TA, s.tcs->ar, s.tcs->phase);
             return;
         }
     }
@@ -304,7 +328,7 @@ __device__ __forceinline__ cx<R> pair_d(const ChainCtx& c, int kb, int i) {
 //   strip_column: Y = Pprev W (R x K, R the rows of the half's corner block),
 //                 Pout = Y Gk (Pout may alias Pprev; Y may alias the X of
 //                 inv_column).  Needs s.kc and s.kp.
-// The lead-attached first column of a half is prepared elsewhere (rgf_sweep.cu).
+// The lead-attached first column of a half is prepared elsewhere (rgf_half.cuh).
 // kb >= 0 (pair steps, kb = the pair's second column): the diagonal of X
 // additionally loses t^2 kappa_i / d_i (see pair_scales; s.kn holds the keep
 // mask of kb).
@@ -377,7 +401,7 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
     } else if constexpr (std::is_same<R, double>::value && TC64) {
         if (s.tcs) {
             for (int r0 = 0; r0 < rows; r0 += 128) {
-                const DenseOp64 op{Y, KL, Gk, KL, Pout, KL, r0};
+                const DenseOp64 op{Y, KL, Gk, KL, Pout, KL, r0, false};
                 s.tcs->phase = tc::zgemm(op, min(128, rows - r0), K, K, s.tcs->ar, s.tcs->phase);
             }
             return;

@@ -1,350 +1,13 @@
-// rgf_sweep.cu -- the RGF recursion (Eqs. 4-5) and the Landauer trace (Eq. 2)
-// for a batch of chains (ribbon, energy), as two half sweeps per chain joined
-// by one Dyson step (Eq. 3).
-//
-// The paper slices the ribbon into cross-sections and applies, slice after
-// slice, g_j = (z - H_jj - V^T g_{j-1} V)^-1 together with the corner block
-// G_1j = G_1,j-1 V g_j (Eqs. 4-5).  Here each unit cell (2N orbitals) is
-// sliced further into its four atom columns (x = 0, a, 1.5a, 2.5a): a column
-// has no internal hopping, neighbouring columns are coupled by t*I (same row)
-// or by a bidiagonal t-stencil (rows j +- 1).  The recursion is the same
-// Dyson step on blocks of KL = ceil(N/2) or KR = floor(N/2) orbitals, 4L
-// columns per chain.
-//
-// Domain decomposition.  A chain's recursion is strictly sequential along the
-// ribbon; the paper notes that running it in parallel needs a modified
-// recursion (its remark on MPI).  The columns 0 .. n-1 (n = 4L) are cut into
-// a left part 0 .. m-1 and a right part m .. n-1 (m = n/2).  Each part runs
-// the recursion from its own lead, on its own SM, at the same time:
-//
-//   left  (k = 0 .. m-1):   gl_k = (z - eps_k - t^2 S_k^T gl_{k-1} S_k)^-1
-//                           Pl_k = U_even^T G^left_{0,k}  = Pl_{k-1} W_k gl_k
-//   right (k = n-1 .. m):   gr_k = (z - eps_k - t^2 S_{k+1} gr_{k+1} S_{k+1}^T)^-1
-//                           Pr_k = U_odd^T G^right_{n-1,k} = Pr_{k+1} W_{k+1}^T gr_k
-//
-// (W_k = t S_k the coupling of columns k-1 and k; each part sees only its own
-// lead.)  The Dyson equation across the bond between columns m-1 and m then
-// gives the corner block of the whole system,
-//
-//   G_{0,n-1} = G^left_{0,m-1} W_m (I - gr_m SigmaL_m)^-1 G^right_{m,n-1},
-//   SigmaL_m = W_m^T gl_{m-1} W_m,
-//
-// so U_even^T G_{0,n-1} U_odd = (Pl_{m-1} W_m) (I - gr_m SigmaL_m)^-1 Pr_m^T and
-// T = sum_pq gamma_p gamma'_q |(U_even^T G_{0,n-1} U_odd)_pq|^2 (Eq. 2 in the
-// mode basis, gamma = -2 Im w).  Same work as one sweep over n columns, half
-// the sequential depth.
-//
-// Lead-attached columns.  The first column of each part carries the lead
-// self-energy, Sigma = U diag(w) U^T.  Near E = 0 the transverse cut of an
-// armchair ribbon is zigzag-like and the modes with |tau_p| > |t| have a
-// surface state: |w_p| ~ 1/eta (~1e9 eV at eta = 1e-8).  In the site basis
-// those entries would be summed with the order-1 on-site terms and drown
-// them.  The first column is therefore formed and inverted in the mode basis,
-// in binary64, by its own kernel (prep_kernel):
-//
-//   A~ = U^T diag(z - eps) U - diag(w),   g~ = A~^-1,
-//   P_0 = g~ U^T (rows in the mode basis),   g_0 = U P_0 (site basis),
-//
-// where the surface-state modes meet only their own order-1/eta diagonal.
-// The corner blocks are carried with their rows in the mode bases, so the
-// order-eta components that Gamma ~ 1/eta weights in the trace keep their own
-// relative accuracy.  (A lead-attached column with a removed atom is formed
-// in the site basis instead.)
-//
-// Launches (one stream): prep_kernel (binary64, 2 blocks per chain),
-// half_kernel<R, TC> (the recursion of each part, 2 blocks per chain, the
-// dominant kernel), merge_kernel (binary64, 1 block per chain: the Dyson step
-// across the cut, the trace and the status word).  Removed atoms become
-// identity rows/columns with zero couplings (an exact equivalence to dropping
-// them).  With TC (precision RGF_MIXED_TC) the two dense contractions of a
-// column step -- the Gauss-Jordan rank-b updates and the strip product -- run
-// on the tcgen05 tensor cores by exact digit slicing of their double-float
-// operands (rgf_tc.cuh); every block then holds the SM's TMEM for the launch.
-#include "rgf_steps.cuh"
+// rgf_sweep.cu -- the three-launch schedule of the forward sweep: end-column
+// preparation, half sweeps and joins as separate launches over every chain
+// (the method and the device bodies are in rgf_half.cuh).
+#include "rgf_half.cuh"
 
 namespace rgf {
 
 size_t sweep_smem_bytes(int Kmax, bool tc) {
     return sweep_total_bytes(Kmax, gj_panel_width(Kmax, tc), tc);
 }
-
-namespace {
-
-// Columns of the left part; the right part has ncol - m.
-__host__ __device__ inline int left_cols(int ncol) { return ncol / 2; }
-
-// The buffers of one half of a chain's workspace (16-byte elements, ld KL).
-template <class R>
-struct Half {
-    cx<R>* X;        // slice matrix / scratch
-    cx<R>* G;        // g of the last column done
-    cx<R>* P;        // corner block, rows in the lead's mode basis
-    int* flag;       // Gauss-Jordan / tensor-core flags of this half
-};
-template <class R>
-__device__ inline Half<R> half_of(void* ws, const ChainDev& ch, int h) {
-    const size_t B = (size_t)col_KL(ch.N) * col_KL(ch.N);
-    cx<R>* base = reinterpret_cast<cx<R>*>(ws) + ch.ws_off + (size_t)h * half_ws_elems(ch.N);
-    return Half<R>{base, base + B, base + 2 * B, reinterpret_cast<int*>(base + 3 * B)};
-}
-
-// In-place conversion of a K1 x K2 block (ld) between binary64 and the
-// working precision (both 16-byte complex elements).  Every thread; barrier.
-template <class R>
-__device__ void to_working(cx<R>* p, int K1, int K2, int ld) {
-    for (int e = threadIdx.x; e < K1 * K2; e += NT) {
-        const int i = e / K2, j = e % K2;
-        const zd v = reinterpret_cast<zd*>(p)[(size_t)i * ld + j];
-        p[(size_t)i * ld + j] = from_z<R>(v.re, v.im);
-    }
-    __syncthreads();
-}
-template <class R>
-__device__ void to_binary64(cx<R>* p, int K1, int K2, int ld) {
-    for (int e = threadIdx.x; e < K1 * K2; e += NT) {
-        const int i = e / K2, j = e % K2;
-        const zd v = to_z(p[(size_t)i * ld + j]);
-        reinterpret_cast<zd*>(p)[(size_t)i * ld + j] = v;
-    }
-    __syncthreads();
-}
-
-__device__ inline double max_abs2(const zd* A, int K, int ld, double* red) {
-    double m = 0.0;
-    for (int e = threadIdx.x; e < K * K; e += NT) {
-        const double a = cabs2(A[(size_t)(e / K) * ld + e % K]);
-        m = (a > m || isnan(a)) ? a : m;
-    }
-    return block_max(m, red);
-}
-
-// Everything the sweep kernels read besides their own shared memory.
-struct SweepArgs {
-    const ChainDev* chains;
-    const int* order;
-    int nchains, Kmax;
-    double eta_d;
-    const zd* leadout;
-    const int* lead_status;
-    const LeadDev* leads;
-    void* ws;
-    double* T;
-    int32_t* status;
-};
-
-// The lead-attached first column of half h of chain ci, in binary64: h = 0 the
-// left lead's column 0 (KL even-row left atoms), h = 1 the right lead's column
-// n-1 (KR odd-row right atoms).  Writes g (site basis) and P (rows in the
-// lead's mode basis) into the half's G and P in the working precision R, and
-// the Gauss-Jordan flags into the half's flag word.  bm: the launch's panel
-// width.  Every thread; ends with a barrier.
-template <class R>
-__device__ __noinline__ void prep_body(const SweepArgs a, int ci, int h, int bm) {
-    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, false, bm);
-    const ChainDev& ch = a.chains[ci];
-    const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, h);
-    const Half<R> hw = half_of<R>(a.ws, ch, h);
-    zd* X = reinterpret_cast<zd*>(hw.X);
-    zd* G = reinterpret_cast<zd*>(hw.G);
-    zd* P = reinterpret_cast<zd*>(hw.P);
-    const int KL = c.KL, k = h ? c.ncol - 1 : 0, K = h ? c.KR : c.KL;
-    const zd* U = h ? c.UR() : c.UL();                  // K x K, ld K
-    const zd* Sig = h ? c.SigR() : c.SigL();            // K x K, ld K
-    load_col(c, k, s.kc, s.eps);
-    if (threadIdx.x == 0) s.gj.ctl[2] = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < K; i += NT)
-        if (!s.kc[i]) s.gj.ctl[2] = 1;
-    __syncthreads();
-    const bool removed = s.gj.ctl[2] != 0;
-    int flag;
-    if (!removed) {
-        // A~ = U^T diag(z - eps) U - diag(w) into G; g~ = A~^-1 into X
-        for (int e = threadIdx.x; e < K * K; e += NT) {
-            const int i = e / K, p = e % K;
-            const double u = U[(size_t)i * K + p].re;
-            X[(size_t)i * KL + p] = {(c.z.re - s.eps[i]) * u, c.z.im * u};
-        }
-        __syncthreads();
-        cta_gemm<double, true, false>(K, K, K, U, K, X, KL, G, KL, GEMM_SET, s.gemm);
-        for (int p = threadIdx.x; p < K; p += NT) G[(size_t)p * KL + p] = csub(G[(size_t)p * KL + p], c.w()[p]);
-        __syncthreads();
-        const double amax2 = max_abs2(G, K, KL, s.red);
-        flag = cta_gj_invert<double>(G, K, KL, X, KL, s.gj, amax2);
-        // P = g~ U^T, then g = U P
-        cta_gemm<double, false, true>(K, K, K, X, KL, U, K, P, KL, GEMM_SET, s.gemm);
-        cta_gemm<double, false, false>(K, K, K, U, K, P, KL, G, KL, GEMM_SET, s.gemm);
-    } else {
-        // site basis: (z - eps) I - Sigma on the kept atoms, identity rows and
-        // columns at removed atoms; then P = U^T g
-        for (int e = threadIdx.x; e < K * K; e += NT) {
-            const int i = e / K, l = e % K;
-            zd v;
-            if (!s.kc[i] || !s.kc[l]) v = (i == l) ? zd{1.0, 0.0} : zd{0.0, 0.0};
-            else v = csub((i == l) ? zd{c.z.re - s.eps[i], c.z.im} : zd{0.0, 0.0}, Sig[(size_t)i * K + l]);
-            X[(size_t)i * KL + l] = v;
-        }
-        __syncthreads();
-        const double amax2 = max_abs2(X, K, KL, s.red);
-        flag = cta_gj_invert<double>(X, K, KL, G, KL, s.gj, amax2);
-        cta_gemm<double, true, false>(K, K, K, U, K, G, KL, P, KL, GEMM_SET, s.gemm);
-    }
-    to_working<R>(hw.G, K, K, KL);
-    to_working<R>(hw.P, K, K, KL);
-    if (threadIdx.x == 0) *hw.flag = flag;
-    __syncthreads();
-}
-
-// The recursion of half h of chain ci from its second column to the cut:
-// columns 1 .. m-1 (left) or n-2 .. m (right), in pairs of t I-bonded columns
-// wherever the chain's schedule and pair_ok allow (pair_column in
-// rgf_steps.cuh), else one column at a time.  bm: the launch's panel width
-// (the chain's schedule may narrow it); tst: the block's tensor-core state
-// (TC).  ORs the Gauss-Jordan
-// and tensor-core flags into the half's flag word.  Every thread; ends with a
-// barrier.
-template <class R, bool TC>
-__device__ __forceinline__ void half_body(const SweepArgs& a, int ci, int h, int bm, tc::State* tst) {
-    SweepSmem<R> s = carve<R>(rgf_dyn_smem, a.Kmax, TC, bm);
-    const ChainDev& ch = a.chains[ci];
-    const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, h);
-    const Half<R> hw = half_of<R>(a.ws, ch, h);
-    const int m = left_cols(c.ncol), steps = h ? c.ncol - m : m;
-    if (ch.panel > 0 && ch.panel < bm) s.gj.bmax = ch.panel;
-    const bool pairs_on = ch.pairs != 0;
-    if constexpr (TC) {
-        s.gj.tcs = tst;
-        s.tcs = tst;
-    }
-    int flag = 0;
-    for (int j = 1; j < steps;) {
-        const int k = h ? c.ncol - 1 - j : j;
-        // a pair: this column and the next one in the recursion share t I bonds
-        // (c0-c1 or c2-c3 of one cell); the second column of the first pair of
-        // each half is the one after the prepared end column
-        const int kb = h ? k - 1 : k + 1;
-        const bool pairable = pairs_on && j + 1 < steps && (h ? (k & 1) == 1 : (k & 1) == 0);
-        load_col(c, k, s.kc, s.eps);
-        load_col(c, prev_col(c, k), s.kp, nullptr);
-        if (pairable) load_col(c, kb, s.kn, nullptr);
-        __syncthreads();
-        const bool pair = pairable && pair_ok<R>(c, kb, s);
-        // one call site each for the inverse and the strip product (inlined)
-        flag |= inv_column<R, TC>(c, k, hw.G, hw.G, hw.X, s, pair ? kb : -1);
-        if (pair) pair_scales<R>(c, k, kb, hw.G, s);
-        strip_column<R, TC>(c, k, hw.G, hw.P, hw.P, hw.X, s);
-        if (pair) pair_finish<R>(c, k, hw.G, s);
-        j += pair ? 2 : 1;
-    }
-    if constexpr (TC) {
-        if (*(volatile int*)tst->ar.err()) flag |= 4;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *hw.flag |= flag;
-    __syncthreads();
-}
-
-// The Dyson step across the bond between columns m-1 and m of chain ci, in
-// binary64, and the trace; writes T and the status word.  Scratch: the two
-// halves' X and, once read, their G and P.  bm: the launch's panel width.
-// Every thread; ends with a barrier.
-template <class R>
-__device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
-    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, false, bm);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const ChainDev& ch = a.chains[ci];
-    const int lst = lead_state(a.lead_status, ch.lead);
-    if (lst != ST_OK) {
-        if (threadIdx.x == 0) {
-            a.T[ci] = NAN;
-            if (a.status) a.status[ci] = lst;
-        }
-        __syncthreads();
-        return;
-    }
-    const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, 0);
-    const Half<R> L = half_of<R>(a.ws, ch, 0), Rt = half_of<R>(a.ws, ch, 1);
-    const int KL = c.KL, KR = c.KR, m = left_cols(c.ncol);
-    const int K = col_size(c, m), Kp = col_size(c, m - 1), ct = m & 3;
-    int flag = *L.flag | *Rt.flag;
-    load_col(c, m, s.kc, nullptr);
-    load_col(c, m - 1, s.kp, nullptr);
-    __syncthreads();
-    zd* XL = reinterpret_cast<zd*>(L.X);
-    zd* XR = reinterpret_cast<zd*>(Rt.X);
-    zd* GLd = reinterpret_cast<zd*>(L.G);
-    zd* GRd = reinterpret_cast<zd*>(Rt.G);
-    zd* PRd = reinterpret_cast<zd*>(Rt.P);
-    const double t = c.t, t2 = c.t2;
-    // SigmaL_m = t^2 S^T gl_{m-1} S (kept atoms only) into XL
-    for (int i = warp; i < K; i += NWARP) {
-        int a0, a1;
-        col_src(ct, i, Kp, a0, a1);
-        const bool ki = s.kc[i];
-        const bool ka0 = a0 >= 0 && s.kp[a0], ka1 = a1 >= 0 && s.kp[a1];
-        for (int l = lane; l < K; l += 32) {
-            zd v = {0.0, 0.0};
-            if (ki && s.kc[l]) {
-                int b0, b1;
-                col_src(ct, l, Kp, b0, b1);
-                const bool kb0 = b0 >= 0 && s.kp[b0], kb1 = b1 >= 0 && s.kp[b1];
-                if (ka0 && kb0) v = cadd(v, to_z(L.G[(size_t)a0 * KL + b0]));
-                if (ka0 && kb1) v = cadd(v, to_z(L.G[(size_t)a0 * KL + b1]));
-                if (ka1 && kb0) v = cadd(v, to_z(L.G[(size_t)a1 * KL + b0]));
-                if (ka1 && kb1) v = cadd(v, to_z(L.G[(size_t)a1 * KL + b1]));
-                v = cscale(v, t2);
-            }
-            XL[(size_t)i * KL + l] = v;
-        }
-    }
-    __syncthreads();
-    // X = I - gr_m SigmaL_m into XR, its inverse into XL
-    to_binary64<R>(Rt.G, K, K, KL);
-    cta_gemm<double, false, false>(K, K, K, GRd, KL, XL, KL, XR, KL, GEMM_SET, s.gemm);
-    for (int e = threadIdx.x; e < K * K; e += NT) {
-        const int i = e / K, l = e % K;
-        zd& x = XR[(size_t)i * KL + l];
-        x = {((i == l) ? 1.0 : 0.0) - x.re, -x.im};
-    }
-    __syncthreads();
-    const double amax2 = max_abs2(XR, K, KL, s.red);
-    flag |= cta_gj_invert<double>(XR, K, KL, XL, KL, s.gj, amax2);
-    // Y = Pl_{m-1} W_m (KL x K) into GL (gl no longer needed), then
-    // Y (I - gr SigmaL)^-1 into XR and its product with Pr_m^T into GL
-    for (int r = warp; r < KL; r += NWARP)
-        for (int l = lane; l < K; l += 32) {
-            zd v = {0.0, 0.0};
-            if (s.kc[l]) {
-                int a0, a1;
-                col_src(ct, l, Kp, a0, a1);
-                if (a0 >= 0 && s.kp[a0]) v = cadd(v, to_z(L.P[(size_t)r * KL + a0]));
-                if (a1 >= 0 && s.kp[a1]) v = cadd(v, to_z(L.P[(size_t)r * KL + a1]));
-                v = cscale(v, t);
-            }
-            GLd[(size_t)r * KL + l] = v;
-        }
-    __syncthreads();
-    cta_gemm<double, false, false>(KL, K, K, GLd, KL, XL, KL, XR, KL, GEMM_SET, s.gemm);
-    to_binary64<R>(Rt.P, KR, K, KL);
-    cta_gemm<double, false, true>(KL, KR, K, XR, KL, PRd, KL, GLd, KL, GEMM_SET, s.gemm);
-    // T = sum_pq gamma_p gamma'_q |P_pq|^2
-    double acc = 0.0;
-    const zd* w = c.w();
-    for (int e = threadIdx.x; e < KL * KR; e += NT) {
-        const int p = e / KR, q = e % KR;
-        const zd v = GLd[(size_t)p * KL + q];
-        acc += (-2.0 * w[p].im) * (-2.0 * w[q].im) * (v.re * v.re + v.im * v.im);
-    }
-    const double T = block_sum(acc, s.red);
-    if (threadIdx.x == 0) {
-        const int st = chain_status(c, flag, T);
-        a.T[ci] = (st == ST_OK) ? T : NAN;
-        if (a.status) a.status[ci] = st;
-    }
-    __syncthreads();
-}
-
-}  // namespace
 
 // Three-launch schedule: each kernel runs one step for every half (or chain),
 // blocks in the order of `order`.
@@ -373,119 +36,34 @@ __global__ void __launch_bounds__(NT, 1) merge_kernel(SweepArgs a, int bm) {
     merge_body<R>(a, a.order[blockIdx.x], bm);
 }
 
-// Persistent schedule: gridDim.x blocks (at most one per SM) take halves from
-// the work queue (queue[0] = next item; item 2i + h = half h of chain
-// order[i], so the halves go out longest chain first) until it is empty.  A
-// block prepares its half's end column, runs its recursion, and counts the
-// half done on its chain (queue[1 + ci]); the block that brings the count to
-// two -- its partner half is complete by then -- joins the halves and writes T
-// and the status word.  Nothing waits: a block never spins on another block,
-// the queue and the counters only hand out work.  The release of a finished
-// half (its workspace, by every thread) to the joining block is the block
-// barrier, a device-scope fence and the counter's atomic on one side, the
-// atomic and a fence on the other.  With TC the block holds TMEM for the
-// whole launch.
-template <class R, bool TC>
-__global__ void __launch_bounds__(NT, 1) batch_kernel(SweepArgs a, int bm, int* queue) {
-    __shared__ int s_item, s_join;
-    tc::State tst;
-    if constexpr (TC) {
-        SweepSmem<R> s = carve<R>(rgf_dyn_smem, a.Kmax, TC, bm);
-        tc_attach<R>(a.Kmax, s, tst);
-    }
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&queue[0], 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= 2 * a.nchains) break;
-        {
-            const int ci = a.order[item >> 1], h = item & 1;
-            if (lead_state(a.lead_status, a.chains[ci].lead) == ST_OK) {
-                prep_body<R>(a, ci, h, bm);
-                half_body<R, TC>(a, ci, h, bm, &tst);
-            }
-        }
-        // the chain is looked up again from the item in shared memory, so that
-        // nothing of the loop stays live in registers across the half sweep
-        if (threadIdx.x == 0) {
-            const int cj = a.order[*(volatile int*)&s_item >> 1];
-            __threadfence();
-            s_join = cj | (atomicAdd(&queue[1 + cj], 1) << 30);
-            __threadfence();
-        }
-        __syncthreads();
-        {
-            const int j = *(volatile int*)&s_join;
-            if ((j >> 30) == 1) merge_body<R>(a, j & ((1 << 30) - 1), bm);
-        }
-        __syncthreads();                 // s_item and s_join are rewritten next
-    }
-    if constexpr (TC) tc::teardown(tst.ar);
-}
-
 namespace {
 
-template <class K>
-cudaError_t set_smem(K kern, size_t smem) {
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-// Precisions: 0 RGF_FP64, 1 RGF_MIXED, 2 RGF_MIXED_TC, 3 RGF_FP64_TC.
-bool uses_tc(int precision) { return precision == 2 || precision == 3; }
-bool binary64(int precision) { return precision == 0 || precision == 3; }
-
-// Panel width of a launch of `precision` and the shared memory of its
-// binary64 steps and of its recursion.
-int launch_panel(int precision, int Kmax) { return gj_panel_width(Kmax, uses_tc(precision)); }
-size_t f64_smem(int precision, int Kmax) {
-    return sweep_total_bytes(Kmax, launch_panel(precision, Kmax), false);
-}
-size_t rec_smem(int precision, int Kmax) {
-    const size_t b = sweep_total_bytes(Kmax, launch_panel(precision, Kmax), uses_tc(precision));
-    // a tensor-core block holds all 512 TMEM columns: ask for more than half
-    // of an SM's shared memory so that no second block shares its SM (the
-    // register file already allows only one)
-    return uses_tc(precision) && b < 120 * 1024 ? 120 * 1024 : b;
-}
-
-SweepArgs make_args(const ChainDev* chains, const int* order, int nchains, int Kmax,
-                    double eta_device, const void* leadout, const int* lead_status,
-                    const LeadDev* leads, void* ws, double* T, int32_t* status) {
-    return SweepArgs{chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status,
-                     leads, ws, T, status};
+// The shared-memory limits of the three-launch kernels of `precision`.
+cudaError_t configure_phased(int precision, int Kmax) {
+    const size_t f64 = f64_smem(precision, Kmax), rec = rec_smem(precision, Kmax);
+    cudaError_t e;
+    if (binary64(precision)) {
+        if ((e = set_smem(prep_kernel<double>, f64)) != cudaSuccess) return e;
+        if ((e = set_smem(merge_kernel<double>, f64)) != cudaSuccess) return e;
+        return set_smem(precision == 3 ? half_kernel<double, true> : half_kernel<double, false>, rec);
+    }
+    if ((e = set_smem(prep_kernel<df32>, f64)) != cudaSuccess) return e;
+    if ((e = set_smem(merge_kernel<df32>, f64)) != cudaSuccess) return e;
+    return set_smem(precision == 2 ? half_kernel<df32, true> : half_kernel<df32, false>, rec);
 }
 
 }  // namespace
 
 cudaError_t configure_sweep(int precision, int Kmax) {
-    const size_t f64 = f64_smem(precision, Kmax), rec = rec_smem(precision, Kmax);
-    const size_t both = rec > f64 ? rec : f64;
-    cudaError_t e;
-    if (binary64(precision)) {
-        if ((e = set_smem(prep_kernel<double>, f64)) != cudaSuccess) return e;
-        if ((e = set_smem(merge_kernel<double>, f64)) != cudaSuccess) return e;
-        if (precision == 3) {
-            if ((e = set_smem(half_kernel<double, true>, rec)) != cudaSuccess) return e;
-            return set_smem(batch_kernel<double, true>, both);
-        }
-        if ((e = set_smem(half_kernel<double, false>, rec)) != cudaSuccess) return e;
-        return set_smem(batch_kernel<double, false>, both);
-    }
-    if ((e = set_smem(prep_kernel<df32>, f64)) != cudaSuccess) return e;
-    if ((e = set_smem(merge_kernel<df32>, f64)) != cudaSuccess) return e;
-    if (precision == 2) {
-        if ((e = set_smem(half_kernel<df32, true>, rec)) != cudaSuccess) return e;
-        return set_smem(batch_kernel<df32, true>, both);
-    }
-    if ((e = set_smem(half_kernel<df32, false>, rec)) != cudaSuccess) return e;
-    return set_smem(batch_kernel<df32, false>, both);
+    cudaError_t e = configure_phased(precision, Kmax);
+    return e == cudaSuccess ? configure_batch(precision, Kmax) : e;
 }
 
 cudaError_t launch_prep(int precision, const ChainDev* chains, const int* order, int nchains,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
                         const LeadDev* leads, void* ws, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    cudaError_t e = configure_sweep(precision, Kmax);
+    cudaError_t e = configure_phased(precision, Kmax);
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, nullptr, nullptr);
@@ -498,7 +76,7 @@ cudaError_t launch_half(int precision, const ChainDev* chains, const int* order,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
                         const LeadDev* leads, void* ws, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    cudaError_t e = configure_sweep(precision, Kmax);
+    cudaError_t e = configure_phased(precision, Kmax);
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, nullptr, nullptr);
@@ -515,31 +93,12 @@ cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
                          cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
-    cudaError_t e = configure_sweep(precision, Kmax);
+    cudaError_t e = configure_phased(precision, Kmax);
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, T, status);
     auto kern = binary64(precision) ? merge_kernel<double> : merge_kernel<df32>;
     kern<<<nchains, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch(int precision, const ChainDev* chains, const int* order, int nchains,
-                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
-                         const LeadDev* leads, void* ws, double* T, int32_t* status, int* queue,
-                         int nsm, cudaStream_t st) {
-    if (nchains <= 0) return cudaSuccess;
-    cudaError_t e = configure_sweep(precision, Kmax);
-    if (e != cudaSuccess) return e;
-    const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
-                                  leads, ws, T, status);
-    const size_t f64 = f64_smem(precision, Kmax), rec = rec_smem(precision, Kmax);
-    const int grid = nsm < 2 * nchains ? (nsm > 0 ? nsm : 1) : 2 * nchains;
-    auto kern = precision == 0   ? batch_kernel<double, false>
-                : precision == 3 ? batch_kernel<double, true>
-                : precision == 2 ? batch_kernel<df32, true>
-                                 : batch_kernel<df32, false>;
-    kern<<<grid, NT, rec > f64 ? rec : f64, st>>>(a, launch_panel(precision, Kmax), queue);
     return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ T_HOP = -2.7
 GOLDEN = Path(__file__).resolve().parent / "golden"
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-8), (2, 1e-8)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-8), (2, 1e-8), (3, 1e-9)])
 def test_gradient_matches_oracle_closed_form(rgflib, prec, tol):
     N, L = 11, 6
     eps = workloads.anderson_onsite(N, L, 0.3, 11)
@@ -37,7 +37,7 @@ def test_gradient_oracle_n11_l20(rgflib):
     eps = workloads.anderson_onsite(N, L, 0.15, 4)
     rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps)
     Es = np.array([-0.8, -0.2, 0.45])
-    for prec, tol in ((0, 1e-10), (1, 1e-8), (2, 1e-8)):
+    for prec, tol in ((0, 1e-10), (1, 1e-8), (2, 1e-8), (3, 1e-9)):
         T, g, st = rgflib.conductance_grad([rib] * 3, Es, 1e-8, 1e-8, prec)
         for c, E in enumerate(Es):
             ref = ograd.closed_form(N, L, E, 1e-8, 1e-8, T_HOP, eps, None)
@@ -76,7 +76,7 @@ def test_gradient_against_finite_differences_n101(rgflib):
             ribs.append(rgflib.Ribbon(N, L, T_HOP, onsite=e2))
     Tfd, st = rgflib.conductance(ribs, np.full(len(ribs), E))
     fd = (Tfd[0::2] - Tfd[1::2]) / (2 * d)
-    for prec in (0, 1, 2):
+    for prec in (0, 1, 2, 3):
         T, g, st = rgflib.conductance_grad([rib], np.array([E]), 1e-8, 1e-8, prec, ckpt_stride=23)
         assert st[0] == 0
         gs = np.array([g[0, n, i] for (n, i) in sites])
@@ -84,7 +84,7 @@ def test_gradient_against_finite_differences_n101(rgflib):
         assert np.all(err < 1e-5 + 1e-4 * np.abs(fd)), (prec, err.max())
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-7), (1, 1e-5), (2, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-7), (1, 1e-5), (2, 1e-5), (3, 1e-5)])
 def test_gradient_next_to_a_half_system_pole(rgflib, prec, tol):
     # N = 20, L = 40 (Anderson +-0.15 eV, seed 7) at E = -0.0764 eV, next to a
     # pole of the half systems: a reverse sweep over the column slices is off
@@ -100,7 +100,7 @@ def test_gradient_next_to_a_half_system_pole(rgflib, prec, tol):
     assert err < tol, (prec, err)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 2e-4), (2, 2e-4)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-5), (1, 2e-4), (2, 2e-4), (3, 2e-4)])
 def test_gradient_near_zero_energy_matches_golden(rgflib, prec, tol):
     # The N = 101, L = 500 ribbon at three energies with |E| < 0.07 eV: the
     # largest entries, seeded random sites and sites where a reverse sweep
