@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="each step through rgf_conductance_dev instead of a prepared CUDA-graph "
                          "batch")
+    ap.add_argument("--domains", type=int, default=2,
+                    help="domains per chain (default 2; 0: automatic, more than 2 for few long chains)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default schedule instead of the autotuner's choice for the width")
     ap.add_argument("--check-chains", type=int, default=0,
@@ -486,6 +488,10 @@ def main():
     # lead decimation, work-queue reset, persistent batch kernel) or the same
     # launches through rgf_conductance_dev.
     rgf.set_schedule(rgf.RGF_SCHED_PHASED if args.schedule == "phased" else rgf.RGF_SCHED_PERSISTENT)
+    rgf.set_domains(args.domains)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    ndom = args.domains if args.domains >= 2 else rgf.auto_domains(n, 4 * L, nsm)
+    ndom = max(2, min(ndom, 2 * L))
     tuned = None
     if not args.no_autotune:
         t0 = time.perf_counter()
@@ -599,6 +605,8 @@ def main():
     # against the measured sustained bf16 tensor peak.
     ph = np.array(phases)                       # [steps, 4]: lead, prep, half, merge
     half_s = float(ph[:, 2].mean()) / 1e3
+    if ndom > 2:                                # the joins are part of the recursion's work
+        half_s = float((ph[:, 2] + ph[:, 3]).mean()) / 1e3
     steps_ok = float(ok.sum()) * L
     F_alg = cell_slicing_flops_per_step(N)
     achieved = F_alg * steps_ok / half_s / 1e12
@@ -613,7 +621,8 @@ def main():
     else:
         bound, peak = "tensor", float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         peak_src = f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peaks_src})"
-    kernel_tag = "batch" if args.schedule == "persistent" else "half"
+    kernel_tag = ("domain" if ndom > 2 else
+                  "batch" if args.schedule == "persistent" else "half")
     traffic_file = ROOT / "profiles" / "traffic.json"
     traffic, traffic_note = None, "no DRAM counters recorded for this kernel and workload"
     if traffic_file.exists():
@@ -649,6 +658,9 @@ def main():
             "phases_note": ("persistent: ms_kernel = the batch kernel (end columns, half sweeps, joins), "
                             "ms_prep = the work-queue reset, ms_merge = 0"
                             if kernel_tag == "batch" else
+                            "domains: achieved over ms_kernel (every domain of every chain) + "
+                            "ms_merge (the joins and the trace)"
+                            if kernel_tag == "domain" else
                             "phased: ms_kernel = the half-sweep launch")}
 
     cpu = None
@@ -659,7 +671,7 @@ def main():
     # our kernels per step: energy fill, lead decimation, then the batch kernel
     # (persistent) or preparation, half sweeps and join (phased); one width,
     # so one launch group
-    launches_per_step = 2 + (1 if args.schedule == "persistent" else 3)
+    launches_per_step = 2 + (1 if args.schedule == "persistent" and ndom == 2 else 3)
     if rank == 0:
         T_all = np.full(len(job), np.nan)
         for idx, Tr, _ in gathered:
@@ -675,7 +687,9 @@ def main():
                           "precision": args.precision, "l2": "flushed (256 MB write) between steps",
                           "parallelism": f"chains sharded over {world} rank(s) (LPT), one disorder "
                                          "realisation per rank",
-                          "schedule": args.schedule + (" (CUDA graph)" if use_graph else ""),
+                          "schedule": (args.schedule if ndom == 2 else "phased") +
+                                      (" (CUDA graph)" if use_graph else ""),
+                          "domains_per_chain": ndom,
                           "tuning": tuned},
                "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                           "reasons": clocks["reasons"]},

@@ -125,6 +125,25 @@ std::vector<rgf_tune_entry> g_tune[4];
 int g_schedule = RGF_SCHED_PHASED;
 thread_local const rgf_tune_entry* g_force = nullptr;
 thread_local int g_force_schedule = -1;
+int g_domains = 2;                       // domains per chain; 0 = automatic
+thread_local int g_force_domains = 0;
+
+// Domains per chain for a call (forward sweep): forced (>= 2), else as many as
+// leave every chain one SM per domain, but at most sqrt(ncol / 16): the joins
+// run one after the other, about sixteen column steps each, so that many
+// domains balance the shortened recursion against the joins.  At most ncol/2
+// (every domain two columns or more).
+int domains_for(int requested, int nchains, int ncol_min, int nsm) {
+    int d;
+    if (requested >= 2) {
+        d = requested;
+    } else {
+        const int per = nchains > 0 ? nsm / nchains : 2;
+        const int cap = (int)std::floor(std::sqrt((double)ncol_min / 16.0));
+        d = std::max(2, std::min(per, cap));
+    }
+    return std::max(2, std::min(d, ncol_min / 2));
+}
 
 rgf_tune_entry default_entry() { return rgf_tune_entry{0x7fffffff, RGF_ENGINE_TENSOR, 0, 1}; }
 
@@ -153,6 +172,7 @@ struct Plan {
     std::vector<rgf::LeadDev> leads;
     std::vector<int> order;          // all chains, longest first (gradient sweep)
     std::vector<Group> groups;       // forward sweep
+    int ndom = 2;                    // domains per chain (forward sweep)
     std::vector<int> seg_cols;
     size_t ws_elems = 0, lead_ws_elems = 0, lead_out_elems = 0, grad_elems = 0;
     int Kmax = 1;
@@ -170,6 +190,20 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, int precision, P
     pl.seg_cols.resize(nchains);
     std::vector<double> cost(nchains);
     std::vector<int> engine(nchains, 0);
+    if (!grad) {
+        int ncol_min = 1 << 30, nsm = 1;
+        for (int c = 0; c < nchains; ++c) {
+            if (!rib[c]) return fail(RGF_EINVAL, "rib[" + std::to_string(c) + "] is NULL");
+            ncol_min = std::min(ncol_min, 4 * rib[c]->L);
+        }
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 1;
+        int req = g_force_domains;
+        if (!req) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            req = g_domains;
+        }
+        pl.ndom = domains_for(req, nchains, ncol_min, nsm);
+    }
     for (int c = 0; c < nchains; ++c) {
         const rgf_ribbon* r = rib[c];
         if (!r) return fail(RGF_EINVAL, "rib[" + std::to_string(c) + "] is NULL");
@@ -198,7 +232,7 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, int precision, P
             ch.tc = (int8_t)(tc_precision(precision) && te.engine == RGF_ENGINE_TENSOR);
             engine[c] = ch.tc;
             pl.seg_cols[c] = 0;
-            pl.ws_elems += rgf::sweep_ws_elems(r->N);
+            pl.ws_elems += rgf::chain_ws_elems(r->N, pl.ndom);
         }
         rgf::LeadDev& ld = pl.leads[c];
         ld.N = r->N;
@@ -334,7 +368,7 @@ rgf_status enqueue_forward(const Plan& pl, const DevLayout& d, unsigned char* ba
     RGF_CUDA(rgf::launch_lead(dleads, n, pl.Kmax, eta_lead, dlws, dlout, dlst, nullptr, st),
              "lead decimation launch");
     RGF_CUDA(rec(1), "cudaEventRecord");
-    if (schedule == RGF_SCHED_PERSISTENT) {
+    if (schedule == RGF_SCHED_PERSISTENT && pl.ndom == 2) {
         RGF_CUDA(cudaMemsetAsync(dqueue, 0, d.queue_bytes, st), "cudaMemsetAsync(work queue)");
         RGF_CUDA(rec(2), "cudaEventRecord");
         const int nsm = sm_count();
@@ -352,7 +386,7 @@ rgf_status enqueue_forward(const Plan& pl, const DevLayout& d, unsigned char* ba
         size_t k = 0;
         for (const Group& g : pl.groups) {
             RGF_CUDA(rgf::launch_prep(g.precision, dchains, dorder + k, (int)g.order.size(), g.Kmax,
-                                      eta_device, dlout, dlst, dleads, dws, st),
+                                      eta_device, dlout, dlst, dleads, dws, st, pl.ndom),
                      "end-column preparation launch");
             k += g.order.size();
         }
@@ -360,7 +394,7 @@ rgf_status enqueue_forward(const Plan& pl, const DevLayout& d, unsigned char* ba
         k = 0;
         for (const Group& g : pl.groups) {
             RGF_CUDA(rgf::launch_half(g.precision, dchains, dorder + k, (int)g.order.size(), g.Kmax,
-                                      eta_device, dlout, dlst, dleads, dws, st),
+                                      eta_device, dlout, dlst, dleads, dws, st, pl.ndom),
                      "half sweep launch");
             k += g.order.size();
         }
@@ -368,7 +402,8 @@ rgf_status enqueue_forward(const Plan& pl, const DevLayout& d, unsigned char* ba
         k = 0;
         for (const Group& g : pl.groups) {
             RGF_CUDA(rgf::launch_merge(g.precision, dchains, dorder + k, (int)g.order.size(), g.Kmax,
-                                       eta_device, dlout, dlst, dleads, dws, T_dev, status_dev, st),
+                                       eta_device, dlout, dlst, dleads, dws, T_dev, status_dev, st,
+                                       pl.ndom),
                      "merge launch");
             k += g.order.size();
         }
@@ -802,6 +837,22 @@ rgf_status rgf_set_schedule(int schedule) {
     return RGF_OK;
 }
 
+rgf_status rgf_set_domains(int ndom) {
+    if (ndom != 0 && (ndom < 2 || ndom > 4096)) return fail(RGF_EINVAL, "ndom must be 0 or in [2, 4096]");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_domains = ndom;
+    return RGF_OK;
+}
+
+int rgf_get_domains(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_domains;
+}
+
+int rgf_auto_domains(int nchains, int ncol_min, int nsm) {
+    return domains_for(0, nchains, std::max(ncol_min, 4), std::max(nsm, 1));
+}
+
 int rgf_get_schedule(void) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     return g_schedule;
@@ -902,9 +953,11 @@ rgf_status rgf_autotune(int precision, const int* N, int nN, int cells, int reps
             for (int rep = 0; rep <= reps && result == RGF_OK; ++rep) {   // rep 0: warm-up
                 g_force = &cand[ci];
                 g_force_schedule = RGF_SCHED_PHASED;
+                g_force_domains = 2;
                 result = run_path(&r, dE, 1, 1e-8, 1e-8, precision, 0, dT, nullptr);
                 g_force = nullptr;
                 g_force_schedule = -1;
+                g_force_domains = 0;
                 if (result != RGF_OK) break;
                 double ph[kProfEvents - 1];
                 result = rgf_profile_read_phases(ph);

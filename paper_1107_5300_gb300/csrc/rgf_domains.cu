@@ -1,0 +1,52 @@
+// rgf_domains.cu -- the recursion of chains cut into more than two domains:
+// the two lead-attached halves at the ends and ndom - 2 interior domains
+// between them, every domain on its own SM at the same time; merge_body joins
+// them (the method and the device bodies are in rgf_half.cuh).
+#include "rgf_half.cuh"
+
+namespace rgf {
+
+// Block b runs domain b % ndom of chain order[b / ndom].
+template <class R, bool TC>
+__global__ void __launch_bounds__(NT, 1) domain_kernel(SweepArgs a, int bm) {
+    const int ci = a.order[blockIdx.x / a.ndom], d = blockIdx.x % a.ndom;
+    if (lead_state(a.lead_status, a.chains[ci].lead) != ST_OK) return;
+    tc::State tst;
+    if constexpr (TC) {
+        SweepSmem<R> s = carve<R>(rgf_dyn_smem, a.Kmax, TC, bm);
+        tc_attach<R>(a.Kmax, s, tst);
+    }
+    domain_body<R, TC>(a, ci, d, bm, &tst);
+    if constexpr (TC) tc::teardown(tst.ar);
+}
+
+namespace {
+
+auto domain_kern(int precision) {
+    return precision == 0   ? domain_kernel<double, false>
+           : precision == 3 ? domain_kernel<double, true>
+           : precision == 2 ? domain_kernel<df32, true>
+                            : domain_kernel<df32, false>;
+}
+
+}  // namespace
+
+cudaError_t configure_domains(int precision, int Kmax) {
+    return set_smem(domain_kern(precision), rec_smem(precision, Kmax));
+}
+
+cudaError_t launch_domains(int precision, const ChainDev* chains, const int* order, int nchains,
+                           int Kmax, double eta_device, const void* leadout,
+                           const int* lead_status, const LeadDev* leads, void* ws, int ndom,
+                           cudaStream_t st) {
+    if (nchains <= 0) return cudaSuccess;
+    cudaError_t e = configure_domains(precision, Kmax);
+    if (e != cudaSuccess) return e;
+    const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
+                                  leads, ws, nullptr, nullptr, ndom);
+    domain_kern(precision)<<<nchains * ndom, NT, rec_smem(precision, Kmax), st>>>(
+        a, launch_panel(precision, Kmax));
+    return cudaGetLastError();
+}
+
+}  // namespace rgf

@@ -129,7 +129,27 @@ struct SweepArgs {
     void* ws;
     double* T;
     int32_t* status;
+    int ndom;        // domains per chain (2: the two halves)
 };
+
+// The buffers of interior domain d (1 .. ndom-2) of a chain (ld KL): for its
+// columns a .. b, the left-connected recursion of the isolated domain leaves
+// G = g_b, P = G_ab (rows: column a) and A = G_aa.
+template <class R>
+struct Inner {
+    cx<R>* X;
+    cx<R>* G;
+    cx<R>* P;
+    cx<R>* A;
+    int* flag;
+};
+template <class R>
+__device__ inline Inner<R> inner_of(void* ws, const ChainDev& ch, int d) {
+    const size_t B = (size_t)col_KL(ch.N) * col_KL(ch.N);
+    cx<R>* base = reinterpret_cast<cx<R>*>(ws) + ch.ws_off + sweep_ws_elems(ch.N) +
+                  (size_t)(d - 1) * interior_ws_elems(ch.N);
+    return Inner<R>{base, base + B, base + 2 * B, base + 3 * B, reinterpret_cast<int*>(base + 4 * B)};
+}
 
 // The lead-attached first column of half h of chain ci, in binary64: h = 0 the
 // left lead's column 0 (KL even-row left atoms), h = 1 the right lead's column
@@ -243,6 +263,235 @@ __device__ __forceinline__ void half_body(const SweepArgs& a, int ci, int h, int
     __syncthreads();
 }
 
+// Domain d of chain ci when the chain has ndom > 2 domains, in one body for
+// the three kinds (one inlined copy each of the inverse and the strip
+// product):
+//   d = 0, ndom-1: the lead-attached halves, as half_body (their end columns
+//     prepared by prep_body), the left one ending before the first interior
+//     domain, the right one starting at the last;
+//   interior d: columns a = dom_bound(d) .. b = dom_bound(d + 1) - 1 as an
+//     isolated system, recursed left to right.  It starts with its first two
+//     columns, t I-bonded row by row: each row is a dimer [[d1, -t], [-t, d2]]
+//     (d = z - eps), so A = G_aa = diag(d2 / D), P = G_a,a+1 = diag(t / D) and
+//     G = g_a+1 = diag(d1 / D) with D = d1 d2 - t^2 (a removed atom leaves its
+//     partner alone: 1 / d).  Column a also carries an absorbing self-energy
+//     -i |t| on its kept atoms (d1 = z - eps + i |t|), which the join takes
+//     back out exactly: an isolated segment has a discrete spectrum, and an
+//     energy next to one of its levels would make its blocks, and the joins,
+//     ill-conditioned; open at one end, like the halves, it is not.  Starting
+//     from the dimers also keeps an atom near resonance (|z - eps| small) from
+//     entering as an isolated 1 / (z - eps).  Each step then adds column k (or
+//     a pair k, kb) to the partial system a .. k-1 by the Dyson equation:
+//         g_k = (A_k - W_k^T g_{k-1} W_k)^-1                       (inv_column)
+//         Y = P W_k,  P <- Y g_k,  A <- A + Y g_k Y^T = A + P Y^T  (G_aa, G_ab)
+//     On return G = g_b, P = G_ab and A = G_aa of the isolated domain; the
+//     joins in merge_body use them.
+// A pair takes Z, the inverse of its shifted first column (the pair's own
+// block at k): the strip forms (Y Z), the interior adds (Y Z) Y^T to A, and
+// then P = (Y Z) diag(s) and g_kb = diag(1/d) + diag(s) Z diag(s)
+// (pair_scales, pair_finish).  Every thread; ends with a barrier.
+template <class R, bool TC>
+__device__ __forceinline__ void domain_body(const SweepArgs& a, int ci, int d, int bm,
+                                            tc::State* tst) {
+    SweepSmem<R> s = carve<R>(rgf_dyn_smem, a.Kmax, TC, bm);
+    const ChainDev& ch = a.chains[ci];
+    const bool right = d == a.ndom - 1, inner = d > 0 && !right;
+    const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, right ? 1 : 0);
+    const int KL = c.KL;
+    cx<R> *X, *G, *P, *A = nullptr;
+    int* fl;
+    int k0, k1, rows;                   // columns k0 .. k1-1 (right half: k1-1 down to k0)
+    if (inner) {
+        const Inner<R> iw = inner_of<R>(a.ws, ch, d);
+        X = iw.X; G = iw.G; P = iw.P; A = iw.A; fl = iw.flag;
+        k0 = dom_bound(c.ncol, d, a.ndom);
+        k1 = dom_bound(c.ncol, d + 1, a.ndom);
+        rows = col_size(c, k0);
+    } else {
+        const Half<R> hw = half_of<R>(a.ws, ch, right ? 1 : 0);
+        X = hw.X; G = hw.G; P = hw.P; fl = hw.flag;
+        k0 = right ? dom_bound(c.ncol, a.ndom - 1, a.ndom) : 0;
+        k1 = right ? c.ncol : dom_bound(c.ncol, 1, a.ndom);
+        rows = right ? c.KR : c.KL;
+    }
+    if (ch.panel > 0 && ch.panel < bm) s.gj.bmax = ch.panel;
+    const bool pairs_on = ch.pairs != 0;
+    if constexpr (TC) {
+        s.gj.tcs = tst;
+        s.tcs = tst;
+    }
+    if (inner) {
+        // the dimers of columns k0, k0 + 1 (binary64; same row, same size)
+        const int K0 = rows;
+        load_col(c, k0, s.kc, s.eps);
+        load_col(c, k0 + 1, s.kn, nullptr);
+        __syncthreads();
+        for (int e = threadIdx.x; e < K0 * K0; e += NT) {
+            const int i = e / K0, l = e - i * K0;
+            zd ga = {0.0, 0.0}, gab = {0.0, 0.0}, gb = {0.0, 0.0};
+            if (i == l) {
+                const zd d1 = {c.z.re - s.eps[i], c.z.im + fabs(c.t)};
+                const zd d2 = {c.z.re - site_eps(c, k0 + 1, i), c.z.im};
+                const bool k1a = s.kc[i], k2a = s.kn[i];
+                if (k1a && k2a) {
+                    const zd det = csub(cmul(d1, d2), zd{c.t2, 0.0});
+                    const zd r = crecip(det);
+                    ga = cmul(d2, r);
+                    gab = cscale(r, c.t);
+                    gb = cmul(d1, r);
+                } else {
+                    ga = k1a ? crecip(d1) : zd{1.0, 0.0};
+                    gb = k2a ? crecip(d2) : zd{1.0, 0.0};
+                }
+            }
+            A[(size_t)i * KL + l] = from_z<R>(ga.re, ga.im);
+            P[(size_t)i * KL + l] = from_z<R>(gab.re, gab.im);
+            G[(size_t)i * KL + l] = from_z<R>(gb.re, gb.im);
+        }
+        __syncthreads();
+    }
+    const int steps = k1 - k0;
+    int flag = 0;
+    for (int j = inner ? 2 : 1; j < steps;) {
+        const int k = right ? k1 - 1 - j : k0 + j;
+        const int kb = right ? k - 1 : k + 1;
+        const bool pairable = pairs_on && j + 1 < steps && (right ? (k & 1) == 1 : (k & 1) == 0);
+        load_col(c, k, s.kc, s.eps);
+        load_col(c, prev_col(c, k), s.kp, nullptr);
+        if (pairable) load_col(c, kb, s.kn, nullptr);
+        __syncthreads();
+        const bool pair = pairable && pair_ok<R>(c, kb, s);
+        const int K = col_size(c, k);
+        flag |= inv_column<R, TC>(c, k, G, G, X, s, pair ? kb : -1);
+        strip_column<R, TC>(c, k, G, P, P, X, s, rows);          // Y = P W into X, P <- Y G
+        if (inner) acc_product<R, TC>(rows, K, P, X, A, KL, s);  // A += P Y^T
+        if (pair) {
+            pair_scales<R>(c, k, kb, G, s);                      // G = Z diag(s)
+            const cx<R>* sc = s.gj.mult;
+            for (int e = threadIdx.x; e < rows * K; e += NT) {
+                const int i = e / K, l = e - i * K;
+                P[(size_t)i * KL + l] = cmul(P[(size_t)i * KL + l], sc[l]);
+            }
+            __syncthreads();
+            pair_finish<R>(c, k, G, s);
+        }
+        j += pair ? 2 : 1;
+    }
+    if constexpr (TC) {
+        if (*(volatile int*)tst->ar.err()) flag |= 4;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (inner) *fl = flag;
+        else *fl |= flag;
+    }
+    __syncthreads();
+}
+
+// The interior domains joined, left to right, onto the left half in binary64.
+// Joining domain d (columns ka .. kb, blocks A = G_aa, B = G_ab, D = g_b of the
+// domain with its absorbing self-energy -i|t| at ka) to the system from the
+// left lead up to column q = ka - 1 (E = its g at q, C = its corner block from
+// the left lead's modes to q): the left part acts on column ka as W^T E W in
+// place of the absorbing term, so with Sigma = W^T E W + i|t| (Dyson, Eq. 3)
+//     G'_ab = (I - A Sigma)^-1 B = Y,     g'_b = D + B^T Sigma Y,
+//     C'    = (C W) Y                     (G of the grown system from the lead
+//                                          to kb; G_ba = B^T by symmetry).
+// On return L.G = g'_b and L.P = C' of the last interior domain, in the working
+// precision; L.X and the interior domains' buffers are scratch.  Returns the
+// OR of the interior domains' flags and the joins' Gauss-Jordan flags.
+template <class R>
+__device__ int join_interiors(const SweepArgs& a, const ChainDev& ch, const ChainCtx& c,
+                              SweepSmem<double>& s, const Half<R>& L) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int KL = c.KL;
+    const double t = c.t, t2 = c.t2;
+    zd* E = reinterpret_cast<zd*>(L.G);
+    zd* C = reinterpret_cast<zd*>(L.P);
+    zd* LX = reinterpret_cast<zd*>(L.X);
+    int q = dom_bound(c.ncol, 1, a.ndom) - 1;
+    int flag = 0;
+    to_binary64<R>(L.G, col_size(c, q), col_size(c, q), KL);
+    to_binary64<R>(L.P, KL, col_size(c, q), KL);
+    for (int d = 1; d + 1 < a.ndom; ++d) {
+        const Inner<R> I = inner_of<R>(a.ws, ch, d);
+        const int ka = dom_bound(c.ncol, d, a.ndom), kb = dom_bound(c.ncol, d + 1, a.ndom) - 1;
+        const int Ka = col_size(c, ka), Kb = col_size(c, kb), Kq = col_size(c, q), ct = ka & 3;
+        flag |= *I.flag;
+        to_binary64<R>(I.A, Ka, Ka, KL);
+        to_binary64<R>(I.P, Ka, Kb, KL);
+        to_binary64<R>(I.G, Kb, Kb, KL);
+        zd* A = reinterpret_cast<zd*>(I.A);
+        zd* B = reinterpret_cast<zd*>(I.P);
+        zd* D = reinterpret_cast<zd*>(I.G);
+        zd* IX = reinterpret_cast<zd*>(I.X);
+        load_col(c, ka, s.kc, nullptr);
+        load_col(c, q, s.kp, nullptr);
+        __syncthreads();
+        // Sigma = t^2 S^T E S on column ka (kept atoms only) into LX
+        for (int i = warp; i < Ka; i += NWARP) {
+            int a0, a1;
+            col_src(ct, i, Kq, a0, a1);
+            const bool ki = s.kc[i];
+            const bool ka0 = a0 >= 0 && s.kp[a0], ka1 = a1 >= 0 && s.kp[a1];
+            for (int l = lane; l < Ka; l += 32) {
+                zd v = {0.0, 0.0};
+                if (ki && s.kc[l]) {
+                    int b0, b1;
+                    col_src(ct, l, Kq, b0, b1);
+                    const bool kb0 = b0 >= 0 && s.kp[b0], kb1 = b1 >= 0 && s.kp[b1];
+                    if (ka0 && kb0) v = cadd(v, E[(size_t)a0 * KL + b0]);
+                    if (ka0 && kb1) v = cadd(v, E[(size_t)a0 * KL + b1]);
+                    if (ka1 && kb0) v = cadd(v, E[(size_t)a1 * KL + b0]);
+                    if (ka1 && kb1) v = cadd(v, E[(size_t)a1 * KL + b1]);
+                    v = cscale(v, t2);
+                }
+                if (i == l && ki) v.im += fabs(t);      // the absorbing term taken out
+                LX[(size_t)i * KL + l] = v;
+            }
+        }
+        __syncthreads();
+        // X = I - A Sigma into IX; B^T Sigma into A (A read for the last time)
+        cta_gemm<double, false, false>(Ka, Ka, Ka, A, KL, LX, KL, IX, KL, GEMM_SET, s.gemm);
+        for (int e = threadIdx.x; e < Ka * Ka; e += NT) {
+            const int i = e / Ka, l = e % Ka;
+            zd& x = IX[(size_t)i * KL + l];
+            x = {((i == l) ? 1.0 : 0.0) - x.re, -x.im};
+        }
+        __syncthreads();
+        cta_gemm<double, true, false>(Kb, Ka, Ka, B, KL, LX, KL, A, KL, GEMM_SET, s.gemm);
+        // X^-1 into LX, Y = X^-1 B into IX
+        const double amax2 = max_abs2(IX, Ka, KL, s.red);
+        flag |= cta_gj_invert<double>(IX, Ka, KL, LX, KL, s.gj, amax2);
+        cta_gemm<double, false, false>(Ka, Kb, Ka, LX, KL, B, KL, IX, KL, GEMM_SET, s.gemm);
+        // g'_b = D + (B^T Sigma) Y into E
+        cta_gemm<double, false, false>(Kb, Kb, Ka, A, KL, IX, KL, E, KL, GEMM_SET, s.gemm);
+        for (int e = threadIdx.x; e < Kb * Kb; e += NT) {
+            const int i = e / Kb, l = e % Kb;
+            E[(size_t)i * KL + l] = cadd(E[(size_t)i * KL + l], D[(size_t)i * KL + l]);
+        }
+        // C W (KL x Ka) into LX, then C' = (C W) Y into C
+        for (int r = warp; r < KL; r += NWARP)
+            for (int l = lane; l < Ka; l += 32) {
+                zd v = {0.0, 0.0};
+                if (s.kc[l]) {
+                    int a0, a1;
+                    col_src(ct, l, Kq, a0, a1);
+                    if (a0 >= 0 && s.kp[a0]) v = cadd(v, C[(size_t)r * KL + a0]);
+                    if (a1 >= 0 && s.kp[a1]) v = cadd(v, C[(size_t)r * KL + a1]);
+                    v = cscale(v, t);
+                }
+                LX[(size_t)r * KL + l] = v;
+            }
+        __syncthreads();
+        cta_gemm<double, false, false>(KL, Kb, Ka, LX, KL, IX, KL, C, KL, GEMM_SET, s.gemm);
+        q = kb;
+    }
+    to_working<R>(L.G, col_size(c, q), col_size(c, q), KL);
+    to_working<R>(L.P, KL, col_size(c, q), KL);
+    return flag;
+}
+
 // The Dyson step across the bond between columns m-1 and m of chain ci, in
 // binary64, and the trace; writes T and the status word.  Scratch: the two
 // halves' X and, once read, their G and P.  bm: the launch's panel width.
@@ -263,9 +512,14 @@ __device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
     }
     const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, 0);
     const Half<R> L = half_of<R>(a.ws, ch, 0), Rt = half_of<R>(a.ws, ch, 1);
-    const int KL = c.KL, KR = c.KR, m = left_cols(c.ncol);
-    const int K = col_size(c, m), Kp = col_size(c, m - 1), ct = m & 3;
     int flag = *L.flag | *Rt.flag;
+    int m = left_cols(c.ncol);
+    if (a.ndom > 2) {
+        flag |= join_interiors<R>(a, ch, c, s, L);
+        m = dom_bound(c.ncol, a.ndom - 1, a.ndom);
+    }
+    const int KL = c.KL, KR = c.KR;
+    const int K = col_size(c, m), Kp = col_size(c, m - 1), ct = m & 3;
     load_col(c, m, s.kc, nullptr);
     load_col(c, m - 1, s.kp, nullptr);
     __syncthreads();
@@ -371,9 +625,9 @@ size_t rec_smem(int precision, int Kmax) {
 
 SweepArgs make_args(const ChainDev* chains, const int* order, int nchains, int Kmax,
                     double eta_device, const void* leadout, const int* lead_status,
-                    const LeadDev* leads, void* ws, double* T, int32_t* status) {
+                    const LeadDev* leads, void* ws, double* T, int32_t* status, int ndom = 2) {
     return SweepArgs{chains, order, nchains, Kmax, eta_device, (const zd*)leadout, lead_status,
-                     leads, ws, T, status};
+                     leads, ws, T, status, ndom};
 }
 
 }  // namespace

@@ -71,6 +71,23 @@ __host__ __device__ inline size_t half_ws_elems(int N) {
     return 3 * KL * KL + 1;
 }
 __host__ __device__ inline size_t sweep_ws_elems(int N) { return 2 * half_ws_elems(N); }
+// With ndom > 2 domains per chain the ndom - 2 interior domains hold X, G, P
+// and A (each KL x KL) and a flag element each, after the two halves.
+__host__ __device__ inline size_t interior_ws_elems(int N) {
+    size_t KL = (size_t)col_KL(N);
+    return 4 * KL * KL + 1;
+}
+__host__ __device__ inline size_t chain_ws_elems(int N, int ndom) {
+    return sweep_ws_elems(N) + (size_t)(ndom > 2 ? ndom - 2 : 0) * interior_ws_elems(N);
+}
+// First column of domain d of ndom over ncol columns (domain d covers columns
+// dom_bound(d) .. dom_bound(d + 1) - 1; two domains split at ncol / 2).  The
+// inner boundaries are even columns (c0 or c2 of a cell), so that an interior
+// domain starts with a t I-bonded pair of columns; with ndom <= ncol / 2 every
+// domain keeps two columns or more.
+__host__ __device__ inline int dom_bound(int ncol, int d, int ndom) {
+    return d >= ndom ? ncol : (int)((((long long)ncol * d) / ndom) & ~1ll);
+}
 
 // Shared memory of the sweep / lead kernels for a largest column size Kmax
 // (tc: with the tensor-core area of the RGF_MIXED_TC path).
@@ -95,20 +112,29 @@ cudaError_t launch_lead(const LeadDev* leads, int nlead, int Kmax, double eta_le
 // The conductance of every chain in three launches on `st`:
 //   launch_prep:  the lead-attached end column of each half in binary64, in the
 //                 leads' transverse-mode basis (2 blocks per chain);
-//   launch_half:  the column recursion of each half (2 blocks per chain);
-//   launch_merge: the two halves joined across the middle bond, and the trace
-//                 (1 block per chain; writes T and status).
-// leadout / lead_status as launch_lead left them; ws: sweep_ws_elems per chain.
+//   launch_half:  the column recursion of each domain (ndom blocks per chain:
+//                 the two halves, and with ndom > 2 the interior domains);
+//   launch_merge: the domains joined across their boundary bonds, and the
+//                 trace (1 block per chain; writes T and status).
+// leadout / lead_status as launch_lead left them; ws: chain_ws_elems per chain.
 cudaError_t launch_prep(int precision, const ChainDev* chains, const int* order, int nchains,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
-                        const LeadDev* leads, void* ws, cudaStream_t st);
+                        const LeadDev* leads, void* ws, cudaStream_t st, int ndom = 2);
 cudaError_t launch_half(int precision, const ChainDev* chains, const int* order, int nchains,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
-                        const LeadDev* leads, void* ws, cudaStream_t st);
+                        const LeadDev* leads, void* ws, cudaStream_t st, int ndom = 2);
 cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order, int nchains,
                          int Kmax, double eta_device, const void* leadout, const int* lead_status,
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
-                         cudaStream_t st);
+                         cudaStream_t st, int ndom = 2);
+// The domain kernels of ndom > 2 (rgf_domains.cu): launch_domains runs every
+// domain of every chain (ndom blocks per chain); configure_domains sets their
+// shared-memory limits.
+cudaError_t launch_domains(int precision, const ChainDev* chains, const int* order, int nchains,
+                           int Kmax, double eta_device, const void* leadout,
+                           const int* lead_status, const LeadDev* leads, void* ws, int ndom,
+                           cudaStream_t st);
+cudaError_t configure_domains(int precision, int Kmax);
 
 // The same three steps as one persistent kernel (rgf_batch.cu): one block per
 // SM (at most 2 * nchains), each taking the next half from a work queue in the

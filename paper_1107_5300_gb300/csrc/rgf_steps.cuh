@@ -373,10 +373,10 @@ __device__ int inv_column(const ChainCtx& c, int k, const cx<R>* Gprev, cx<R>* G
 
 template <class R, bool TC64 = false>
 __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx<R>* Pprev,
-                             cx<R>* Pout, cx<R>* Y, SweepSmem<R>& s) {
+                             cx<R>* Pout, cx<R>* Y, SweepSmem<R>& s, int nrows = -1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int KL = c.KL, K = col_size(c, k), Kq = col_size(c, prev_col(c, k));
-    const int rows = c.dir ? c.KR : c.KL;
+    const int rows = nrows >= 0 ? nrows : (c.dir ? c.KR : c.KL);
     for (int r = warp; r < rows; r += NWARP)
         for (int l = lane; l < K; l += 32) {
             cx<R> v = czero<R>();
@@ -408,6 +408,78 @@ __device__ void strip_column(const ChainCtx& c, int k, const cx<R>* Gk, const cx
         }
     }
     cta_gemm<R, false, false>(rows, K, K, Y, KL, Gk, KL, Pout, KL, GEMM_SET, s.gemm);
+}
+
+// C += A B^T (C: m x m, A and B: m x kd, leading dimension ld; C must not
+// overlap A or B): the update of an interior domain's first-column block,
+// G_aa += P_k Y^T.  On the tensor cores when the block holds them.
+struct AccOp {
+    const zf* A;
+    const zf* B;
+    zf* C;
+    int ld, r0;
+    using Old = float4;
+    __device__ bool colA() const { return false; }
+    __device__ zf a(int m, int k) const { return A[(size_t)(r0 + m) * ld + k]; }
+    __device__ zf b(int k, int n) const { return B[(size_t)n * ld + k]; }
+    __device__ float4 load(int m, int n, bool) const {
+        return *reinterpret_cast<const float4*>(C + (size_t)(r0 + m) * ld + n);
+    }
+    __device__ void store(int m, int n, float4 x, df32 re, df32 im, bool) const {
+        const df32 r = df_add(df32{x.x, x.y}, re), q = df_add(df32{x.z, x.w}, im);
+        *reinterpret_cast<float4*>(C + (size_t)(r0 + m) * ld + n) = make_float4(r.hi, r.lo, q.hi, q.lo);
+    }
+};
+struct AccOp64 {
+    static constexpr bool kF64 = true;
+    const zd* A;
+    const zd* B;
+    zd* C;
+    int ld, r0;
+    using Old = zd;
+    __device__ bool colA() const { return false; }
+    __device__ zd a(int m, int k) const { return A[(size_t)(r0 + m) * ld + k]; }
+    __device__ zd b(int k, int n) const { return B[(size_t)n * ld + k]; }
+    __device__ zd load(int m, int n, bool) const { return C[(size_t)(r0 + m) * ld + n]; }
+    __device__ void store(int m, int n, zd x, double re, double im, bool) const {
+        C[(size_t)(r0 + m) * ld + n] = zd{x.re + re, x.im + im};
+    }
+};
+
+// Out-of-line copies (one each), so that the interior recursion carries no
+// third inlined tensor-core product beside the inverse's and the strip's.
+static __device__ __noinline__ uint32_t tc_acc(int m, int kd, const zf* A, const zf* B, zf* C, int ld,
+                                               tc::Area ar, uint32_t phase) {
+    for (int r0 = 0; r0 < m; r0 += 128) {
+        const AccOp op{A, B, C, ld, r0};
+        phase = tc::zgemm(op, min(128, m - r0), m, kd, ar, phase);
+    }
+    return phase;
+}
+static __device__ __noinline__ uint32_t tc_acc64(int m, int kd, const zd* A, const zd* B, zd* C,
+                                                 int ld, tc::Area ar, uint32_t phase) {
+    for (int r0 = 0; r0 < m; r0 += 128) {
+        const AccOp64 op{A, B, C, ld, r0};
+        phase = tc::zgemm(op, min(128, m - r0), m, kd, ar, phase);
+    }
+    return phase;
+}
+
+template <class R, bool TC64 = false>
+__device__ void acc_product(int m, int kd, const cx<R>* A, const cx<R>* B, cx<R>* C, int ld,
+                            SweepSmem<R>& s) {
+    if constexpr (std::is_same<R, df32>::value) {
+        if (s.tcs) {
+            s.tcs->phase = tc_acc(m, kd, A, B, C, ld, s.tcs->ar, s.tcs->phase);
+            return;
+        }
+    } else if constexpr (std::is_same<R, double>::value && TC64) {
+        if (s.tcs) {
+            s.tcs->phase = tc_acc64(m, kd, A, B, C, ld, s.tcs->ar, s.tcs->phase);
+            return;
+        }
+    }
+    cta_gemm<R, false, true>(m, m, kd, A, ld, B, ld, C, ld, GEMM_ADD, s.gemm);
 }
 
 // Two columns a, b = the next one in the recursion, joined by t I between the

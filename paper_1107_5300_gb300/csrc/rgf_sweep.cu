@@ -56,17 +56,18 @@ cudaError_t configure_phased(int precision, int Kmax) {
 
 cudaError_t configure_sweep(int precision, int Kmax) {
     cudaError_t e = configure_phased(precision, Kmax);
-    return e == cudaSuccess ? configure_batch(precision, Kmax) : e;
+    if (e == cudaSuccess) e = configure_batch(precision, Kmax);
+    return e == cudaSuccess ? configure_domains(precision, Kmax) : e;
 }
 
 cudaError_t launch_prep(int precision, const ChainDev* chains, const int* order, int nchains,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
-                        const LeadDev* leads, void* ws, cudaStream_t st) {
+                        const LeadDev* leads, void* ws, cudaStream_t st, int ndom) {
     if (nchains <= 0) return cudaSuccess;
     cudaError_t e = configure_phased(precision, Kmax);
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
-                                  leads, ws, nullptr, nullptr);
+                                  leads, ws, nullptr, nullptr, ndom);
     auto kern = binary64(precision) ? prep_kernel<double> : prep_kernel<df32>;
     kern<<<2 * nchains, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
     return cudaGetLastError();
@@ -74,8 +75,11 @@ cudaError_t launch_prep(int precision, const ChainDev* chains, const int* order,
 
 cudaError_t launch_half(int precision, const ChainDev* chains, const int* order, int nchains,
                         int Kmax, double eta_device, const void* leadout, const int* lead_status,
-                        const LeadDev* leads, void* ws, cudaStream_t st) {
+                        const LeadDev* leads, void* ws, cudaStream_t st, int ndom) {
     if (nchains <= 0) return cudaSuccess;
+    if (ndom > 2)
+        return launch_domains(precision, chains, order, nchains, Kmax, eta_device, leadout,
+                              lead_status, leads, ws, ndom, st);
     cudaError_t e = configure_phased(precision, Kmax);
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
@@ -91,12 +95,12 @@ cudaError_t launch_half(int precision, const ChainDev* chains, const int* order,
 cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order, int nchains,
                          int Kmax, double eta_device, const void* leadout, const int* lead_status,
                          const LeadDev* leads, void* ws, double* T, int32_t* status,
-                         cudaStream_t st) {
+                         cudaStream_t st, int ndom) {
     if (nchains <= 0) return cudaSuccess;
     cudaError_t e = configure_phased(precision, Kmax);
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
-                                  leads, ws, T, status);
+                                  leads, ws, T, status, ndom);
     auto kern = binary64(precision) ? merge_kernel<double> : merge_kernel<df32>;
     kern<<<nchains, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
     return cudaGetLastError();

@@ -31,7 +31,8 @@ EXPORTS = ["rgf_generate_onsite", "rgf_build_ribbon", "rgf_build_ribbon_dev", "r
            "rgf_profile_read_phases", "rgf_set_lead_controls", "rgf_status_str", "rgf_last_error",
            "rgf_version", "rgf_set_schedule", "rgf_get_schedule", "rgf_batch_create",
            "rgf_batch_launch", "rgf_batch_free", "rgf_set_tuning", "rgf_get_tuning",
-           "rgf_tune_lookup", "rgf_autotune"]
+           "rgf_tune_lookup", "rgf_autotune", "rgf_set_domains", "rgf_get_domains",
+           "rgf_auto_domains"]
 RGF_SCHED_PERSISTENT, RGF_SCHED_PHASED = 0, 1
 RGF_ENGINE_PIPES, RGF_ENGINE_TENSOR = 0, 1
 RGF_TUNE_MAX_ENTRIES, RGF_TUNE_MAX_CANDIDATES = 64, 12
@@ -109,6 +110,12 @@ lib.rgf_tune_lookup.argtypes = [C.c_int, C.c_int, C.POINTER(TuneEntry)]
 lib.rgf_tune_lookup.restype = C.c_int
 lib.rgf_autotune.argtypes = [C.c_int, _ip, C.c_int, C.c_int, C.c_int, C.POINTER(TuneEntry), _dp, _ip]
 lib.rgf_autotune.restype = C.c_int
+lib.rgf_set_domains.argtypes = [C.c_int]
+lib.rgf_set_domains.restype = C.c_int
+lib.rgf_get_domains.argtypes = []
+lib.rgf_get_domains.restype = C.c_int
+lib.rgf_auto_domains.argtypes = [C.c_int, C.c_int, C.c_int]
+lib.rgf_auto_domains.restype = C.c_int
 lib.rgf_status_str.restype = C.c_char_p
 lib.rgf_status_str.argtypes = [C.c_int]
 lib.rgf_last_error.restype = C.c_char_p
@@ -440,3 +447,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def set_domains(ndom):
+    """Domains per chain of the forward sweep (default 2; 0 = automatic; process-wide)."""
+    _check(lib.rgf_set_domains(int(ndom)))
+
+
+def get_domains():
+    return int(lib.rgf_get_domains())
+
+
+def auto_domains(nchains, ncol_min, nsm):
+    """The automatic domain count for nchains chains, the shortest of ncol_min columns, nsm SMs."""
+    return int(lib.rgf_auto_domains(int(nchains), int(ncol_min), int(nsm)))

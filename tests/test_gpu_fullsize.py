@@ -94,3 +94,28 @@ def test_mixed_paths_match_binary64_at_full_size(rgflib, full_ribbon, bench_fp64
     assert d.max() <= (5e-9 if prec == 3 else 1e-6), d.max()
     nch = np.array([bands.channels_closed_form(W["N"], e) for e in Es])
     assert np.all(T64 >= -1e-9) and np.all(T64 <= nch + 1e-9)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [0, 2])
+def test_full_size_many_domains_vs_oracle(rgflib, full_ribbon, prec):
+    # the six golden chains with the automatic domain count (25 domains each:
+    # 152 SMs over 6 chains, at most sqrt(16000 / 16)); near E = 0 the joins'
+    # rounding adds up (measured 1.9e-9 in binary64 at 5 meV, against 1e-10
+    # with two domains), away from it the two-domain bounds hold
+    g, e0 = GOLD["L4000"], GOLD["L4000_E0"]
+    Es = np.array(g["E"] + [e0["E"]])
+    ref = np.array(g["T"] + [e0["T"]])
+    assert rgflib.auto_domains(len(Es), 4 * W["L"], 152) == 25
+    rgflib.set_domains(0)
+    try:
+        T, st = rgflib.conductance([full_ribbon] * len(Es), Es, 1e-8, 1e-8, prec, check=False)
+    finally:
+        rgflib.set_domains(2)
+    assert (st == 0).all(), st
+    d = np.abs(T - ref)
+    print(f"L4000 many domains precision={prec}: |dT| = {np.array2string(d, precision=3)}")
+    far = np.abs(Es) >= 0.1
+    assert d[far].max() < TOL[(prec, 4000)], d
+    assert d[~far][:-1].max() < (5e-9 if prec == 0 else 1e-6), d
+    assert d[-1] < TOL_E0, d

@@ -7,6 +7,7 @@ import pytest
 def lib(rgflib):
     yield rgflib
     rgflib.set_schedule(rgflib.RGF_SCHED_PHASED)
+    rgflib.set_domains(2)
     for p in (rgflib.RGF_FP64, rgflib.RGF_MIXED, rgflib.RGF_MIXED_TC):
         rgflib.set_tuning(p, [])
 
@@ -85,3 +86,26 @@ def test_autotune_argument_checks(lib):
         lib.autotune(lib.RGF_MIXED_TC, [1], cells=2)
     with pytest.raises(lib.RGFError):
         lib.autotune(lib.RGF_MIXED_TC, [11], cells=0)
+
+
+def test_automatic_domain_count(lib):
+    # one SM per domain for every chain, at most sqrt(ncol / 16), at least 2,
+    # at most ncol / 2
+    assert lib.auto_domains(69, 16000, 152) == 2        # the bench batch: two halves
+    assert lib.auto_domains(1, 16000, 152) == 31        # one long chain
+    assert lib.auto_domains(10, 16000, 152) == 15
+    assert lib.auto_domains(1, 16, 152) == 2
+    assert lib.auto_domains(1, 4, 152) == 2
+    assert lib.auto_domains(2048, 400, 152) == 2
+
+
+def test_domain_setting(lib):
+    assert lib.get_domains() == 2
+    lib.set_domains(7)
+    assert lib.get_domains() == 7
+    for bad in (1, -2, 5000):
+        with pytest.raises(lib.RGFError):
+            lib.set_domains(bad)
+    assert lib.get_domains() == 7
+    lib.set_domains(0)
+    assert lib.get_domains() == 0
