@@ -209,29 +209,29 @@ int rgf_get_schedule(void);
  * Domains per chain (no counterpart in the paper; process-wide; default 2,
  * 0 = automatic).  A chain's columns are cut into ndom domains that run at the
  * same time, one SM each: the two lead-attached halves at the ends and ndom - 2
- * interior domains, each recursed as an isolated system that keeps the blocks
- * of its first and last columns (G_aa, G_ab, g_b).  The merge then joins the
- * interior domains onto the left half one after the other, by the Dyson
- * equation across each boundary bond (binary64), and the right half last.
- * This is the modified recursion that running one chain in parallel needs: it
- * shortens a chain's sequential depth ndom / 2 times, at one more product per
- * interior column step and one join (an inverse and four products) per
- * interior domain.
+ * interior domains between them, each recursed as a segment open at its first
+ * column (an absorbing self-energy there, taken back out when it is joined)
+ * that keeps the blocks of its first and last columns (G_aa, G_ab, g_b).  A
+ * tree of joins (the Dyson equation across each boundary bond, binary64)
+ * combines the interior domains in ceil(log2(ndom - 2)) launches; the merge
+ * then joins the left half, the combined interior and the right half.  This
+ * is the modified recursion that running one chain in parallel needs: it
+ * shortens a chain's sequential depth about ndom / 2 times, at one more
+ * product per interior column step.
  * Automatic: as many domains as give every chain of the call one SM per domain
  * (2 while there are more than SMs / 2 chains, the bench batches), at most
- * sqrt(ncol / 16) (ncol = 4 L of the shortest chain), which balances the
- * shortened recursion against the joins; rgf_auto_domains returns that choice
- * for nchains chains, a shortest chain of ncol_min columns and nsm SMs (plain
- * host call).  Forced values (>= 2) are capped at ncol / 2.  With more than
- * two domains the sweep runs the three-launch schedule.  Accuracy: each join
- * forms the Green's function of the grown system at a free cut, which near
+ * ncol / 32 (ncol = 4 L of the shortest chain); rgf_auto_domains returns that
+ * choice for nchains chains, a shortest chain of ncol_min columns and nsm SMs
+ * (plain host call).  Forced values (>= 2) are capped at ncol / 2.  With more
+ * than two domains the sweep runs the three-launch schedule.  Accuracy: each
+ * join forms the Green's function of a grown segment at a free cut, which near
  * E = 0 is as ill-conditioned as the middle cut of the two halves, so the
  * rounding of the joins adds up: at L = 4000 (bench ribbon, 25 domains,
  * binary64) T stays within 3e-12 of 40-digit-pinned values away from E = 0
  * but moves to 2e-9 at |E| <= 5 meV (1e-10 with two domains); hence the
- * default of two.  The gradient and LDOS
- * sweeps and rgf_conductance_noalloc always use the two halves.  Errors:
- * RGF_EINVAL (ndom not 0 and outside [2, 4096]).
+ * default of two.  The gradient and LDOS sweeps and rgf_conductance_noalloc
+ * always use the two halves.  Errors: RGF_EINVAL (ndom not 0 and outside
+ * [2, 4096]).
  */
 rgf_status rgf_set_domains(int ndom);
 int rgf_get_domains(void);

@@ -129,18 +129,17 @@ int g_domains = 2;                       // domains per chain; 0 = automatic
 thread_local int g_force_domains = 0;
 
 // Domains per chain for a call (forward sweep): forced (>= 2), else as many as
-// leave every chain one SM per domain, but at most sqrt(ncol / 16): the joins
-// run one after the other, about sixteen column steps each, so that many
-// domains balance the shortened recursion against the joins.  At most ncol/2
-// (every domain two columns or more).
+// leave every chain one SM per domain, but at most ncol / 32: the joins run as
+// a tree, log2 of the interior domains deep, each level a few tens of column
+// steps' worth, so domains of 32 columns or more keep them a minor part.  At
+// most ncol / 2 (every domain two columns or more).
 int domains_for(int requested, int nchains, int ncol_min, int nsm) {
     int d;
     if (requested >= 2) {
         d = requested;
     } else {
         const int per = nchains > 0 ? nsm / nchains : 2;
-        const int cap = (int)std::floor(std::sqrt((double)ncol_min / 16.0));
-        d = std::max(2, std::min(per, cap));
+        d = std::max(2, std::min(per, ncol_min / 32));
     }
     return std::max(2, std::min(d, ncol_min / 2));
 }

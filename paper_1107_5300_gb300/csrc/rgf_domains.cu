@@ -20,6 +20,15 @@ __global__ void __launch_bounds__(NT, 1) domain_kernel(SweepArgs a, int bm) {
     if constexpr (TC) tc::teardown(tst.ar);
 }
 
+// Level `level` of the tree of joins of the interior domains: block b runs
+// join b % njoin of chain order[b / njoin].
+template <class R>
+__global__ void __launch_bounds__(NT, 1) tree_kernel(SweepArgs a, int bm, int level, int njoin) {
+    const int ci = a.order[blockIdx.x / njoin], j = blockIdx.x % njoin;
+    if (lead_state(a.lead_status, a.chains[ci].lead) != ST_OK) return;
+    tree_join_body<R>(a, ci, level, j, bm);
+}
+
 namespace {
 
 auto domain_kern(int precision) {
@@ -32,7 +41,30 @@ auto domain_kern(int precision) {
 }  // namespace
 
 cudaError_t configure_domains(int precision, int Kmax) {
-    return set_smem(domain_kern(precision), rec_smem(precision, Kmax));
+    cudaError_t e = set_smem(domain_kern(precision), rec_smem(precision, Kmax));
+    if (e != cudaSuccess) return e;
+    return set_smem(binary64(precision) ? tree_kernel<double> : tree_kernel<df32>,
+                    f64_smem(precision, Kmax));
+}
+
+cudaError_t launch_tree(int precision, const ChainDev* chains, const int* order, int nchains,
+                        int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                        const LeadDev* leads, void* ws, int ndom, cudaStream_t st) {
+    const int M = ndom - 2;
+    if (nchains <= 0 || M < 2) return cudaSuccess;
+    cudaError_t e = configure_domains(precision, Kmax);
+    if (e != cudaSuccess) return e;
+    const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
+                                  leads, ws, nullptr, nullptr, ndom);
+    auto kern = binary64(precision) ? tree_kernel<double> : tree_kernel<df32>;
+    for (int level = 0; (1 << level) < M; ++level) {
+        const int njoin = (M + (2 << level) - 1) / (2 << level);
+        kern<<<nchains * njoin, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax),
+                                                                     level, njoin);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_domains(int precision, const ChainDev* chains, const int* order, int nchains,

@@ -388,6 +388,138 @@ __device__ __forceinline__ void domain_body(const SweepArgs& a, int ci, int d, i
     __syncthreads();
 }
 
+// One join of the tree that combines the interior domains (ndom > 3):
+// at level l, join j combines node d1 = 1 + j 2^(l+1) (its domains d1 ..
+// d1 + 2^l - 1) with node d2 = d1 + 2^l (domains d2 .. min(d2 + 2^l, ndom-1)
+// - 1), both interior segments open only at their first column (the
+// absorbing term -i|t|).  With a1 .. b1 and a2 .. b2 their columns, blocks
+// A = G_aa, B = G_ab, D = g_b, and Sigma = W^T D1 W + i|t| on column a2 (the
+// coupling from node 1 in place of node 2's absorbing term), the Dyson
+// equation across the bond b1 -> a2 gives the combined segment a1 .. b2:
+//     Y = (I - A2 Sigma)^-1 B2,             G'_a2a2 = (I - A2 Sigma)^-1 A2,
+//     D' = D2 + B2^T Sigma Y,               B' = (B1 W) Y,
+//     A' = A1 + (B1 W) G'_a2a2 (B1 W)^T,
+// written into node d1's buffers in binary64 (level 0 converts its inputs
+// from the working precision).  One inverse and seven products; a block per
+// join, every join of a level at the same time.
+template <class R>
+__device__ __noinline__ void tree_join_body(const SweepArgs a, int ci, int level, int j, int bm) {
+    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, false, bm);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const ChainDev& ch = a.chains[ci];
+    const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, 0);
+    const int M = a.ndom - 2, w = 1 << level;
+    const int d1 = 1 + j * 2 * w, d2 = d1 + w;
+    const int KL = c.KL;
+    if (d2 > M) {
+        // an odd domain out at level 0 still goes over to binary64, as the
+        // levels above expect
+        if (level == 0 && d1 <= M) {
+            const Inner<R> I = inner_of<R>(a.ws, ch, d1);
+            const int ka = dom_bound(c.ncol, d1, a.ndom), kb = dom_bound(c.ncol, d1 + 1, a.ndom) - 1;
+            to_binary64<R>(I.A, col_size(c, ka), col_size(c, ka), KL);
+            to_binary64<R>(I.P, col_size(c, ka), col_size(c, kb), KL);
+            to_binary64<R>(I.G, col_size(c, kb), col_size(c, kb), KL);
+        }
+        return;
+    }
+    const double t = c.t, t2 = c.t2;
+    const int a1 = dom_bound(c.ncol, d1, a.ndom), b1 = dom_bound(c.ncol, d2, a.ndom) - 1;
+    const int a2 = dom_bound(c.ncol, d2, a.ndom);
+    const int b2 = dom_bound(c.ncol, min(d2 + w, a.ndom - 1), a.ndom) - 1;
+    const int K1 = col_size(c, a1), Kb1 = col_size(c, b1), K2 = col_size(c, a2), Kb2 = col_size(c, b2);
+    const Inner<R> I1 = inner_of<R>(a.ws, ch, d1), I2 = inner_of<R>(a.ws, ch, d2);
+    if (level == 0) {
+        to_binary64<R>(I1.A, K1, K1, KL);
+        to_binary64<R>(I1.P, K1, Kb1, KL);
+        to_binary64<R>(I1.G, Kb1, Kb1, KL);
+        to_binary64<R>(I2.A, K2, K2, KL);
+        to_binary64<R>(I2.P, K2, Kb2, KL);
+        to_binary64<R>(I2.G, Kb2, Kb2, KL);
+    }
+    zd* X1 = reinterpret_cast<zd*>(I1.X);
+    zd* A1 = reinterpret_cast<zd*>(I1.A);
+    zd* B1 = reinterpret_cast<zd*>(I1.P);
+    zd* D1 = reinterpret_cast<zd*>(I1.G);
+    zd* X2 = reinterpret_cast<zd*>(I2.X);
+    zd* A2 = reinterpret_cast<zd*>(I2.A);
+    zd* B2 = reinterpret_cast<zd*>(I2.P);
+    zd* D2 = reinterpret_cast<zd*>(I2.G);
+    int flag = *I1.flag | *I2.flag;
+    const int ct = a2 & 3;
+    load_col(c, a2, s.kc, nullptr);
+    load_col(c, b1, s.kp, nullptr);
+    __syncthreads();
+    // Sigma = t^2 S^T D1 S + i|t| on column a2 (kept atoms only) into X1
+    for (int i = warp; i < K2; i += NWARP) {
+        int p0, p1;
+        col_src(ct, i, Kb1, p0, p1);
+        const bool ki = s.kc[i];
+        const bool kp0 = p0 >= 0 && s.kp[p0], kp1 = p1 >= 0 && s.kp[p1];
+        for (int l = lane; l < K2; l += 32) {
+            zd v = {0.0, 0.0};
+            if (ki && s.kc[l]) {
+                int q0, q1;
+                col_src(ct, l, Kb1, q0, q1);
+                const bool kq0 = q0 >= 0 && s.kp[q0], kq1 = q1 >= 0 && s.kp[q1];
+                if (kp0 && kq0) v = cadd(v, D1[(size_t)p0 * KL + q0]);
+                if (kp0 && kq1) v = cadd(v, D1[(size_t)p0 * KL + q1]);
+                if (kp1 && kq0) v = cadd(v, D1[(size_t)p1 * KL + q0]);
+                if (kp1 && kq1) v = cadd(v, D1[(size_t)p1 * KL + q1]);
+                v = cscale(v, t2);
+                if (i == l) v.im += fabs(t);
+            }
+            X1[(size_t)i * KL + l] = v;
+        }
+    }
+    __syncthreads();
+    // X = I - A2 Sigma into X2; B2^T Sigma into D1 (D1 read for the last time)
+    cta_gemm<double, false, false>(K2, K2, K2, A2, KL, X1, KL, X2, KL, GEMM_SET, s.gemm);
+    for (int e = threadIdx.x; e < K2 * K2; e += NT) {
+        const int i = e / K2, l = e % K2;
+        zd& x = X2[(size_t)i * KL + l];
+        x = {((i == l) ? 1.0 : 0.0) - x.re, -x.im};
+    }
+    __syncthreads();
+    cta_gemm<double, true, false>(Kb2, K2, K2, B2, KL, X1, KL, D1, KL, GEMM_SET, s.gemm);
+    // X^-1 into X1; Y = X^-1 B2 into X2; G'_a2a2 = X^-1 A2 into B2
+    const double amax2 = max_abs2(X2, K2, KL, s.red);
+    flag |= cta_gj_invert<double>(X2, K2, KL, X1, KL, s.gj, amax2);
+    cta_gemm<double, false, false>(K2, Kb2, K2, X1, KL, B2, KL, X2, KL, GEMM_SET, s.gemm);
+    cta_gemm<double, false, false>(K2, K2, K2, X1, KL, A2, KL, B2, KL, GEMM_SET, s.gemm);
+    // D' = D2 + (B2^T Sigma) Y into A2, then into D1's place below
+    cta_gemm<double, false, false>(Kb2, Kb2, K2, D1, KL, X2, KL, A2, KL, GEMM_SET, s.gemm);
+    for (int e = threadIdx.x; e < Kb2 * Kb2; e += NT) {
+        const int i = e / Kb2, l = e % Kb2;
+        A2[(size_t)i * KL + l] = cadd(A2[(size_t)i * KL + l], D2[(size_t)i * KL + l]);
+    }
+    // B1 W (K1 x K2) into X1
+    for (int r = warp; r < K1; r += NWARP)
+        for (int l = lane; l < K2; l += 32) {
+            zd v = {0.0, 0.0};
+            if (s.kc[l]) {
+                int p0, p1;
+                col_src(ct, l, Kb1, p0, p1);
+                if (p0 >= 0 && s.kp[p0]) v = cadd(v, B1[(size_t)r * KL + p0]);
+                if (p1 >= 0 && s.kp[p1]) v = cadd(v, B1[(size_t)r * KL + p1]);
+                v = cscale(v, t);
+            }
+            X1[(size_t)r * KL + l] = v;
+        }
+    __syncthreads();
+    // B' = (B1 W) Y into B1; (B1 W) G'_a2a2 into X2; A' = A1 + that (B1 W)^T
+    cta_gemm<double, false, false>(K1, Kb2, K2, X1, KL, X2, KL, B1, KL, GEMM_SET, s.gemm);
+    cta_gemm<double, false, false>(K1, K2, K2, X1, KL, B2, KL, X2, KL, GEMM_SET, s.gemm);
+    cta_gemm<double, false, true>(K1, K1, K2, X2, KL, X1, KL, A1, KL, GEMM_ADD, s.gemm);
+    for (int e = threadIdx.x; e < Kb2 * Kb2; e += NT) {
+        const int i = e / Kb2, l = e % Kb2;
+        D1[(size_t)i * KL + l] = A2[(size_t)i * KL + l];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *I1.flag = flag;
+    __syncthreads();
+}
+
 // The interior domains joined, left to right, onto the left half in binary64.
 // Joining domain d (columns ka .. kb, blocks A = G_aa, B = G_ab, D = g_b of the
 // domain with its absorbing self-energy -i|t| at ka) to the system from the
@@ -413,14 +545,21 @@ __device__ int join_interiors(const SweepArgs& a, const ChainDev& ch, const Chai
     int flag = 0;
     to_binary64<R>(L.G, col_size(c, q), col_size(c, q), KL);
     to_binary64<R>(L.P, KL, col_size(c, q), KL);
-    for (int d = 1; d + 1 < a.ndom; ++d) {
+    // with more than one interior domain the tree of joins (tree_join_body)
+    // has left all of them combined in domain 1's buffers, in binary64
+    const bool tree = a.ndom > 3;
+    const int dlast = tree ? 1 : a.ndom - 2;
+    for (int d = 1; d <= dlast; ++d) {
         const Inner<R> I = inner_of<R>(a.ws, ch, d);
-        const int ka = dom_bound(c.ncol, d, a.ndom), kb = dom_bound(c.ncol, d + 1, a.ndom) - 1;
+        const int ka = dom_bound(c.ncol, d, a.ndom);
+        const int kb = dom_bound(c.ncol, tree ? a.ndom - 1 : d + 1, a.ndom) - 1;
         const int Ka = col_size(c, ka), Kb = col_size(c, kb), Kq = col_size(c, q), ct = ka & 3;
         flag |= *I.flag;
-        to_binary64<R>(I.A, Ka, Ka, KL);
-        to_binary64<R>(I.P, Ka, Kb, KL);
-        to_binary64<R>(I.G, Kb, Kb, KL);
+        if (!tree) {
+            to_binary64<R>(I.A, Ka, Ka, KL);
+            to_binary64<R>(I.P, Ka, Kb, KL);
+            to_binary64<R>(I.G, Kb, Kb, KL);
+        }
         zd* A = reinterpret_cast<zd*>(I.A);
         zd* B = reinterpret_cast<zd*>(I.P);
         zd* D = reinterpret_cast<zd*>(I.G);

@@ -135,6 +135,12 @@ cudaError_t launch_domains(int precision, const ChainDev* chains, const int* ord
                            const int* lead_status, const LeadDev* leads, void* ws, int ndom,
                            cudaStream_t st);
 cudaError_t configure_domains(int precision, int Kmax);
+// The tree of joins that combines the ndom - 2 interior domains of every
+// chain into one segment (ceil(log2(ndom - 2)) launches; nothing for ndom <=
+// 3); launch_merge runs it before the final joins.
+cudaError_t launch_tree(int precision, const ChainDev* chains, const int* order, int nchains,
+                        int Kmax, double eta_device, const void* leadout, const int* lead_status,
+                        const LeadDev* leads, void* ws, int ndom, cudaStream_t st);
 
 // The same three steps as one persistent kernel (rgf_batch.cu): one block per
 // SM (at most 2 * nchains), each taking the next half from a work queue in the

@@ -99,6 +99,11 @@ cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order
     if (nchains <= 0) return cudaSuccess;
     cudaError_t e = configure_phased(precision, Kmax);
     if (e != cudaSuccess) return e;
+    if (ndom > 3) {
+        e = launch_tree(precision, chains, order, nchains, Kmax, eta_device, leadout, lead_status,
+                        leads, ws, ndom, st);
+        if (e != cudaSuccess) return e;
+    }
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, T, status, ndom);
     auto kern = binary64(precision) ? merge_kernel<double> : merge_kernel<df32>;

@@ -1,6 +1,6 @@
-"""Chains cut into more than two domains (interior domains recursed as isolated
-systems, joined by the Dyson equation across their boundary bonds) against the
-oracle, in all four precisions."""
+"""Chains cut into more than two domains (interior domains recursed as segments
+open at their first column, combined by a tree of Dyson joins across their
+boundary bonds) against the oracle, in all four precisions."""
 import numpy as np
 import pytest
 
@@ -27,7 +27,7 @@ def _oracle(N, L, E, eps, rem):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
-@pytest.mark.parametrize("ndom", [3, 4, 6])
+@pytest.mark.parametrize("ndom", [3, 4, 6, 9])
 def test_interior_domains_vs_oracle(rgflib, domains, prec, ndom):
     # domain boundaries on every column type (ncol = 4L split in ndom parts),
     # edge vacancies, energies near and away from E = 0
@@ -58,7 +58,7 @@ def test_pair_fallback_inside_interior_domains(rgflib, domains, prec):
         eps[cell, 2 * 5 + 1] = E - delta
     rem = workloads.edge_removed(N, L, 0.3, 9)
     rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps, removed=rem)
-    for ndom in (3, 5, 8):
+    for ndom in (3, 5, 8, 13):
         domains(ndom)
         T, st = rgflib.conductance([rib] * 2, np.array([E, -0.4]), 1e-8, 1e-8, prec, check=False)
         assert (st == 0).all()
@@ -69,9 +69,9 @@ def test_pair_fallback_inside_interior_domains(rgflib, domains, prec):
 
 def test_domain_count_is_capped_and_automatic(rgflib, domains):
     # forcing more domains than half the columns caps them (L = 2: 8 columns,
-    # at most 4 domains); the automatic count for one chain of 160 columns is 3
+    # at most 4 domains); the automatic count for one chain of 160 columns is 5
     assert rgflib.auto_domains(1, 8, 152) == 2
-    assert rgflib.auto_domains(1, 160, 152) == 3
+    assert rgflib.auto_domains(1, 160, 152) == 5
     N, L = 15, 2
     eps = workloads.anderson_onsite(N, L, 0.2, 3)
     rib = rgflib.Ribbon(N, L, T_HOP, onsite=eps)

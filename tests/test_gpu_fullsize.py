@@ -100,7 +100,7 @@ def test_mixed_paths_match_binary64_at_full_size(rgflib, full_ribbon, bench_fp64
 @pytest.mark.parametrize("prec", [0, 2])
 def test_full_size_many_domains_vs_oracle(rgflib, full_ribbon, prec):
     # the six golden chains with the automatic domain count (25 domains each:
-    # 152 SMs over 6 chains, at most sqrt(16000 / 16)); near E = 0 the joins'
+    # 152 SMs over 6 chains); near E = 0 the joins'
     # rounding adds up (measured 1.9e-9 in binary64 at 5 meV, against 1e-10
     # with two domains), away from it the two-domain bounds hold
     g, e0 = GOLD["L4000"], GOLD["L4000_E0"]

@@ -89,11 +89,12 @@ def test_autotune_argument_checks(lib):
 
 
 def test_automatic_domain_count(lib):
-    # one SM per domain for every chain, at most sqrt(ncol / 16), at least 2,
-    # at most ncol / 2
+    # one SM per domain for every chain, at most ncol / 32, at least 2, at
+    # most ncol / 2
     assert lib.auto_domains(69, 16000, 152) == 2        # the bench batch: two halves
-    assert lib.auto_domains(1, 16000, 152) == 31        # one long chain
+    assert lib.auto_domains(1, 16000, 152) == 152       # one long chain: every SM
     assert lib.auto_domains(10, 16000, 152) == 15
+    assert lib.auto_domains(1, 160, 152) == 5
     assert lib.auto_domains(1, 16, 152) == 2
     assert lib.auto_domains(1, 4, 152) == 2
     assert lib.auto_domains(2048, 400, 152) == 2
