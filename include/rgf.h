@@ -77,7 +77,11 @@ typedef enum {
                             sliced from binary64 and summed in binary64: products
                             accurate to a few units of 2^-53 of (row max x column max
                             x inner dimension), in the forward, gradient and LDOS
-                            sweeps alike. */
+                            sweeps alike.
+                            With both _TC precisions, ribbons wider than N = 1940
+                            (ceil(N/2) > 970) run their products on the pipes, as
+                            RGF_MIXED / RGF_FP64: the tensor-core tiles and the
+                            sweep's panels no longer fit one block's shared memory. */
 } rgf_precision;
 
 /* One ribbon instance (the paper's input step: geometry, defects, disorder). */

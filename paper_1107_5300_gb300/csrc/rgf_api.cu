@@ -228,7 +228,8 @@ rgf_status make_plan(const rgf_ribbon* const* rib, int nchains, int precision, P
             const rgf_tune_entry te = lookup_tune(precision, rgf::col_KL(r->N));
             ch.panel = (int8_t)te.panel;
             ch.pairs = (int8_t)(te.pairs != 0);
-            ch.tc = (int8_t)(tc_precision(precision) && te.engine == RGF_ENGINE_TENSOR);
+            ch.tc = (int8_t)(tc_precision(precision) && te.engine == RGF_ENGINE_TENSOR &&
+                             rgf::tc_layout_fits(rgf::col_KL(r->N)));
             engine[c] = ch.tc;
             pl.seg_cols[c] = 0;
             pl.ws_elems += rgf::chain_ws_elems(r->N, pl.ndom);

@@ -361,6 +361,8 @@ cudaError_t launch_grad(int precision, const ChainDev* chains, const int* order,
                         const LeadDev* leads, void* ws, const int* seg_cols, double* T, double* dT,
                         double* rho, int out_mode, int32_t* status, cudaStream_t st) {
     if (nchains <= 0) return cudaSuccess;
+    // the _TC precisions on the pipes where the tensor-core layout does not fit
+    if ((precision == 2 || precision == 3) && !tc_layout_fits(Kmax)) precision = precision == 2 ? 1 : 0;
     const bool tc = precision == 2 || precision == 3;
     const size_t smem = sweep_smem_bytes(Kmax, tc);
     cudaError_t e;

@@ -92,6 +92,11 @@ __host__ __device__ inline int dom_bound(int ncol, int d, int ndom) {
 // Shared memory of the sweep / lead kernels for a largest column size Kmax
 // (tc: with the tensor-core area of the RGF_MIXED_TC path).
 size_t sweep_smem_bytes(int Kmax, bool tc = false);
+// Whether the tensor-core layout (the sweep's buffers beside the digit tiles)
+// fits a block's shared memory for columns of up to Kmax orbitals: up to
+// Kmax = 970 (N = 1940).  Wider chains of the _TC precisions run their
+// products on the pipes.
+bool tc_layout_fits(int Kmax);
 
 // Controls of the decimation (process-wide, set through rgf_set_lead_controls):
 // iteration cap and the tolerance of the fixed-point residual test.

@@ -9,6 +9,10 @@ size_t sweep_smem_bytes(int Kmax, bool tc) {
     return sweep_total_bytes(Kmax, gj_panel_width(Kmax, tc), tc);
 }
 
+bool tc_layout_fits(int Kmax) {
+    return sweep_total_bytes(Kmax, gj_panel_width(Kmax, true), true) <= 232448;
+}
+
 // Three-launch schedule: each kernel runs one step for every half (or chain),
 // blocks in the order of `order`.
 template <class R>

@@ -132,6 +132,12 @@ class RGFError(RuntimeError):
         self.status = status
 
 
+# Per-chain failures (the call ran and every chain has its status); the other
+# codes (RGF_EINVAL, RGF_ENOMEM, RGF_ECUDA from a host-buffer call) mean the
+# outputs were not written, and always raise.
+_CHAIN_ERRORS = (RGF_ENOCONV, RGF_ESINGULAR, RGF_ENONFINITE, RGF_ETIMEOUT, RGF_EBOUNDS)
+
+
 def _check(st: int, allow=()):
     if st != RGF_OK and st not in allow:
         raise RGFError(st, lib.rgf_last_error().decode())
@@ -237,8 +243,7 @@ def conductance(ribbons, E, eta_device=1e-8, eta_lead=1e-8, precision=RGF_FP64, 
     r = lib.rgf_conductance(_handles(ribbons), _ptr(E, C.c_double), E.size, float(eta_device),
                             float(eta_lead), int(precision), _ptr(T, C.c_double),
                             st.ctypes.data_as(_i32p))
-    if check:
-        _check(r)
+    _check(r, allow=() if check else _CHAIN_ERRORS)
     return T, st
 
 
@@ -266,8 +271,7 @@ def conductance_grad(ribbons, E, eta_device=1e-8, eta_lead=1e-8, precision=RGF_F
                                  float(eta_device), float(eta_lead), int(precision),
                                  int(ckpt_stride), _ptr(T, C.c_double), _ptr(g, C.c_double),
                                  st.ctypes.data_as(_i32p))
-    if check:
-        _check(r)
+    _check(r, allow=() if check else _CHAIN_ERRORS)
     return T, g, st
 
 
@@ -299,8 +303,7 @@ def ldos(ribbons, E, eta_device=1e-8, eta_lead=1e-8, precision=RGF_FP64, ckpt_st
     r = lib.rgf_ldos(_handles(ribbons), _ptr(E, C.c_double), E.size, float(eta_device),
                      float(eta_lead), int(precision), int(ckpt_stride), _ptr(T, C.c_double),
                      _ptr(rho, C.c_double), st.ctypes.data_as(_i32p))
-    if check:
-        _check(r)
+    _check(r, allow=() if check else _CHAIN_ERRORS)
     return T, rho, st
 
 

@@ -256,6 +256,29 @@ def test_wide_columns_vs_oracle(rgflib, wide_case, prec):
         assert abs(t - ref) < tol * max(1.0, abs(ref)), (e, t, ref)
 
 
+@pytest.mark.slow
+def test_widest_accepted_ribbon_precisions_agree(rgflib):
+    # N = 2047, the widest ribbon the ABI accepts (KL = 1024 orbitals per
+    # column: eight row tiles of the tensor-core products, the narrowest
+    # Gauss-Jordan panel, the largest shared-memory layout).  The oracle's
+    # full-cell decimation at M = 4094 is out of reach in a test, so the four
+    # precisions are checked against each other and against 0 <= T <= n_ch.
+    N, L = 2047, 2
+    eps = workloads.anderson_onsite(N, L, 0.1, 2047)
+    rem = workloads.edge_removed(N, L, 0.05, 2048)
+    Es = np.array([-0.11, 0.043])
+    out = {}
+    for prec in (0, 1, 2, 3):
+        T, st = _run(rgflib, N, L, Es, eps, rem, prec)
+        assert (st == 0).all(), (prec, st)
+        out[prec] = T
+    for e, t in zip(Es, out[0]):
+        assert -1e-9 <= t <= bands.channels_closed_form(N, e) + 1e-9
+    assert np.max(np.abs(out[1] - out[0])) < 1e-7
+    assert np.max(np.abs(out[2] - out[0])) < 1e-7
+    assert np.max(np.abs(out[3] - out[0])) < 1e-9
+
+
 def test_config5_width_precisions_agree(rgflib):
     # N = 1001 (KL = 501, the 2002-orbital ribbon): four row tiles and four
     # accumulation groups; the four precisions agree and respect 0 <= T <= n_ch
