@@ -153,6 +153,10 @@ extern "C" rgf_status rgf_conductance_noalloc(int N, int L, double t, const doub
     e = cudaGetLastError();
     if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
     const int Kmax = rgf::col_KL(N);
+    // as rgf_conductance_dev: the tensor-core layout of the widest columns
+    // exceeds a block's shared memory, and their products run on the pipes
+    if ((precision == RGF_MIXED_TC || precision == RGF_FP64_TC) && !rgf::tc_layout_fits(Kmax))
+        precision = precision == RGF_MIXED_TC ? RGF_MIXED : RGF_FP64;
     e = rgf::launch_lead(dleads, nE, Kmax, eta_lead, sp + o_lws, sp + o_lout, dlst, nullptr, st);
     if (e != cudaSuccess) return nfail(RGF_ECUDA, cudaGetErrorString(e));
     e = rgf::launch_prep(precision, dchains, dorder, nE, Kmax, eta_device, sp + o_lout, dlst, dleads,
