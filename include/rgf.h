@@ -78,8 +78,8 @@ typedef enum {
                             accurate to a few units of 2^-53 of (row max x column max
                             x inner dimension), in the forward, gradient and LDOS
                             sweeps alike.
-                            With both _TC precisions, ribbons wider than N = 1940
-                            (ceil(N/2) > 970) run their products on the pipes, as
+                            With both _TC precisions, ribbons wider than N = 1960
+                            (ceil(N/2) > 980) run their products on the pipes, as
                             RGF_MIXED / RGF_FP64: the tensor-core tiles and the
                             sweep's panels no longer fit one block's shared memory. */
 } rgf_precision;

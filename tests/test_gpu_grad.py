@@ -161,3 +161,23 @@ def test_device_gradient_entry_point(rgflib):
     assert np.array_equal(Gd.cpu().numpy(), g_h) and np.array_equal(Td.cpu().numpy(), T_h)
     ref = 0.5 * g_h[0] - 1.0 * g_h[1] + 2.0 * g_h[2]
     assert np.abs(Vd.cpu().numpy() - ref).max() < 1e-14 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.slow
+def test_widest_ribbon_gradient_and_ldos_run_on_the_pipes(rgflib):
+    # N = 2047 (KL = 1024): the tensor-core layout of the two-sided sweep does
+    # not fit a block's shared memory beyond KL = 980, so RGF_MIXED_TC runs the
+    # same kernel as RGF_MIXED (RGF_FP64_TC as RGF_FP64, by the same rule):
+    # bit-identical gradients and local densities of states
+    N, L = 2047, 1
+    eps = workloads.anderson_onsite(N, L, 0.1, 71)
+    rib = rgflib.Ribbon(N, L, -2.7, onsite=eps)
+    E = np.array([0.057])
+    Ta, ga, sa = rgflib.conductance_grad([rib], E, 1e-8, 1e-8, rgflib.RGF_MIXED_TC)
+    Tb, gb, sb = rgflib.conductance_grad([rib], E, 1e-8, 1e-8, rgflib.RGF_MIXED)
+    assert (sa == 0).all() and (sb == 0).all()
+    assert np.array_equal(Ta, Tb) and np.array_equal(ga, gb)
+    assert np.isfinite(gb).all() and np.abs(gb).max() > 0.0
+    _, ra, _ = rgflib.ldos([rib], E, 1e-8, 1e-8, rgflib.RGF_MIXED_TC)
+    _, rb, _ = rgflib.ldos([rib], E, 1e-8, 1e-8, rgflib.RGF_MIXED)
+    assert np.array_equal(ra, rb) and rb.max() > 0.0 and rb.min() > -1e-9 * rb.max()
