@@ -216,7 +216,8 @@ int rgf_get_schedule(void);
  * interior domains between them, each recursed as a segment open at its first
  * column (an absorbing self-energy there, taken back out when it is joined)
  * that keeps the blocks of its first and last columns (G_aa, G_ab, g_b).  A
- * tree of joins (the Dyson equation across each boundary bond, binary64)
+ * tree of joins (the Dyson equation across each boundary bond, binary64; in
+ * the _TC precisions its products on the tensor cores, sliced from binary64)
  * combines the interior domains in ceil(log2(ndom - 2)) launches; the merge
  * then joins the left half, the combined interior and the right half.  This
  * is the modified recursion that running one chain in parallel needs: it

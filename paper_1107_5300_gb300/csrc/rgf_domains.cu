@@ -21,12 +21,19 @@ __global__ void __launch_bounds__(NT, 1) domain_kernel(SweepArgs a, int bm) {
 }
 
 // Level `level` of the tree of joins of the interior domains: block b runs
-// join b % njoin of chain order[b / njoin].
-template <class R>
+// join b % njoin of chain order[b / njoin].  TCJ: the joins' products on the
+// tensor cores (binary64 slicing).
+template <class R, bool TCJ>
 __global__ void __launch_bounds__(NT, 1) tree_kernel(SweepArgs a, int bm, int level, int njoin) {
     const int ci = a.order[blockIdx.x / njoin], j = blockIdx.x % njoin;
     if (lead_state(a.lead_status, a.chains[ci].lead) != ST_OK) return;
-    tree_join_body<R>(a, ci, level, j, bm);
+    tc::State tst;
+    if constexpr (TCJ) {
+        SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, true, bm);
+        tc_attach<double>(a.Kmax, s, tst);
+    }
+    tree_join_body<R, TCJ>(a, ci, level, j, bm, &tst);
+    if constexpr (TCJ) tc::teardown(tst.ar);
 }
 
 namespace {
@@ -37,14 +44,23 @@ auto domain_kern(int precision) {
            : precision == 2 ? domain_kernel<df32, true>
                             : domain_kernel<df32, false>;
 }
+// The joins: the tensor-core precisions on the tensor cores, binary64 sliced.
+auto tree_kern(int precision) {
+    return precision == 0   ? tree_kernel<double, false>
+           : precision == 3 ? tree_kernel<double, true>
+           : precision == 2 ? tree_kernel<df32, true>
+                            : tree_kernel<df32, false>;
+}
+size_t tree_smem(int precision, int Kmax) {
+    return uses_tc(precision) ? rec_smem(precision, Kmax) : f64_smem(precision, Kmax);
+}
 
 }  // namespace
 
 cudaError_t configure_domains(int precision, int Kmax) {
     cudaError_t e = set_smem(domain_kern(precision), rec_smem(precision, Kmax));
     if (e != cudaSuccess) return e;
-    return set_smem(binary64(precision) ? tree_kernel<double> : tree_kernel<df32>,
-                    f64_smem(precision, Kmax));
+    return set_smem(tree_kern(precision), tree_smem(precision, Kmax));
 }
 
 cudaError_t launch_tree(int precision, const ChainDev* chains, const int* order, int nchains,
@@ -56,11 +72,11 @@ cudaError_t launch_tree(int precision, const ChainDev* chains, const int* order,
     if (e != cudaSuccess) return e;
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, nullptr, nullptr, ndom);
-    auto kern = binary64(precision) ? tree_kernel<double> : tree_kernel<df32>;
+    auto kern = tree_kern(precision);
     for (int level = 0; (1 << level) < M; ++level) {
         const int njoin = (M + (2 << level) - 1) / (2 << level);
-        kern<<<nchains * njoin, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax),
-                                                                     level, njoin);
+        kern<<<nchains * njoin, NT, tree_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax),
+                                                                      level, njoin);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

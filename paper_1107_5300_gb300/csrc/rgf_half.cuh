@@ -401,10 +401,18 @@ __device__ __forceinline__ void domain_body(const SweepArgs& a, int ci, int d, i
 //     A' = A1 + (B1 W) G'_a2a2 (B1 W)^T,
 // written into node d1's buffers in binary64 (level 0 converts its inputs
 // from the working precision).  One inverse and seven products; a block per
-// join, every join of a level at the same time.
-template <class R>
-__device__ __noinline__ void tree_join_body(const SweepArgs a, int ci, int level, int j, int bm) {
-    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, false, bm);
+// join, every join of a level at the same time.  TCJ (the tensor-core
+// precisions): the products and the inverse's rank-b updates on the tensor
+// cores, sliced from binary64 and summed in binary64 (the block holds TMEM,
+// tst); else on the FP64 pipes.
+template <class R, bool TCJ>
+__device__ __noinline__ void tree_join_body(const SweepArgs a, int ci, int level, int j, int bm,
+                                            tc::State* tst) {
+    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, TCJ, bm);
+    if constexpr (TCJ) {
+        s.gj.tcs = tst;
+        s.tcs = tst;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const ChainDev& ch = a.chains[ci];
     const ChainCtx c = make_ctx(ch, a.leads[ch.lead], a.leadout, a.eta_d, 0);
@@ -474,21 +482,21 @@ __device__ __noinline__ void tree_join_body(const SweepArgs a, int ci, int level
     }
     __syncthreads();
     // X = I - A2 Sigma into X2; B2^T Sigma into D1 (D1 read for the last time)
-    cta_gemm<double, false, false>(K2, K2, K2, A2, KL, X1, KL, X2, KL, GEMM_SET, s.gemm);
+    dense_product<double, false, TCJ>(K2, K2, K2, A2, KL, X1, KL, X2, KL, s);
     for (int e = threadIdx.x; e < K2 * K2; e += NT) {
         const int i = e / K2, l = e % K2;
         zd& x = X2[(size_t)i * KL + l];
         x = {((i == l) ? 1.0 : 0.0) - x.re, -x.im};
     }
     __syncthreads();
-    cta_gemm<double, true, false>(Kb2, K2, K2, B2, KL, X1, KL, D1, KL, GEMM_SET, s.gemm);
+    dense_product<double, true, TCJ>(Kb2, K2, K2, B2, KL, X1, KL, D1, KL, s);
     // X^-1 into X1; Y = X^-1 B2 into X2; G'_a2a2 = X^-1 A2 into B2
     const double amax2 = max_abs2(X2, K2, KL, s.red);
-    flag |= cta_gj_invert<double>(X2, K2, KL, X1, KL, s.gj, amax2);
-    cta_gemm<double, false, false>(K2, Kb2, K2, X1, KL, B2, KL, X2, KL, GEMM_SET, s.gemm);
-    cta_gemm<double, false, false>(K2, K2, K2, X1, KL, A2, KL, B2, KL, GEMM_SET, s.gemm);
+    flag |= cta_gj_invert<double, TCJ>(X2, K2, KL, X1, KL, s.gj, amax2);
+    dense_product<double, false, TCJ>(K2, Kb2, K2, X1, KL, B2, KL, X2, KL, s);
+    dense_product<double, false, TCJ>(K2, K2, K2, X1, KL, A2, KL, B2, KL, s);
     // D' = D2 + (B2^T Sigma) Y into A2, then into D1's place below
-    cta_gemm<double, false, false>(Kb2, Kb2, K2, D1, KL, X2, KL, A2, KL, GEMM_SET, s.gemm);
+    dense_product<double, false, TCJ>(Kb2, Kb2, K2, D1, KL, X2, KL, A2, KL, s);
     for (int e = threadIdx.x; e < Kb2 * Kb2; e += NT) {
         const int i = e / Kb2, l = e % Kb2;
         A2[(size_t)i * KL + l] = cadd(A2[(size_t)i * KL + l], D2[(size_t)i * KL + l]);
@@ -508,12 +516,15 @@ __device__ __noinline__ void tree_join_body(const SweepArgs a, int ci, int level
         }
     __syncthreads();
     // B' = (B1 W) Y into B1; (B1 W) G'_a2a2 into X2; A' = A1 + that (B1 W)^T
-    cta_gemm<double, false, false>(K1, Kb2, K2, X1, KL, X2, KL, B1, KL, GEMM_SET, s.gemm);
-    cta_gemm<double, false, false>(K1, K2, K2, X1, KL, B2, KL, X2, KL, GEMM_SET, s.gemm);
-    cta_gemm<double, false, true>(K1, K1, K2, X2, KL, X1, KL, A1, KL, GEMM_ADD, s.gemm);
+    dense_product<double, false, TCJ>(K1, Kb2, K2, X1, KL, X2, KL, B1, KL, s);
+    dense_product<double, false, TCJ>(K1, K2, K2, X1, KL, B2, KL, X2, KL, s);
+    acc_product<double, TCJ>(K1, K2, X2, X1, A1, KL, s);
     for (int e = threadIdx.x; e < Kb2 * Kb2; e += NT) {
         const int i = e / Kb2, l = e % Kb2;
         D1[(size_t)i * KL + l] = A2[(size_t)i * KL + l];
+    }
+    if constexpr (TCJ) {
+        if (*(volatile int*)tst->ar.err()) flag |= 4;
     }
     __syncthreads();
     if (threadIdx.x == 0) *I1.flag = flag;
@@ -532,7 +543,7 @@ __device__ __noinline__ void tree_join_body(const SweepArgs a, int ci, int level
 // On return L.G = g'_b and L.P = C' of the last interior domain, in the working
 // precision; L.X and the interior domains' buffers are scratch.  Returns the
 // OR of the interior domains' flags and the joins' Gauss-Jordan flags.
-template <class R>
+template <class R, bool TCJ>
 __device__ int join_interiors(const SweepArgs& a, const ChainDev& ch, const ChainCtx& c,
                               SweepSmem<double>& s, const Half<R>& L) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -591,20 +602,20 @@ __device__ int join_interiors(const SweepArgs& a, const ChainDev& ch, const Chai
         }
         __syncthreads();
         // X = I - A Sigma into IX; B^T Sigma into A (A read for the last time)
-        cta_gemm<double, false, false>(Ka, Ka, Ka, A, KL, LX, KL, IX, KL, GEMM_SET, s.gemm);
+        dense_product<double, false, TCJ>(Ka, Ka, Ka, A, KL, LX, KL, IX, KL, s);
         for (int e = threadIdx.x; e < Ka * Ka; e += NT) {
             const int i = e / Ka, l = e % Ka;
             zd& x = IX[(size_t)i * KL + l];
             x = {((i == l) ? 1.0 : 0.0) - x.re, -x.im};
         }
         __syncthreads();
-        cta_gemm<double, true, false>(Kb, Ka, Ka, B, KL, LX, KL, A, KL, GEMM_SET, s.gemm);
+        dense_product<double, true, TCJ>(Kb, Ka, Ka, B, KL, LX, KL, A, KL, s);
         // X^-1 into LX, Y = X^-1 B into IX
         const double amax2 = max_abs2(IX, Ka, KL, s.red);
-        flag |= cta_gj_invert<double>(IX, Ka, KL, LX, KL, s.gj, amax2);
-        cta_gemm<double, false, false>(Ka, Kb, Ka, LX, KL, B, KL, IX, KL, GEMM_SET, s.gemm);
+        flag |= cta_gj_invert<double, TCJ>(IX, Ka, KL, LX, KL, s.gj, amax2);
+        dense_product<double, false, TCJ>(Ka, Kb, Ka, LX, KL, B, KL, IX, KL, s);
         // g'_b = D + (B^T Sigma) Y into E
-        cta_gemm<double, false, false>(Kb, Kb, Ka, A, KL, IX, KL, E, KL, GEMM_SET, s.gemm);
+        dense_product<double, false, TCJ>(Kb, Kb, Ka, A, KL, IX, KL, E, KL, s);
         for (int e = threadIdx.x; e < Kb * Kb; e += NT) {
             const int i = e / Kb, l = e % Kb;
             E[(size_t)i * KL + l] = cadd(E[(size_t)i * KL + l], D[(size_t)i * KL + l]);
@@ -623,7 +634,7 @@ __device__ int join_interiors(const SweepArgs& a, const ChainDev& ch, const Chai
                 LX[(size_t)r * KL + l] = v;
             }
         __syncthreads();
-        cta_gemm<double, false, false>(KL, Kb, Ka, LX, KL, IX, KL, C, KL, GEMM_SET, s.gemm);
+        dense_product<double, false, TCJ>(KL, Kb, Ka, LX, KL, IX, KL, C, KL, s);
         q = kb;
     }
     to_working<R>(L.G, col_size(c, q), col_size(c, q), KL);
@@ -634,10 +645,17 @@ __device__ int join_interiors(const SweepArgs& a, const ChainDev& ch, const Chai
 // The Dyson step across the bond between columns m-1 and m of chain ci, in
 // binary64, and the trace; writes T and the status word.  Scratch: the two
 // halves' X and, once read, their G and P.  bm: the launch's panel width.
+// TCJ (chains of more than two domains in a tensor-core precision): the
+// joins' products and inverses' rank-b updates on the tensor cores, sliced
+// from binary64 and summed in binary64 (the block holds TMEM, tst).
 // Every thread; ends with a barrier.
-template <class R>
-__device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
-    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, false, bm);
+template <class R, bool TCJ = false>
+__device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm, tc::State* tst = nullptr) {
+    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, TCJ, bm);
+    if constexpr (TCJ) {
+        s.gj.tcs = tst;
+        s.tcs = tst;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const ChainDev& ch = a.chains[ci];
     const int lst = lead_state(a.lead_status, ch.lead);
@@ -654,7 +672,7 @@ __device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
     int flag = *L.flag | *Rt.flag;
     int m = left_cols(c.ncol);
     if (a.ndom > 2) {
-        flag |= join_interiors<R>(a, ch, c, s, L);
+        flag |= join_interiors<R, TCJ>(a, ch, c, s, L);
         m = dom_bound(c.ncol, a.ndom - 1, a.ndom);
     }
     const int KL = c.KL, KR = c.KR;
@@ -692,7 +710,7 @@ __device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
     __syncthreads();
     // X = I - gr_m SigmaL_m into XR, its inverse into XL
     to_binary64<R>(Rt.G, K, K, KL);
-    cta_gemm<double, false, false>(K, K, K, GRd, KL, XL, KL, XR, KL, GEMM_SET, s.gemm);
+    dense_product<double, false, TCJ>(K, K, K, GRd, KL, XL, KL, XR, KL, s);
     for (int e = threadIdx.x; e < K * K; e += NT) {
         const int i = e / K, l = e % K;
         zd& x = XR[(size_t)i * KL + l];
@@ -700,7 +718,7 @@ __device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
     }
     __syncthreads();
     const double amax2 = max_abs2(XR, K, KL, s.red);
-    flag |= cta_gj_invert<double>(XR, K, KL, XL, KL, s.gj, amax2);
+    flag |= cta_gj_invert<double, TCJ>(XR, K, KL, XL, KL, s.gj, amax2);
     // Y = Pl_{m-1} W_m (KL x K) into GL (gl no longer needed), then
     // Y (I - gr SigmaL)^-1 into XR and its product with Pr_m^T into GL
     for (int r = warp; r < KL; r += NWARP)
@@ -716,7 +734,7 @@ __device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
             GLd[(size_t)r * KL + l] = v;
         }
     __syncthreads();
-    cta_gemm<double, false, false>(KL, K, K, GLd, KL, XL, KL, XR, KL, GEMM_SET, s.gemm);
+    dense_product<double, false, TCJ>(KL, K, K, GLd, KL, XL, KL, XR, KL, s);
     to_binary64<R>(Rt.P, KR, K, KL);
     cta_gemm<double, false, true>(KL, KR, K, XR, KL, PRd, KL, GLd, KL, GEMM_SET, s.gemm);
     // T = sum_pq gamma_p gamma'_q |P_pq|^2
@@ -726,6 +744,9 @@ __device__ __noinline__ void merge_body(const SweepArgs a, int ci, int bm) {
         const int p = e / KR, q = e % KR;
         const zd v = GLd[(size_t)p * KL + q];
         acc += (-2.0 * w[p].im) * (-2.0 * w[q].im) * (v.re * v.re + v.im * v.im);
+    }
+    if constexpr (TCJ) {
+        if (*(volatile int*)tst->ar.err()) flag |= 4;
     }
     const double T = block_sum(acc, s.red);
     if (threadIdx.x == 0) {

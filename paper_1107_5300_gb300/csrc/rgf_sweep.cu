@@ -40,6 +40,17 @@ __global__ void __launch_bounds__(NT, 1) merge_kernel(SweepArgs a, int bm) {
     merge_body<R>(a, a.order[blockIdx.x], bm);
 }
 
+// The joins of chains cut into more than two domains in a tensor-core
+// precision: products on the tensor cores (binary64 slicing).
+template <class R>
+__global__ void __launch_bounds__(NT, 1) merge_tc_kernel(SweepArgs a, int bm) {
+    tc::State tst;
+    SweepSmem<double> s = carve<double>(rgf_dyn_smem, a.Kmax, true, bm);
+    tc_attach<double>(a.Kmax, s, tst);
+    merge_body<R, true>(a, a.order[blockIdx.x], bm, &tst);
+    tc::teardown(tst.ar);
+}
+
 namespace {
 
 // The shared-memory limits of the three-launch kernels of `precision`.
@@ -110,6 +121,13 @@ cudaError_t launch_merge(int precision, const ChainDev* chains, const int* order
     }
     const SweepArgs a = make_args(chains, order, nchains, Kmax, eta_device, leadout, lead_status,
                                   leads, ws, T, status, ndom);
+    if (ndom > 2 && uses_tc(precision)) {
+        auto kern = binary64(precision) ? merge_tc_kernel<double> : merge_tc_kernel<df32>;
+        const size_t smem = rec_smem(precision, Kmax);
+        if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+        kern<<<nchains, NT, smem, st>>>(a, launch_panel(precision, Kmax));
+        return cudaGetLastError();
+    }
     auto kern = binary64(precision) ? merge_kernel<double> : merge_kernel<df32>;
     kern<<<nchains, NT, f64_smem(precision, Kmax), st>>>(a, launch_panel(precision, Kmax));
     return cudaGetLastError();
