@@ -551,13 +551,18 @@ __device__ __forceinline__ uint32_t zgemm(Op op, int M, int N, int Kc, Area ar, 
                 if (tid == 0) {
                     fence_after();
                     const uint32_t id = idesc(NR);
+                    // digit tile i starts TILE * 2 bytes after tile i - 1: its
+                    // descriptor's address field (16-byte units, every shared
+                    // address below 2^18) is kTileDesc further on
+                    constexpr uint64_t kTileDesc = (uint64_t)(TILE * 2) >> 4;
+                    const uint64_t da = sdesc(ta), db = sdesc(tb);
 #pragma unroll
                     for (int l = 0; l < S; ++l)
 #pragma unroll
                         for (int i = 0; i <= l; ++i) {
                             const int j = l - i, acc = l < NACC - 1 ? l : NACC - 1;
-                            mma(tmem + (uint32_t)(ACOLS * acc), sdesc(ta + i * TILE), sdesc(tb + j * TILE),
-                                id, (init >> acc) & 1u);
+                            mma(tmem + (uint32_t)(ACOLS * acc), da + (uint64_t)i * kTileDesc,
+                                db + (uint64_t)j * kTileDesc, id, (init >> acc) & 1u);
                             init |= 1u << acc;
                         }
                     if (!*ar.skip()) commit(ar.bar());
